@@ -1,0 +1,280 @@
+"""CPU oracle for TFHE gate bootstrapping and CMUX memory (test infrastructure only).
+
+A thin ctypes wrapper over `tfhe_oracle.c`, a plain schoolbook implementation of
+the scheme's definitions (paper Section 2.1.2 "TFHE" and Section 8 "CMUX Memory").
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark import
+this package; the product library never does, and this package imports nothing
+from the product library.
+
+Every function is written against the definitions; all arithmetic is mod 2^32.
+Parity of absolute ciphertext words with the CUDA path rests on the readings R1-R8
+listed at the top of `tfhe_oracle.c`; those readings are pinned by the properties
+the scheme fixes (decryption, truth tables, rounding bounds, algebraic
+identities, structure counts), not by printed ciphertexts (the paper prints none).
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tfhe_oracle.c")
+_LIB = os.path.join(_HERE, "libtfhe_oracle.so")
+
+
+class _P(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("N", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("Bgbit", ctypes.c_int32), ("ks_t", ctypes.c_int32),
+                ("ks_basebit", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-std=c11", "-o", _LIB, _SRC])
+    return _LIB
+
+
+@functools.lru_cache(maxsize=1)
+def _lib():
+    build()
+    lib = ctypes.CDLL(_LIB)
+    vp, i32, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
+    P = ctypes.POINTER(_P)
+    sig = {
+        "orc_poly_mul": (None, [i32, vp, vp, vp]),
+        "orc_rotate": (None, [i32, i32, vp, vp]),
+        "orc_tlwe_phase": (u32, [i32, vp, vp]),
+        "orc_tlwe_decrypt": (i32, [i32, vp, vp]),
+        "orc_trlwe_phase": (None, [i32, vp, vp, vp]),
+        "orc_trlwe_decrypt": (None, [i32, vp, vp, vp]),
+        "orc_decompose": (None, [i32, i32, u32, vp]),
+        "orc_external_product": (None, [P, vp, vp, vp]),
+        "orc_cmux": (None, [P, vp, vp, vp, vp]),
+        "orc_modswitch": (u32, [i32, u32]),
+        "orc_ks_digits": (None, [i32, i32, u32, vp]),
+        "orc_blind_rotate": (None, [P, vp, vp, vp]),
+        "orc_sample_extract": (None, [i32, vp, vp]),
+        "orc_keyswitch": (None, [P, vp, vp, vp]),
+        "orc_gate_combine": (i32, [i32, i32, vp, vp, vp]),
+        "orc_homgate": (i32, [P, vp, vp, i32, vp, vp, vp]),
+        "orc_gate_batch": (i32, [P, vp, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_int64,
+                                 ctypes.c_int64]),
+        "orc_cmux_tree_read": (None, [P, vp, vp, i32, vp]),
+        "orc_ram_write": (None, [P, vp, i32, vp, vp]),
+        "orc_extprod_count": (ctypes.c_uint64, []),
+        "orc_extprod_count_reset": (None, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def _p(params):
+    n, N, l, Bgbit, t, bb = params.abi() if hasattr(params, "abi") else params
+    return ctypes.byref(_P(n, N, l, Bgbit, t, bb))
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+# ---- polynomial primitives -----------------------------------------------------
+
+def poly_mul(a_int, b_torus):
+    a, pa = _c(a_int, np.int32)
+    b, pb = _c(b_torus, np.uint32)
+    out = np.zeros(a.size, np.uint32)
+    _lib().orc_poly_mul(a.size, pa, pb, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def rotate(p, k):
+    a, pa = _c(p, np.uint32)
+    out = np.zeros(a.size, np.uint32)
+    _lib().orc_rotate(a.size, int(k), pa, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def decompose(l, Bgbit, t):
+    out = np.zeros(l, np.int32)
+    _lib().orc_decompose(l, Bgbit, int(t) & 0xFFFFFFFF, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def ks_digits(t, basebit, a):
+    out = np.zeros(t, np.uint32)
+    _lib().orc_ks_digits(t, basebit, int(a) & 0xFFFFFFFF, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def fn_address(name: str) -> int:
+    """Address of an oracle C function (for the exhaustive C checkers in the tests)."""
+    return ctypes.cast(getattr(_lib(), name), ctypes.c_void_p).value
+
+
+def modswitch(N, x):
+    return int(_lib().orc_modswitch(N, int(x) & 0xFFFFFFFF))
+
+
+# ---- encryption-side checks ------------------------------------------------------
+
+def tlwe_phase(s, c):
+    s, ps = _c(s, np.uint32)
+    c, pc = _c(c, np.uint32)
+    return int(_lib().orc_tlwe_phase(s.size, ps, pc))
+
+
+def tlwe_decrypt(s, c) -> np.ndarray:
+    """Decrypt one TLWE (u32[n+1]) or a batch (u32[k][n+1])."""
+    s, ps = _c(s, np.uint32)
+    c = np.ascontiguousarray(c, np.uint32)
+    flat = c.reshape(-1, s.size + 1)
+    out = np.array([_lib().orc_tlwe_decrypt(s.size, ps, ctypes.c_void_p(row.ctypes.data))
+                    for row in flat], np.uint8)
+    return out if c.ndim > 1 else out[0]
+
+
+def trlwe_phase(s, c):
+    s, ps = _c(s, np.uint32)
+    c, pc = _c(c, np.uint32)
+    out = np.zeros(s.size, np.uint32)
+    _lib().orc_trlwe_phase(s.size, ps, pc, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def trlwe_decrypt(s, c):
+    s, ps = _c(s, np.uint32)
+    c, pc = _c(c, np.uint32)
+    out = np.zeros(s.size, np.uint8)
+    _lib().orc_trlwe_decrypt(s.size, ps, pc, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+# ---- evaluation ----------------------------------------------------------------
+
+def external_product(params, C, d):
+    C, pC = _c(C, np.uint32)
+    d, pd = _c(d, np.uint32)
+    out = np.zeros_like(d)
+    _lib().orc_external_product(_p(params), pC, pd, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def cmux(params, C, d1, d0):
+    C, pC = _c(C, np.uint32)
+    d1, p1 = _c(d1, np.uint32)
+    d0, p0 = _c(d0, np.uint32)
+    out = np.zeros_like(d0)
+    _lib().orc_cmux(_p(params), pC, p1, p0, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def blind_rotate(params, bsk, bar):
+    bsk, pb = _c(bsk, np.uint32)
+    bar, pbar = _c(bar, np.uint32)
+    out = np.zeros((2, params.N), np.uint32)
+    _lib().orc_blind_rotate(_p(params), pb, pbar, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def sample_extract(trlwe):
+    c, pc = _c(trlwe, np.uint32)
+    N = c.shape[-1]
+    out = np.zeros(N + 1, np.uint32)
+    _lib().orc_sample_extract(N, pc, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def keyswitch(params, ksk, tlwe1):
+    k, pk = _c(ksk, np.uint32)
+    c, pc = _c(tlwe1, np.uint32)
+    out = np.zeros(params.n + 1, np.uint32)
+    _lib().orc_keyswitch(_p(params), pk, pc, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def gate_combine(n, gate_type, c1, c2):
+    a, pa = _c(c1, np.uint32)
+    b, pb = _c(c2, np.uint32)
+    out = np.zeros(n + 1, np.uint32)
+    rc = _lib().orc_gate_combine(n, int(gate_type), pa, pb, ctypes.c_void_p(out.ctypes.data))
+    if rc != 0:
+        raise ValueError("unknown gate type")
+    return out
+
+
+def homgate(params, bsk, ksk, gate_type, c1, c2):
+    bsk, pb = _c(bsk, np.uint32)
+    ksk, pk = _c(ksk, np.uint32)
+    a, pa = _c(c1, np.uint32)
+    b, pbb = _c(c2, np.uint32)
+    out = np.zeros(params.n + 1, np.uint32)
+    rc = _lib().orc_homgate(_p(params), pb, pk, int(gate_type), pa, pbb,
+                            ctypes.c_void_p(out.ctypes.data))
+    if rc != 0:
+        raise ValueError("unknown gate type")
+    return out
+
+
+def gate_batch(params, bsk, ksk, inp, types, idx, gates=None, threads: int | None = None):
+    """Evaluate gates (all, or the listed subset) of a batch; one gate per thread.
+
+    Returns u32[len(gates)][n+1] in the order of `gates`."""
+    bsk, pb = _c(bsk, np.uint32)
+    ksk, pk = _c(ksk, np.uint32)
+    inp, pi = _c(inp, np.uint32)
+    types, pt = _c(types, np.uint8)
+    idx, px = _c(idx, np.int32)
+    G = types.size
+    gates = np.arange(G) if gates is None else np.asarray(gates, np.int64)
+    out = np.zeros((G, params.n + 1), np.uint32)
+    po = ctypes.c_void_p(out.ctypes.data)
+    pp = _p(params)
+    lib = _lib()
+
+    def one(g):
+        rc = lib.orc_gate_batch(pp, pb, pk, pi, inp.shape[0], pt, px, po, int(g), int(g) + 1)
+        if rc != 0:
+            raise ValueError(f"bad gate {g}")
+
+    threads = threads or os.cpu_count() or 1
+    if threads == 1 or len(gates) == 1:
+        for g in gates:
+            one(g)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(one, gates))
+    return out[gates]
+
+
+def cmux_tree_read(params, addr_trgsw, table, v):
+    a, pa = _c(addr_trgsw, np.uint32)
+    t, pt = _c(table, np.uint32)
+    out = np.zeros((2, params.N), np.uint32)
+    _lib().orc_cmux_tree_read(_p(params), pa, pt, int(v), ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def ram_write(params, addr_trgsw, v, new_cell, cells):
+    a, pa = _c(addr_trgsw, np.uint32)
+    nc, pn = _c(new_cell, np.uint32)
+    cells = np.array(cells, np.uint32, copy=True, order="C")
+    _lib().orc_ram_write(_p(params), pa, int(v), pn, ctypes.c_void_p(cells.ctypes.data))
+    return cells
+
+
+def extprod_count() -> int:
+    return int(_lib().orc_extprod_count())
+
+
+def extprod_count_reset() -> None:
+    _lib().orc_extprod_count_reset()

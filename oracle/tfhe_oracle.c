@@ -1,0 +1,347 @@
+/*
+ * tfhe_oracle.c -- plain, slow, obviously correct CPU oracle for TFHE gate
+ * bootstrapping and the CMUX-tree memory of
+ *   "Virtual Secure Platform: A Five-Stage Pipeline Processor over TFHE".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * executes this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or constant generator with
+ * the CUDA path.
+ *
+ * Everything is integer arithmetic modulo 2^32 on uint32 (Torus32): a torus value
+ * x in [-1/2, 1/2) (Section 2.1.2, Notations) is stored as round(x * 2^32) mod 2^32
+ * and its sign is the sign of the int32 view.  Polynomials live in
+ * Z[X]/(X^N + 1) and are multiplied by the schoolbook definition.  No blocking,
+ * transforms or reordering: each function follows the definition it cites.
+ *
+ * Readings of points the paper leaves open (each also listed in the design notes):
+ *   R1 sgn(0): a phase that is >= 0 as int32 decrypts to 1.
+ *   R2 gadget decomposition (implied by the TRGSW rows m/Bg^j, Section 2.1.2
+ *      "TRGSW"): l signed digits in [-Bg/2, Bg/2), rounding to nearest with ties
+ *      upward, digit j (1-based) paired with TRGSW row j (weight 1/Bg^j).
+ *   R3 ModSwitch to Z_{2N}: round half up with 32-bit wrap.
+ *   R4 BlindRotate (Section 2.1.2 "Bootstrapping in TFHE", "CMUX"): accumulator
+ *      starts at X^{-b~} (0, v) with every coefficient of v equal to mu = 1/8, then
+ *      ACC <- CMUX(BK_i, X^{a~_i} ACC, ACC) for i = 0..n-1.
+ *   R5 Identity key switching (Section 2.1.2 "Sample Extraction and Identity Key
+ *      Switching"): unsigned base-2^basebit digits of each extracted mask
+ *      coefficient rounded to t digits; a zero digit contributes nothing.
+ *   R6 gate constants (Section 2.1.2 "Homomorphic Gates"; TFHE's standard linear
+ *      combinations); "NY" negates the first input, "YN" the second.
+ *   R7 CMUX tree (Section 8.2 "Read Unit"): address bit j selects at tree level j,
+ *      least significant bit at the leaves.
+ *   R8 RAM write bar (Section 8.2 "Write Unit" and its Remark): for cell c the
+ *      controlled data passes through v CMUXes, bit j ascending; the selector is
+ *      C_j when bit j of c is 1 and G - C_j otherwise (G the gadget TRGSW of 1).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { int32_t n, N, l, Bgbit, ks_t, ks_basebit; } orc_params;
+
+/* Counts external products evaluated by this thread (for the CMUX-count pin). */
+static _Thread_local uint64_t orc_extprod_calls = 0;
+uint64_t orc_extprod_count(void) { return orc_extprod_calls; }
+void orc_extprod_count_reset(void) { orc_extprod_calls = 0; }
+
+/* ---- Torus polynomials (Section 2.1.2, Notations: T_N[X], Z_N[X]) ---------- */
+
+/* out = a * b in Z[X]/(X^N+1), a with integer coefficients, b on the torus.
+ * Schoolbook: term a_i b_j lands on X^{i+j}; X^N = -1 folds i+j >= N with a minus. */
+void orc_poly_mul(int N, const int32_t *a, const uint32_t *b, uint32_t *out) {
+    uint32_t *acc = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    for (int i = 0; i < N; i++) {
+        const uint32_t ai = (uint32_t)a[i];
+        for (int j = 0; j < N - i; j++) acc[i + j] += ai * b[j];     /* i + j < N */
+        for (int j = N - i; j < N; j++) acc[i + j - N] -= ai * b[j]; /* X^N = -1 */
+    }
+    memcpy(out, acc, sizeof(uint32_t) * (size_t)N);
+    free(acc);
+}
+
+/* out = X^k * p in T_N[X], k in [0, 2N).  X^k p has coefficient p_{j-k} at X^j for
+ * j >= k; the wrapped terms carry X^N = -1.  For k >= N, X^k = -X^{k-N}. */
+void orc_rotate(int N, int k, const uint32_t *p, uint32_t *out) {
+    int neg = 0;
+    k %= 2 * N;
+    if (k < 0) k += 2 * N;
+    if (k >= N) { k -= N; neg = 1; }
+    for (int j = 0; j < N; j++) {
+        uint32_t v = (j >= k) ? p[j - k] : (uint32_t)(0u - p[j - k + N]);
+        out[j] = neg ? (uint32_t)(0u - v) : v;
+    }
+}
+
+/* ---- TLWE / TRLWE phase and decryption (Section 2.1.2 "TLWE", "TRLWE") ----- */
+
+/* phase = b - <a, s> */
+uint32_t orc_tlwe_phase(int n, const uint32_t *s, const uint32_t *c) {
+    uint32_t as = 0;
+    for (int i = 0; i < n; i++) as += c[i] * s[i];
+    return c[n] - as;
+}
+
+/* Decryption returns (1 + sgn(phase)) / 2 with reading R1. */
+int orc_tlwe_decrypt(int n, const uint32_t *s, const uint32_t *c) {
+    return (int32_t)orc_tlwe_phase(n, s, c) >= 0 ? 1 : 0;
+}
+
+/* phase[X] = b[X] - a[X] s[X]; s binary (taken as an integer polynomial). */
+void orc_trlwe_phase(int N, const uint32_t *s, const uint32_t *c, uint32_t *phase) {
+    int32_t *si = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    uint32_t *as = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    for (int i = 0; i < N; i++) si[i] = (int32_t)s[i];
+    orc_poly_mul(N, si, c, as); /* a[X] is the first polynomial of c */
+    for (int i = 0; i < N; i++) phase[i] = c[N + i] - as[i];
+    free(si);
+    free(as);
+}
+
+void orc_trlwe_decrypt(int N, const uint32_t *s, const uint32_t *c, uint8_t *bits) {
+    uint32_t *ph = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    orc_trlwe_phase(N, s, c, ph);
+    for (int i = 0; i < N; i++) bits[i] = (int32_t)ph[i] >= 0 ? 1 : 0;
+    free(ph);
+}
+
+/* ---- Gadget decomposition (reading R2) ------------------------------------ */
+
+/* Digits d_1..d_l in [-Bg/2, Bg/2) with sum_j d_j 2^{32 - j Bgbit} = t rounded to
+ * the nearest multiple of 2^{32 - l Bgbit}.  Adding Bg/2 to every digit position
+ * and half of the last weight turns signed rounding into unsigned truncation. */
+void orc_decompose(int l, int Bgbit, uint32_t t, int32_t *digits) {
+    const uint32_t Bg = 1u << Bgbit, half = Bg / 2;
+    uint32_t offset = 1u << (32 - l * Bgbit - 1);
+    for (int j = 1; j <= l; j++) offset += half << (32 - j * Bgbit);
+    uint32_t u = t + offset;
+    for (int j = 1; j <= l; j++)
+        digits[j - 1] = (int32_t)((u >> (32 - j * Bgbit)) & (Bg - 1)) - (int32_t)half;
+}
+
+/* ---- External product and CMUX (Section 2.1.2 "TRGSW", "CMUX") -------------- */
+
+/* out = C (.) d = sum_{j<l} Dec_j(a) * C[j] + sum_{j<l} Dec_j(b) * C[l+j],
+ * C a TRGSW u32[2l][2][N], d a TRLWE u32[2][N]; each product is in T_N[X]. */
+void orc_external_product(const orc_params *p, const uint32_t *C, const uint32_t *d,
+                          uint32_t *out) {
+    const int N = p->N, l = p->l;
+    int32_t *dig = (int32_t *)malloc(sizeof(int32_t) * (size_t)2 * l * N);
+    uint32_t *prod = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    uint32_t *res = (uint32_t *)calloc((size_t)2 * N, sizeof(uint32_t));
+    int32_t tmp[64];
+    /* digit polynomials: row j < l from the a-polynomial, row l + j from b */
+    for (int c = 0; c < 2; c++)
+        for (int k = 0; k < N; k++) {
+            orc_decompose(l, p->Bgbit, d[c * N + k], tmp);
+            for (int j = 0; j < l; j++) dig[(size_t)(c * l + j) * N + k] = tmp[j];
+        }
+    for (int row = 0; row < 2 * l; row++)
+        for (int col = 0; col < 2; col++) {
+            orc_poly_mul(N, dig + (size_t)row * N, C + ((size_t)row * 2 + col) * N, prod);
+            for (int k = 0; k < N; k++) res[col * N + k] += prod[k];
+        }
+    memcpy(out, res, sizeof(uint32_t) * (size_t)2 * N);
+    free(dig);
+    free(prod);
+    free(res);
+    orc_extprod_calls++;
+}
+
+/* CMUX(C, d1, d0) = d0 + C (.) (d1 - d0): selects d1 when C encrypts 1. */
+void orc_cmux(const orc_params *p, const uint32_t *C, const uint32_t *d1, const uint32_t *d0,
+              uint32_t *out) {
+    const int N2 = 2 * p->N;
+    uint32_t *diff = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N2);
+    uint32_t *ep = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N2);
+    for (int k = 0; k < N2; k++) diff[k] = d1[k] - d0[k];
+    orc_external_product(p, C, diff, ep);
+    for (int k = 0; k < N2; k++) out[k] = d0[k] + ep[k];
+    free(diff);
+    free(ep);
+}
+
+/* ---- Bootstrapping: ModSwitch, BlindRotate, SampleExtract, IKS ------------- */
+
+/* Reading R3: x~ = round(x * 2N / 2^32) mod 2N. */
+uint32_t orc_modswitch(int N, uint32_t x) {
+    int logN2 = 0;
+    while ((1 << logN2) < 2 * N) logN2++;
+    const int s = 32 - logN2;
+    return (uint32_t)(x + (1u << (s - 1))) >> s;
+}
+
+/* Reading R4.  bar = (a~_0..a~_{n-1}, b~) in Z_{2N}; bsk u32[n][2l][2][N];
+ * acc u32[2][N] receives the rotated test vector. */
+void orc_blind_rotate(const orc_params *p, const uint32_t *bsk, const uint32_t *bar,
+                      uint32_t *acc) {
+    const int N = p->N, n = p->n;
+    const size_t per = (size_t)2 * p->l * 2 * N;
+    const uint32_t mu = 1u << 29;
+    uint32_t *tv = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+    uint32_t *rot = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)2 * N);
+    for (int k = 0; k < N; k++) tv[k] = mu;
+    memset(acc, 0, sizeof(uint32_t) * (size_t)N);                      /* a = 0 */
+    orc_rotate(N, (int)((2 * N - bar[n] % (2 * N)) % (2 * N)), tv, acc + N); /* b = X^{-b~} v */
+    for (int i = 0; i < n; i++) {
+        orc_rotate(N, (int)bar[i], acc, rot);
+        orc_rotate(N, (int)bar[i], acc + N, rot + N);
+        orc_cmux(p, bsk + (size_t)i * per, rot, acc, acc);
+    }
+    free(tv);
+    free(rot);
+}
+
+/* TRLWE -> TLWE lvl1 (coefficient 0): a'_0 = a_0, a'_j = -a_{N-j}, b' = b_0. */
+void orc_sample_extract(int N, const uint32_t *c, uint32_t *out) {
+    out[0] = c[0];
+    for (int j = 1; j < N; j++) out[j] = 0u - c[N - j];
+    out[N] = c[N];
+}
+
+/* Reading R5: digits v_1..v_t in [0, base) with sum_j v_j 2^{32 - j basebit} equal to
+ * a rounded to the nearest multiple of 2^{32 - t basebit} (ties upward). */
+void orc_ks_digits(int t, int bb, uint32_t a, uint32_t *digits) {
+    const uint32_t prec = 1u << (32 - (1 + bb * t));
+    const uint32_t abar = a + prec;
+    for (int j = 0; j < t; j++)
+        digits[j] = (abar >> (32 - (j + 1) * bb)) & ((1u << bb) - 1u);
+}
+
+/* ksk u32[N][t][base][n+1]; in: TLWE lvl1 u32[N+1]; out u32[n+1].
+ * res = (0, b') - sum_i sum_j KSK[i][j][digit_ij(a'_i)]. */
+void orc_keyswitch(const orc_params *p, const uint32_t *ksk, const uint32_t *in, uint32_t *out) {
+    const int n = p->n, N = p->N, t = p->ks_t, bb = p->ks_basebit, base = 1 << bb;
+    uint32_t dig[32];
+    memset(out, 0, sizeof(uint32_t) * (size_t)(n + 1));
+    out[n] = in[N];
+    for (int i = 0; i < N; i++) {
+        orc_ks_digits(t, bb, in[i], dig);
+        for (int j = 0; j < t; j++) {
+            const uint32_t v = dig[j];
+            if (v == 0) continue;
+            const uint32_t *row = ksk + ((((size_t)i * t + j) * base + v) * (size_t)(n + 1));
+            for (int k = 0; k <= n; k++) out[k] -= row[k];
+        }
+    }
+}
+
+/* ---- Homomorphic gates (Section 2.1.2 "Homomorphic Gates"; reading R6) ----- */
+
+/* c = (0, kappa) + s1 c1 + s2 c2 for gate type `type` (enum order NAND, AND, OR, NOR,
+ * XOR, XNOR, ANDNY, ANDYN, ORNY, ORYN).  Returns 0, or -1 for an unknown type. */
+int orc_gate_combine(int n, int type, const uint32_t *c1, const uint32_t *c2, uint32_t *out) {
+    const uint32_t e8 = 1u << 29, e4 = 1u << 30;
+    uint32_t kappa;
+    int32_t s1, s2;
+    switch (type) {
+        case 0: kappa = e8;        s1 = -1; s2 = -1; break; /* NAND */
+        case 1: kappa = 0u - e8;   s1 = 1;  s2 = 1;  break; /* AND */
+        case 2: kappa = e8;        s1 = 1;  s2 = 1;  break; /* OR */
+        case 3: kappa = 0u - e8;   s1 = -1; s2 = -1; break; /* NOR */
+        case 4: kappa = e4;        s1 = 2;  s2 = 2;  break; /* XOR */
+        case 5: kappa = 0u - e4;   s1 = -2; s2 = -2; break; /* XNOR */
+        case 6: kappa = 0u - e8;   s1 = -1; s2 = 1;  break; /* ANDNY = (not a) and b */
+        case 7: kappa = 0u - e8;   s1 = 1;  s2 = -1; break; /* ANDYN = a and (not b) */
+        case 8: kappa = e8;        s1 = -1; s2 = 1;  break; /* ORNY = (not a) or b */
+        case 9: kappa = e8;        s1 = 1;  s2 = -1; break; /* ORYN = a or (not b) */
+        default: return -1;
+    }
+    for (int k = 0; k <= n; k++) out[k] = (uint32_t)s1 * c1[k] + (uint32_t)s2 * c2[k];
+    out[n] += kappa;
+    return 0;
+}
+
+/* One bootstrapped gate: combine -> ModSwitch -> BlindRotate -> SampleExtract -> IKS.
+ * Returns 0, or -1 for an unknown gate type. */
+int orc_homgate(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk, int type,
+                const uint32_t *c1, const uint32_t *c2, uint32_t *out) {
+    const int n = p->n, N = p->N;
+    uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint32_t *bar = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)2 * N);
+    uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(N + 1));
+    int rc = orc_gate_combine(n, type, c1, c2, lin);
+    if (rc == 0) {
+        for (int k = 0; k <= n; k++) bar[k] = orc_modswitch(N, lin[k]);
+        orc_blind_rotate(p, bsk, bar, acc);
+        orc_sample_extract(N, acc, ext);
+        orc_keyswitch(p, ksk, ext, out);
+    }
+    free(lin);
+    free(bar);
+    free(acc);
+    free(ext);
+    return rc;
+}
+
+/* Gates g in [g_begin, g_end) of a batch: out[g] = gate(types[g], in[idx[g][0]], in[idx[g][1]]).
+ * Returns 0, or -1 on a bad type or index. */
+int orc_gate_batch(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk,
+                   const uint32_t *in, int64_t num_in, const uint8_t *types,
+                   const int32_t *idx, uint32_t *out, int64_t g_begin, int64_t g_end) {
+    const size_t w = (size_t)p->n + 1;
+    for (int64_t g = g_begin; g < g_end; g++) {
+        int32_t a = idx[2 * g], b = idx[2 * g + 1];
+        if (a < 0 || b < 0 || a >= num_in || b >= num_in) return -1;
+        if (orc_homgate(p, bsk, ksk, types[g], in + (size_t)a * w, in + (size_t)b * w,
+                        out + (size_t)g * w) != 0)
+            return -1;
+    }
+    return 0;
+}
+
+/* ---- CMUX Memory (Section 8.2) ---------------------------------------------- */
+
+/* Read unit, reading R7: addr u32[v][2l][2][N] (TRGSW of address bit j at [j]),
+ * table u32[2^v][2][N]; out u32[2][N] = row at the encrypted address.
+ * Level j halves the candidates: node_j[k] = CMUX(C_j, node_{j-1}[2k+1], node_{j-1}[2k]). */
+void orc_cmux_tree_read(const orc_params *p, const uint32_t *addr, const uint32_t *table, int v,
+                        uint32_t *out) {
+    const size_t tr = (size_t)2 * p->N, gsw = (size_t)2 * p->l * tr;
+    size_t rows = (size_t)1 << v;
+    uint32_t *cur = (uint32_t *)malloc(sizeof(uint32_t) * rows * tr);
+    memcpy(cur, table, sizeof(uint32_t) * rows * tr);
+    for (int j = 0; j < v; j++) {
+        rows >>= 1;
+        for (size_t k = 0; k < rows; k++)
+            orc_cmux(p, addr + (size_t)j * gsw, cur + (2 * k + 1) * tr, cur + (2 * k) * tr,
+                     cur + k * tr);
+    }
+    memcpy(out, cur, sizeof(uint32_t) * tr);
+    free(cur);
+}
+
+/* Write unit, reading R8: cells u32[2^v][2][N] updated in place.  For every cell c,
+ * r <- new_cell; for j = 0..v-1: r <- CMUX(S_j, r, old_c), S_j = C_j if bit j of c is 1
+ * else G - C_j; cell c <- r.  G has 2^{32 - (j+1) Bgbit} at coefficient 0 of the a
+ * column of row j and of the b column of row l + j, zero elsewhere. */
+void orc_ram_write(const orc_params *p, const uint32_t *addr, int v, const uint32_t *new_cell,
+                   uint32_t *cells) {
+    const int N = p->N, l = p->l;
+    const size_t tr = (size_t)2 * N, gsw = (size_t)2 * l * tr;
+    uint32_t *gmc = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)v * gsw);
+    uint32_t *r = (uint32_t *)malloc(sizeof(uint32_t) * tr);
+    /* G - C_j for every address bit (Remark, Section 8.2) */
+    for (int j = 0; j < v; j++) {
+        uint32_t *dst = gmc + (size_t)j * gsw;
+        const uint32_t *src = addr + (size_t)j * gsw;
+        for (size_t k = 0; k < gsw; k++) dst[k] = 0u - src[k];
+        for (int row = 0; row < 2 * l; row++) {
+            int lev = (row < l ? row : row - l) + 1;
+            int col = row < l ? 0 : 1;
+            dst[((size_t)row * 2 + col) * N] += 1u << (32 - lev * p->Bgbit);
+        }
+    }
+    for (size_t c = 0; c < ((size_t)1 << v); c++) {
+        uint32_t *old = cells + c * tr;
+        memcpy(r, new_cell, sizeof(uint32_t) * tr);
+        for (int j = 0; j < v; j++) {
+            const uint32_t *S = ((c >> j) & 1) ? addr + (size_t)j * gsw : gmc + (size_t)j * gsw;
+            orc_cmux(p, S, r, old, r);
+        }
+        memcpy(old, r, sizeof(uint32_t) * tr);
+    }
+    free(gmc);
+    free(r);
+}
