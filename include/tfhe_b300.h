@@ -1,0 +1,236 @@
+/*
+ * tfhe_b300.h -- C ABI of a B300 (sm_103a) library for TFHE gate bootstrapping and
+ * CMUX-tree memory, following "Virtual Secure Platform: A Five-Stage Pipeline
+ * Processor over TFHE" (Matsuoka et al.).
+ *
+ * Scope: the server-side hot path of the paper's encrypted processor -- every
+ * two-input Homomorphic Gate of a circuit level (Section 2.1.2 "Homomorphic
+ * Gates", "Bootstrapping in TFHE") and the CMUX Memory read and write units
+ * (Section 8.2).  Key generation and encryption are client-side and not part of
+ * this library.
+ *
+ * Data conventions (all values Torus32 = uint32, arithmetic mod 2^32):
+ *   TLWE lvl0   u32[n + 1]         a[0..n-1], b                    (Section 2.1.2 "TLWE")
+ *   TLWE lvl1   u32[N + 1]         a[0..N-1], b
+ *   TRLWE       u32[2][N]          a[X], b[X]                      (Section 2.1.2 "TRLWE")
+ *   TRGSW       u32[2l][2][N]      row j < l carries m/Bg^{j+1} on a, row l+j on b
+ *                                                                  (Section 2.1.2 "TRGSW")
+ *   BSK         u32[n][2l][2][N]   BSK[i] = TRGSW(s0[i]) under the lvl1 key
+ *   KSK         u32[N][t][2^basebit][n + 1]
+ *                                  KSK[i][j][v] = TLWE_lvl0(v s1[i] / 2^{(j+1) basebit});
+ *                                  entries with v = 0 are never read (a zero digit
+ *                                  contributes nothing).
+ *
+ * Memory: every ciphertext pointer is a DEVICE pointer owned by the caller unless a
+ * function says otherwise.  The context owns only its own re-laid-out key copies
+ * and workspaces.  Calls are asynchronous on the given stream (a cudaStream_t
+ * passed as void*, NULL for the legacy default stream) and return after
+ * enqueueing.
+ *
+ * Errors: functions return TFHE_OK (0) or a negative TFHE_E* code.  Arguments are
+ * validated on the host before anything is enqueued; on error nothing is
+ * enqueued and tfhe_last_error() describes the cause.  No call aborts the process.
+ * Device-side checks (gate types and input indices that live in device memory)
+ * record a code in a device error word that tfhe_ctx_sync() reports.
+ */
+#ifndef TFHE_B300_H
+#define TFHE_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tfhe_params {
+    int32_t n;          /* lvl0 TLWE dimension, 1..4096 */
+    int32_t N;          /* lvl1 ring degree: power of two, 256..2048 */
+    int32_t l;          /* gadget levels, 1..4 */
+    int32_t Bgbit;      /* log2 of the gadget base, l * Bgbit <= 31 */
+    int32_t ks_t;       /* key-switching levels */
+    int32_t ks_basebit; /* log2 of the key-switching base, t * basebit <= 31 */
+} tfhe_params;
+
+typedef struct tfhe_ctx tfhe_ctx;
+typedef struct tfhe_plan tfhe_plan;
+
+enum {
+    TFHE_OK = 0,
+    TFHE_EINVAL = -1,       /* bad argument (null pointer, size, type, index range) */
+    TFHE_ENOMEM = -2,       /* device allocation failed */
+    TFHE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    TFHE_ETIMEOUT = -4,     /* a device-side wait gave up (bounded spin) */
+    TFHE_EUNSUPPORTED = -5, /* parameters or form not supported by this build */
+    TFHE_ENOKEYS = -6       /* tfhe_ctx_set_keys has not been called */
+};
+
+/* Two-input gate types (uint8 in gate-type arrays).  NY negates the first input,
+ * YN the second: ANDNY = (not a) and b, ORYN = a or (not b). */
+enum {
+    TFHE_NAND = 0, TFHE_AND = 1, TFHE_OR = 2, TFHE_NOR = 3, TFHE_XOR = 4,
+    TFHE_XNOR = 5, TFHE_ANDNY = 6, TFHE_ANDYN = 7, TFHE_ORNY = 8, TFHE_ORYN = 9
+};
+
+/* How the external products of BlindRotate are computed.  Both give bit-identical
+ * ciphertexts.
+ *   TFHE_FORM_NTT: one thread block per gate (or CMUX); each external product is an
+ *     exact negacyclic NTT over the prime 2^64 - 2^32 + 1 (the GPU library form of
+ *     Section 6.2(a)).
+ *   TFHE_FORM_TC: the gates of a batch share each BSK_i, so one BlindRotate step
+ *     over B gates is a dense [B x 2lN] x [2lN x 2N] contraction of signed digits
+ *     by negacyclic Toeplitz blocks of the key, run on the tcgen05 tensor cores
+ *     with the key split into byte planes (exact in bf16, fp32 accumulation kept
+ *     below 2^24, recombined mod 2^32).  Needs N = 1024 and 2l * Bgbit fitting the
+ *     exactness budget; otherwise the call returns TFHE_EUNSUPPORTED. */
+enum { TFHE_FORM_NTT = 0, TFHE_FORM_TC = 1 };
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int tfhe_version(void);
+
+/* Create a context for `params` on CUDA device `device`; *out receives it.
+ * TFHE_EUNSUPPORTED for parameters outside the documented ranges. */
+int tfhe_ctx_create(const tfhe_params *params, int device, tfhe_ctx **out);
+
+/* Release every device buffer the context owns.  NULL is ignored. */
+void tfhe_ctx_destroy(tfhe_ctx *ctx);
+
+/* Text of the last error recorded on this context (never NULL; "" if none).
+ * Valid until the next call on the context. */
+const char *tfhe_last_error(const tfhe_ctx *ctx);
+
+/* Load the bootstrapping and key-switching keys (device pointers, layouts above).
+ * The context copies and re-lays them out on `stream` (NTT-domain BSK for the NTT
+ * form, raw BSK for the TC form, KSK rows without the v = 0 entries and padded to
+ * 16-byte multiples); the caller keeps ownership of its buffers and may free them
+ * once the stream has passed this call. */
+int tfhe_ctx_set_keys(tfhe_ctx *ctx, const uint32_t *bsk, const uint32_t *ksk, void *stream);
+
+/* Pre-size the context's workspaces for batches of up to `max_gates` gates (or
+ * CMUXes), so that later calls do not allocate (required before capturing calls
+ * in a CUDA graph).  Calls with larger batches grow the workspaces themselves. */
+int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates);
+
+/* Wait for `stream` and report device-side errors recorded by this context's
+ * kernels (TFHE_EINVAL, TFHE_ETIMEOUT) or CUDA errors (TFHE_ECUDA); clears the
+ * device error word. */
+int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
+
+/* Per-kernel timing (tracing).  When enabled, the context brackets each of its kernel
+ * launches with CUDA events on the launching stream (not while the stream is being
+ * captured into a graph).  tfhe_ctx_stage_times waits for the recorded events, writes
+ * the summed device time in milliseconds and the launch count of each stage into
+ * ms[TFHE_NUM_STAGES] and launches[TFHE_NUM_STAGES] (either may be NULL), and resets
+ * the counters. */
+enum {
+    TFHE_STAGE_COMBINE = 0,        /* gate linear combination + ModSwitch */
+    TFHE_STAGE_BLIND_ROTATE_NTT = 1, /* whole BlindRotate, NTT form (one launch) */
+    TFHE_STAGE_DECOMPOSE_TC = 2,   /* rotation + gadget digits, TC form (per step) */
+    TFHE_STAGE_EXTPROD_TC = 3,     /* tensor-core external product, TC form (per step) */
+    TFHE_STAGE_KEYSWITCH = 4,      /* SampleExtract + identity key switch */
+    TFHE_STAGE_CMUX = 5,           /* CMUX batches, tree levels, RAM write */
+    TFHE_NUM_STAGES = 8
+};
+int tfhe_ctx_enable_timing(tfhe_ctx *ctx, int on);
+int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches);
+
+/* Bootstrapped two-input gates (Section 2.1.2 "Homomorphic Gates"; a circuit level
+ * of independent gates, Section 6.2(d)):
+ *   out[g] = HomGate(types[g], in[in_idx[2g]], in[in_idx[2g+1]])   for g < G
+ * in:      device u32[num_in][n+1] lvl0 TLWE
+ * types:   device u8[G], each < 10
+ * in_idx:  device i32[G][2], each in [0, num_in).  Both are checked on the device:
+ *          a bad type or index gives that gate an all-zero output and records
+ *          TFHE_EINVAL in the device error word (see tfhe_ctx_sync)
+ * out:     device u32[G][n+1]; must not overlap rows of `in` read by this call
+ * form:    TFHE_FORM_NTT or TFHE_FORM_TC
+ * Each gate: linear combination, ModSwitch to Z_2N, BlindRotate of the test vector
+ * (n CMUXes against BSK), SampleExtract, identity key switch. */
+int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
+                    const int32_t *in_idx, uint32_t *out, int G, int form, void *stream);
+
+/* tfhe_gate_batch with HOST buffers (pinned or pageable): copies the inputs in,
+ * evaluates, copies the outputs back, and returns once `out` holds the result.
+ * Uses context-owned device staging buffers. */
+int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                         const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
+                         int form, void *stream);
+
+/* The stages of tfhe_gate_batch, exposed for testing and for callers that build
+ * their own schedules.
+ *   tfhe_blind_rotate: bar device u32[G][n+1] with values in [0, 2N) (ModSwitched
+ *     a~_0..a~_{n-1}, b~); acc device u32[G][2][N] receives the accumulator
+ *     encrypting X^{-b~ + sum a~_i s_i} v, v the test vector with every coefficient
+ *     1/8 (Section 2.1.2 "Bootstrapping in TFHE", "CMUX").
+ *   tfhe_extract_keyswitch: acc device u32[G][2][N] -> out device u32[G][n+1]:
+ *     SampleExtract of coefficient 0 and identity key switch (Section 2.1.2
+ *     "Sample Extraction and Identity Key Switching"). */
+int tfhe_blind_rotate(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
+                      void *stream);
+int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
+                           void *stream);
+
+/* Batched CMUX (Section 2.1.2 "CMUX"): out[k] = d0[k] + C_k (.) (d1[k] - d0[k]) with
+ * C_k = trgsw + (k / group) * (2l * 2 * N) -- consecutive runs of `group` CMUXes
+ * share one TRGSW selector.  d1, d0, out: device u32[B][2][N]; out may alias d0 or
+ * d1 (same k only).  trgsw: device u32[ceil(B / group)][2l][2][N]. */
+int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint32_t *d1,
+                    const uint32_t *d0, uint32_t *out, int B, int form, void *stream);
+
+/* CMUX-tree read unit (Section 8.2 "Read Unit"): R independent reads of a table of
+ * 2^v TRLWE rows.  Address bit j (least significant first) selects at tree level j:
+ *   node_j[k] = CMUX(C_{r,j}, node_{j-1}[2k+1], node_{j-1}[2k]),  node_{-1} = table.
+ * addr_trgsw: device u32[R][v][2l][2][N]; table: device u32[2^v][2][N];
+ * out: device u32[R][2][N].  1 <= v <= 16. */
+int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *table, int v,
+                        uint32_t *out, int R, int form, void *stream);
+
+/* RAM write unit, CMUX part (Section 8.2 "Write Unit" and its Remark): for every
+ * cell c of the 2^v cells, r <- new_cell; for j = 0..v-1: r <- CMUX(S_j, r, cell_c)
+ * with S_j = C_j if bit j of c is 1 else G - C_j (G the gadget TRGSW of 1); then
+ * cell_c <- r.  addr_trgsw: device u32[v][2l][2][N]; new_cell: device u32[2][N];
+ * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16. */
+int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, const uint32_t *new_cell,
+                   uint32_t *cells, int form, void *stream);
+
+/* ---- Level scheduler (Section 6.2(d): circuit -> DAG -> levels of independent gates) */
+
+/* One circuit, HOST arrays.  Wire w < num_inputs is primary input w; wire
+ * num_inputs + g is the output of gate g.  Gates must be listed in topological
+ * order: both inputs of gate g are wires < num_inputs + g. */
+typedef struct tfhe_circuit {
+    int32_t num_inputs;
+    int32_t num_gates;
+    const uint8_t *types;   /* host u8[num_gates] */
+    const int32_t *in_idx;  /* host i32[num_gates][2] */
+} tfhe_circuit;
+
+/* Build a schedule for `num_circuits` independent circuits evaluated together:
+ * gates are grouped by level (longest path from the primary inputs) and level k of
+ * every circuit runs in one batch.  `form` as for tfhe_gate_batch, or -1 to let
+ * the plan's autotuner pick a form per level width.  The plan owns its device
+ * copies of the wiring; the context must outlive the plan. */
+int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, int num_circuits, int form,
+                      tfhe_plan **out);
+
+/* Number of levels of the plan, and for circuit c the (0-based) level after which
+ * all of its gates are done (for per-circuit completion times). */
+int tfhe_plan_num_levels(const tfhe_plan *plan);
+int tfhe_plan_circuit_last_level(const tfhe_plan *plan, int c);
+
+/* Evaluate the plan.  primary_in: device u32[sum of num_inputs][n+1], circuits in
+ * order; gate_out: device u32[sum of num_gates][n+1], circuits in order, gates in
+ * each circuit's original order.  With use_graph != 0 the level schedule is
+ * captured once into a CUDA graph and replayed on later runs with the same
+ * pointers and stream.  level_events (optional, may be NULL): array of
+ * tfhe_plan_num_levels() cudaEvent_t (as void*), recorded after each level when
+ * use_graph == 0. */
+int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out, int use_graph,
+                  void **level_events, void *stream);
+
+void tfhe_plan_destroy(tfhe_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFHE_B300_H */

@@ -1,0 +1,247 @@
+"""Python binding of the B300 TFHE gate-bootstrapping library (libtfhe_b300.so).
+
+Argument marshalling only: every step of the evaluated path runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (uint32 for ciphertexts, uint8
+gate types, int32 indices); the stream is torch's current CUDA stream unless given.
+
+The raw C entry points are available under their C names (``tfhe_gate_batch`` ...)
+on ``lib()``; ``Context`` wraps them.  There is no CPU fallback: if the shared
+library is missing or cannot be loaded, importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtfhe_b300.so")
+
+TFHE_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPORTED",
+          -6: "ENOKEYS"}
+FORM_NTT = 0
+FORM_TC = 1
+FORM_AUTO = -1
+GATES = ["NAND", "AND", "OR", "NOR", "XOR", "XNOR", "ANDNY", "ANDYN", "ORNY", "ORYN"]
+
+# every symbol the public header declares
+EXPORTS = [
+    "tfhe_version", "tfhe_ctx_create", "tfhe_ctx_destroy", "tfhe_last_error",
+    "tfhe_ctx_set_keys", "tfhe_ctx_reserve", "tfhe_ctx_sync", "tfhe_gate_batch",
+    "tfhe_gate_batch_host", "tfhe_blind_rotate", "tfhe_extract_keyswitch", "tfhe_cmux_batch",
+    "tfhe_cmux_tree_read", "tfhe_ram_write", "tfhe_circuit_plan", "tfhe_plan_num_levels",
+    "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_destroy",
+    "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times",
+]
+STAGES = ["combine", "blind_rotate_ntt", "decompose_tc", "extprod_tc", "keyswitch", "cmux"]
+NUM_STAGES = 8
+
+
+class TfheError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("N", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("Bgbit", ctypes.c_int32), ("ks_t", ctypes.c_int32),
+                ("ks_basebit", ctypes.c_int32)]
+
+
+class CCircuit(ctypes.Structure):
+    _fields_ = [("num_inputs", ctypes.c_int32), ("num_gates", ctypes.c_int32),
+                ("types", ctypes.c_void_p), ("in_idx", ctypes.c_void_p)]
+
+
+@functools.lru_cache(maxsize=1)
+def lib():
+    """Load the in-tree shared library (raises if it has not been built)."""
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2010_09410_b300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "tfhe_version": (i32, []),
+        "tfhe_ctx_create": (i32, [ctypes.POINTER(CParams), i32, ctypes.POINTER(vp)]),
+        "tfhe_ctx_destroy": (None, [vp]),
+        "tfhe_last_error": (ctypes.c_char_p, [vp]),
+        "tfhe_ctx_set_keys": (i32, [vp, vp, vp, vp]),
+        "tfhe_ctx_reserve": (i32, [vp, i32]),
+        "tfhe_ctx_sync": (i32, [vp, vp]),
+        "tfhe_gate_batch": (i32, [vp, vp, i64, vp, vp, vp, i32, i32, vp]),
+        "tfhe_gate_batch_host": (i32, [vp, vp, i64, vp, vp, vp, i32, i32, vp]),
+        "tfhe_blind_rotate": (i32, [vp, vp, vp, i32, i32, vp]),
+        "tfhe_extract_keyswitch": (i32, [vp, vp, vp, i32, vp]),
+        "tfhe_cmux_batch": (i32, [vp, vp, i32, vp, vp, vp, i32, i32, vp]),
+        "tfhe_cmux_tree_read": (i32, [vp, vp, vp, i32, vp, i32, i32, vp]),
+        "tfhe_ram_write": (i32, [vp, vp, i32, vp, vp, i32, vp]),
+        "tfhe_circuit_plan": (i32, [vp, ctypes.POINTER(CCircuit), i32, i32, ctypes.POINTER(vp)]),
+        "tfhe_plan_num_levels": (i32, [vp]),
+        "tfhe_plan_circuit_last_level": (i32, [vp, i32]),
+        "tfhe_plan_run": (i32, [vp, vp, vp, i32, vp, vp]),
+        "tfhe_plan_destroy": (None, [vp]),
+        "tfhe_ctx_enable_timing": (i32, [vp, i32]),
+        "tfhe_ctx_stage_times": (i32, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor or numpy array, None passes NULL."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device: parameters, keys and workspaces."""
+
+    def __init__(self, params, device: int = 0):
+        p = params.abi() if hasattr(params, "abi") else tuple(params)
+        self.params = params
+        self.n, self.N, self.l = p[0], p[1], p[2]
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = lib().tfhe_ctx_create(ctypes.byref(CParams(*p)), device, ctypes.byref(h))
+        if rc != TFHE_OK:
+            raise TfheError(rc, "tfhe_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tfhe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != TFHE_OK:
+            raise TfheError(rc, f"{what}: {lib().tfhe_last_error(self.h).decode()}")
+
+    def set_keys(self, bsk, ksk, stream=None):
+        self._check(lib().tfhe_ctx_set_keys(self.h, _ptr(bsk), _ptr(ksk), _stream(stream)),
+                    "set_keys")
+
+    def enable_timing(self, on: bool = True):
+        self._check(lib().tfhe_ctx_enable_timing(self.h, 1 if on else 0), "enable_timing")
+
+    def stage_times(self):
+        """{stage: (total ms, launches)} since the last call; waits for the events."""
+        ms = (ctypes.c_double * NUM_STAGES)()
+        n = (ctypes.c_int64 * NUM_STAGES)()
+        self._check(lib().tfhe_ctx_stage_times(self.h, ms, n), "stage_times")
+        return {name: (ms[i], n[i]) for i, name in enumerate(STAGES)}
+
+    def reserve(self, max_gates: int):
+        self._check(lib().tfhe_ctx_reserve(self.h, max_gates), "reserve")
+
+    def sync(self, stream=None):
+        self._check(lib().tfhe_ctx_sync(self.h, _stream(stream)), "sync")
+
+    def gate_batch(self, inp, types, idx, out, form=FORM_NTT, stream=None):
+        G = types.numel()
+        self._check(lib().tfhe_gate_batch(self.h, _ptr(inp), inp.shape[0], _ptr(types),
+                                          _ptr(idx), _ptr(out), G, form, _stream(stream)),
+                    "gate_batch")
+        return out
+
+    def gate_batch_host(self, inp, types, idx, out, form=FORM_NTT, stream=None):
+        """Host (numpy or CPU torch) buffers in and out; returns when `out` is filled."""
+        G = types.size if hasattr(types, "size") and not callable(types.size) else types.numel()
+        self._check(lib().tfhe_gate_batch_host(self.h, _ptr(inp), inp.shape[0], _ptr(types),
+                                               _ptr(idx), _ptr(out), G, form, _stream(stream)),
+                    "gate_batch_host")
+        return out
+
+    def blind_rotate(self, bar, acc, form=FORM_NTT, stream=None):
+        self._check(lib().tfhe_blind_rotate(self.h, _ptr(bar), _ptr(acc), bar.shape[0], form,
+                                            _stream(stream)), "blind_rotate")
+        return acc
+
+    def extract_keyswitch(self, acc, out, stream=None):
+        self._check(lib().tfhe_extract_keyswitch(self.h, _ptr(acc), _ptr(out), acc.shape[0],
+                                                 _stream(stream)), "extract_keyswitch")
+        return out
+
+    def cmux_batch(self, trgsw, group, d1, d0, out, form=FORM_NTT, stream=None):
+        self._check(lib().tfhe_cmux_batch(self.h, _ptr(trgsw), group, _ptr(d1), _ptr(d0),
+                                          _ptr(out), d1.shape[0], form, _stream(stream)),
+                    "cmux_batch")
+        return out
+
+    def cmux_tree_read(self, addr_trgsw, table, v, out, form=FORM_NTT, stream=None):
+        self._check(lib().tfhe_cmux_tree_read(self.h, _ptr(addr_trgsw), _ptr(table), v, _ptr(out),
+                                              out.shape[0], form, _stream(stream)),
+                    "cmux_tree_read")
+        return out
+
+    def ram_write(self, addr_trgsw, v, new_cell, cells, form=FORM_NTT, stream=None):
+        self._check(lib().tfhe_ram_write(self.h, _ptr(addr_trgsw), v, _ptr(new_cell), _ptr(cells),
+                                         form, _stream(stream)), "ram_write")
+        return cells
+
+    def plan(self, circuits, form=FORM_AUTO):
+        return Plan(self, circuits, form)
+
+
+class Plan:
+    """A level schedule for one or more circuits (host numpy wiring)."""
+
+    def __init__(self, ctx: Context, circuits, form=FORM_AUTO):
+        import numpy as np
+        self.ctx = ctx
+        self._keep = []
+        arr = (CCircuit * len(circuits))()
+        for i, c in enumerate(circuits):
+            t = np.ascontiguousarray(c.types, np.uint8)
+            x = np.ascontiguousarray(c.idx, np.int32)
+            self._keep += [t, x]
+            arr[i] = CCircuit(c.num_inputs, t.size, t.ctypes.data, x.ctypes.data)
+        h = ctypes.c_void_p()
+        ctx._check(lib().tfhe_circuit_plan(ctx.h, arr, len(circuits), form, ctypes.byref(h)),
+                   "circuit_plan")
+        self.h = h
+        self.num_levels = lib().tfhe_plan_num_levels(h)
+        self.circuit_last_level = [lib().tfhe_plan_circuit_last_level(h, i)
+                                   for i in range(len(circuits))]
+
+    def run(self, primary_in, gate_out, use_graph=False, level_events=None, stream=None):
+        ev = None
+        if level_events is not None:
+            ev = (ctypes.c_void_p * len(level_events))(*[e.cuda_event for e in level_events])
+        self.ctx._check(lib().tfhe_plan_run(self.h, _ptr(primary_in), _ptr(gate_out),
+                                            1 if use_graph else 0, ev, _stream(stream)),
+                        "plan_run")
+        return gate_out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tfhe_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,119 @@
+// cmux.cu -- CMUX Memory (Section 8.2): the read unit's CMUX tree and the CMUX part
+// of the write unit's write bars.
+#include "common.cuh"
+
+// G - C_j for j < v (Remark, Section 8.2): the selector that encrypts 1 - a_j.
+// G is the gadget TRGSW of 1: 2^{32 - (r+1) Bgbit} at coefficient 0 of the a column of
+// row r < l and of the b column of row l + r, zero elsewhere.
+__global__ void k_gadget_minus(const uint32_t *__restrict__ c, uint32_t *__restrict__ gmc,
+                               int v, int l, int N, int Bgbit) {
+    const size_t per = (size_t)2 * l * 2 * N;
+    const size_t total = (size_t)v * per;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = e % per;
+        const int row = (int)(w / (2 * (size_t)N));
+        const int col = (int)((w / N) % 2);
+        const int k = (int)(w % N);
+        uint32_t g = 0;
+        if (k == 0) {
+            const int lev = (row < l ? row : row - l) + 1;
+            if ((row < l && col == 0) || (row >= l && col == 1)) g = 1u << (32 - lev * Bgbit);
+        }
+        gmc[e] = g - c[e];
+    }
+}
+
+static int check_common(tfhe_ctx *ctx, int v, int form) {
+    if (v < 1 || v > 16) return tfhe_set_error(ctx, TFHE_EINVAL, "v must be in 1..16");
+    if (form != TFHE_FORM_NTT && form != TFHE_FORM_TC)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "unknown form");
+    if (form == TFHE_FORM_TC && !tfhe_tc_supported(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form not supported here");
+    return TFHE_OK;
+}
+
+extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
+                                   const uint32_t *table, int v, uint32_t *out, int R, int form,
+                                   void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    int rc = check_common(ctx, v, form);
+    if (rc != TFHE_OK) return rc;
+    if (R < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "cmux_tree_read: R < 0");
+    if (R == 0) return TFHE_OK;
+    if (!addr_trgsw || !table || !out)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "cmux_tree_read: null pointer");
+    if ((int64_t)R << (v - 1) > (int64_t)1 << 30)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "cmux_tree_read: R * 2^(v-1) too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const tfhe_params &p = ctx->p;
+    const int64_t N2 = 2 * (int64_t)p.N;
+    const size_t per = (size_t)2 * p.l * 2 * p.N;
+    const int M0 = 1 << (v - 1);
+    rc = tfhe_ensure_workspace(ctx, R * M0);
+    if (rc != TFHE_OK) return rc;
+    const uint64_t *sel_ntt = nullptr;
+    if (form == TFHE_FORM_NTT) {
+        rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
+        if (rc != TFHE_OK) return rc;
+        rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
+        if (rc != TFHE_OK) return rc;
+        sel_ntt = ctx->ws_trgsw_ntt;
+    }
+    uint32_t *buf[2] = {ctx->ws_acc, ctx->ws_tmp};
+    const uint32_t *in = table;
+    int64_t in_ystride = 0;  // level 0 reads the shared table
+    for (int j = 0; j < v; j++) {
+        const int M = 1 << (v - 1 - j);
+        uint32_t *o = (j == v - 1) ? out : buf[j & 1];
+        CmuxGeom g{in + N2, in, o, 2 * N2, in_ystride, N2, (int64_t)M * N2, (int64_t)v,
+                   M, R, (int64_t)R * M};
+        if (form == TFHE_FORM_NTT)
+            rc = tfhe_cmux_ntt(ctx, sel_ntt + (size_t)j * per, g, st);
+        else
+            rc = tfhe_cmux_tc(ctx, addr_trgsw + (size_t)j * per, g, st);
+        if (rc != TFHE_OK) return rc;
+        in = o;
+        in_ystride = (int64_t)M * N2;
+    }
+    return TFHE_OK;
+}
+
+int tfhe_ram_write_tc(tfhe_ctx *ctx, const uint32_t *c, const uint32_t *gmc, int v,
+                      const uint32_t *new_cell, uint32_t *cells, cudaStream_t st);
+
+extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
+                              const uint32_t *new_cell, uint32_t *cells, int form,
+                              void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    int rc = check_common(ctx, v, form);
+    if (rc != TFHE_OK) return rc;
+    if (!addr_trgsw || !new_cell || !cells)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "ram_write: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const tfhe_params &p = ctx->p;
+    const size_t per = (size_t)2 * p.l * 2 * p.N;
+    if (ctx->ws_gmc_cap < v) {
+        if (ctx->ws_gmc) cudaFree(ctx->ws_gmc);
+        ctx->ws_gmc = nullptr;
+        ctx->ws_gmc_cap = 0;
+        if (cudaMalloc(&ctx->ws_gmc, (size_t)v * per * 4) != cudaSuccess)
+            return tfhe_set_error(ctx, TFHE_ENOMEM, "ram_write: selector workspace");
+        ctx->ws_gmc_cap = v;
+    }
+    k_gadget_minus<<<256, 256, 0, st>>>(addr_trgsw, ctx->ws_gmc, v, p.l, p.N, p.Bgbit);
+    rc = tfhe_check_launch(ctx, "gadget_minus");
+    if (rc != TFHE_OK) return rc;
+    if (form == TFHE_FORM_TC) return tfhe_ram_write_tc(ctx, addr_trgsw, ctx->ws_gmc, v, new_cell,
+                                                       cells, st);
+    rc = tfhe_ensure_trgsw_ws(ctx, (size_t)2 * v);
+    if (rc != TFHE_OK) return rc;
+    rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
+    if (rc != TFHE_OK) return rc;
+    rc = tfhe_trgsw_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
+    if (rc != TFHE_OK) return rc;
+    return tfhe_ram_write_ntt(ctx, ctx->ws_trgsw_ntt, ctx->ws_trgsw_ntt + (size_t)v * per, v,
+                              new_cell, cells, st);
+}

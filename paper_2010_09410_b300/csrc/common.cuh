@@ -1,0 +1,189 @@
+// common.cuh -- internal definitions shared by the library's translation units:
+// the context, error helpers, Torus32 polynomial helpers and arithmetic modulo the
+// prime P = 2^64 - 2^32 + 1 used by the NTT form.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tfhe_b300.h"
+
+#define TFHE_VERSION 10000
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+struct TcWorkspace;  // tensor-core form buffers (tc.cu)
+
+struct tfhe_ctx {
+    tfhe_params p{};
+    int device = 0;
+    int logN = 0;
+    int n_pad = 0;  // KSK row length in words, (n + 1) rounded up to a multiple of 4
+    std::string err;
+
+    // keys
+    bool has_keys = false;
+    uint64_t *bsk_ntt = nullptr;  // [n][2l][2][N] NTT domain (bit-reversed), scaled by N^-1
+    uint32_t *bsk_raw = nullptr;  // [n][2l][2][N] as given
+    uint32_t *ksk = nullptr;      // [N][t][base - 1][n_pad], rows v = 1..base-1
+
+    // NTT twiddles: psi^{brv(k)} and psi^{-brv(k)}, psi a primitive 2N-th root of unity
+    uint64_t *psi_fwd = nullptr;
+    uint64_t *psi_inv = nullptr;
+    uint64_t n_inv = 0;
+
+    // per-batch workspaces (grown on demand)
+    int ws_cap = 0;              // capacity in gates / CMUXes
+    uint32_t *ws_bar = nullptr;  // [cap][n+1] ModSwitched combination
+    uint32_t *ws_acc = nullptr;  // [cap][2][N] accumulators
+    uint32_t *ws_tmp = nullptr;  // [cap][2][N] scratch TRLWE (CMUX tree / RAM)
+    uint64_t *ws_trgsw_ntt = nullptr;  // NTT-domain TRGSW selectors (CMUX batches)
+    size_t ws_trgsw_cap = 0;           // in TRGSWs
+    uint32_t *ws_gmc = nullptr;        // G - C_j selectors for the RAM write
+    int ws_gmc_cap = 0;                // in TRGSWs
+
+    // host-API staging (device side)
+    size_t st_in_cap = 0, st_gate_cap = 0;
+    uint32_t *st_in = nullptr, *st_out = nullptr;
+    uint8_t *st_types = nullptr;
+    int32_t *st_idx = nullptr;
+
+    TcWorkspace *tc = nullptr;
+    int tc_min_width = 128;  // plan autotuner: narrowest level run in the tensor-core form
+
+    int *d_err = nullptr;  // device error word (0 = ok, else a TFHE_E* code)
+
+    // per-kernel timing (tfhe_ctx_enable_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[TFHE_NUM_STAGES];
+};
+
+// Brackets one kernel launch with events when timing is on and the stream is not
+// being captured.  Usage: StageTimer t(ctx, stage, st); launch; t.stop();
+struct StageTimer {
+    tfhe_ctx *ctx;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(tfhe_ctx *c, int s, cudaStream_t stream);
+    void stop();
+};
+
+// Addressing of a 2-D grid of CMUXes (x within a group sharing one selector, y the
+// group): CMUX (x, y) reads d1 + x*dx + y*dy and d0 + x*dx + y*dy, writes
+// out + x*ox + y*oy (word offsets) and uses selector sel + y*sy (in TRGSWs).  Only
+// CMUXes with y*nx + x < count exist.
+struct CmuxGeom {
+    const uint32_t *d1, *d0;
+    uint32_t *out;
+    int64_t dx, dy, ox, oy, sy;
+    int nx, ny;
+    int64_t count;
+};
+
+// error recording helpers (ctx.cu)
+int tfhe_set_error(tfhe_ctx *ctx, int code, const std::string &msg);
+int tfhe_check_launch(tfhe_ctx *ctx, const char *what);
+int tfhe_ensure_workspace(tfhe_ctx *ctx, int gates);
+int tfhe_ensure_trgsw_ws(tfhe_ctx *ctx, size_t count);
+
+// ntt.cu
+int tfhe_ntt_setup(tfhe_ctx *ctx);
+int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
+                      cudaStream_t st);
+int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                          cudaStream_t st);
+int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st);
+int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
+                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st);
+
+// tc.cu
+int tfhe_tc_supported(const tfhe_ctx *ctx);
+int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                         cudaStream_t st);
+int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);
+void tfhe_tc_free(tfhe_ctx *ctx);
+
+#define TFHE_CUDA_TRY(ctx, call)                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return tfhe_set_error((ctx), TFHE_ECUDA,                                    \
+                                  std::string(#call ": ") + cudaGetErrorString(e_));    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Coefficient j of X^k * p (k in [0, 2N)) for a Torus32 polynomial p of degree < N:
+// X^k p has p_{j-k} at X^j for j >= k and -p_{j-k+N} below; X^k = -X^{k-N} for k >= N.
+__device__ __forceinline__ uint32_t rot_coef(const uint32_t *p, int N, int k, int j) {
+    int neg = 0;
+    if (k >= N) { k -= N; neg = 1; }
+    uint32_t v;
+    if (j >= k) v = p[j - k];
+    else v = 0u - p[j - k + N];
+    return neg ? 0u - v : v;
+}
+
+// Signed gadget digits of t (l levels of Bgbit bits, rounding to nearest, digits in
+// [-Bg/2, Bg/2)): adding Bg/2 at every level and half a unit of the last level turns
+// the signed rounding into plain bit extraction of u = t + offset.
+__device__ __forceinline__ uint32_t gadget_offset(int l, int Bgbit) {
+    uint32_t off = 1u << (32 - l * Bgbit - 1);
+    for (int j = 1; j <= l; j++) off += (1u << (Bgbit - 1)) << (32 - j * Bgbit);
+    return off;
+}
+
+__device__ __forceinline__ int32_t gadget_digit(uint32_t u, int j /*1-based*/, int Bgbit) {
+    return (int32_t)((u >> (32 - j * Bgbit)) & ((1u << Bgbit) - 1)) - (1 << (Bgbit - 1));
+}
+
+// ---- arithmetic modulo P = 2^64 - 2^32 + 1 (2^64 = 2^32 - 1 mod P) ----------------
+
+static constexpr uint64_t GL_P = 0xFFFFFFFF00000001ull;
+static constexpr uint64_t GL_EPS = 0xFFFFFFFFull;  // 2^64 mod P
+
+__device__ __forceinline__ uint64_t gl_add(uint64_t a, uint64_t b) {
+    uint64_t s = a + b;
+    if (s < a) s += GL_EPS;  // wrapped past 2^64: add 2^64 mod P
+    if (s >= GL_P) s -= GL_P;
+    return s;
+}
+
+__device__ __forceinline__ uint64_t gl_sub(uint64_t a, uint64_t b) {
+    uint64_t d = a - b;
+    if (a < b) d -= GL_EPS;  // borrowed 2^64: subtract 2^64 mod P
+    return d;
+}
+
+__device__ __forceinline__ uint64_t gl_mul(uint64_t a, uint64_t b) {
+    const uint64_t lo = a * b;
+    const uint64_t hi = __umul64hi(a, b);
+    const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+    // a*b = lo + h0 2^64 + h1 2^96 = lo + h0 (2^32 - 1) - h1  (mod P)
+    uint64_t t = lo - h1;
+    if (lo < h1) t -= GL_EPS;
+    const uint64_t m = (uint64_t)h0 * GL_EPS;
+    uint64_t r = t + m;
+    if (r < t) r += GL_EPS;
+    if (r >= GL_P) r -= GL_P;
+    return r;
+}
+
+// signed digit -> residue
+__device__ __forceinline__ uint64_t gl_from_i32(int32_t d) {
+    return d >= 0 ? (uint64_t)d : GL_P - (uint64_t)(-(int64_t)d);
+}
+
+// residue of an integer V with |V| < P/2 -> V mod 2^32 (P = 1 mod 2^32)
+__device__ __forceinline__ uint32_t gl_lift_u32(uint64_t v) {
+    return (uint32_t)v - (v > (GL_P >> 1) ? 1u : 0u);
+}

@@ -1,0 +1,288 @@
+// gate.cu -- the bootstrapped-gate path around BlindRotate: the gate's linear
+// combination with ModSwitch (first kernel), and SampleExtract with the identity key
+// switch (last kernel); plus the public gate, blind-rotate, CMUX-batch and host-buffer
+// entry points.
+#include "common.cuh"
+
+// Gate constants (Section 2.1.2 "Homomorphic Gates"): c = (0, kappa) + s1 c1 + s2 c2,
+// in Torus32 with 1/8 = 2^29 and 1/4 = 2^30; enum order NAND, AND, OR, NOR, XOR, XNOR,
+// ANDNY, ANDYN, ORNY, ORYN (NY negates the first input, YN the second).
+__constant__ uint32_t c_kappa[10] = {
+    1u << 29, 0u - (1u << 29), 1u << 29, 0u - (1u << 29), 1u << 30,
+    0u - (1u << 30), 0u - (1u << 29), 0u - (1u << 29), 1u << 29, 1u << 29};
+__constant__ int32_t c_s1[10] = {-1, 1, 1, -1, 2, -2, -1, 1, -1, 1};
+__constant__ int32_t c_s2[10] = {-1, 1, 1, -1, 2, -2, 1, -1, 1, -1};
+
+__device__ __forceinline__ bool gate_ok(const uint8_t *types, const int32_t *idx, int64_t num_in,
+                                        int64_t g) {
+    const int32_t a = idx[2 * g], b = idx[2 * g + 1];
+    return types[g] < 10 && a >= 0 && b >= 0 && a < num_in && b < num_in;
+}
+
+// One block per gate: bar[g][k] = ModSwitch(combination_k), k <= n.  ModSwitch rounds
+// x * 2N / 2^32 half up with 32-bit wrap (shift s = 32 - log2(2N)).
+__global__ void k_combine_modswitch(int n, int shift, const uint32_t *__restrict__ in,
+                                    int64_t num_in, const uint8_t *__restrict__ types,
+                                    const int32_t *__restrict__ idx, uint32_t *__restrict__ bar,
+                                    int *err) {
+    const int64_t g = blockIdx.x;
+    uint32_t *o = bar + g * (n + 1);
+    if (!gate_ok(types, idx, num_in, g)) {
+        if (threadIdx.x == 0) atomicCAS(err, 0, TFHE_EINVAL);
+        for (int k = threadIdx.x; k <= n; k += blockDim.x) o[k] = 0;
+        return;
+    }
+    const int t = types[g];
+    const uint32_t *c1 = in + (int64_t)idx[2 * g] * (n + 1);
+    const uint32_t *c2 = in + (int64_t)idx[2 * g + 1] * (n + 1);
+    const uint32_t s1 = (uint32_t)c_s1[t], s2 = (uint32_t)c_s2[t];
+    const uint32_t half = 1u << (shift - 1);
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+        uint32_t x = s1 * c1[k] + s2 * c2[k];
+        if (k == n) x += c_kappa[t];
+        o[k] = (x + half) >> shift;
+    }
+}
+
+// SampleExtract + identity key switch for GT gates per block.  Thread c owns the
+// 16-byte column c of the lvl0 ciphertext (words 4c..4c+3 of the padded row).
+//   phase 1: unsigned key-switching digits of every extracted mask coefficient
+//            a'_0 = a_0, a'_i = -a_{N-i}, rounded to t digits of basebit bits;
+//   phase 2: res -= KSK[i][j][digit] over all (i, j) with a nonzero digit;
+//   phase 3: out = (0, b') - ... with b' = b_0.
+// Gates with a bad type or index (when types != nullptr) get an all-zero output.
+template <int GT>
+__global__ void __launch_bounds__(160) k_extract_keyswitch(
+    int n, int N, int t, int bb, int n_pad, const uint32_t *__restrict__ acc,
+    const uint4 *__restrict__ ksk, uint32_t *__restrict__ out, int G,
+    const uint8_t *__restrict__ types, const int32_t *__restrict__ idx, int64_t num_in) {
+    extern __shared__ uint8_t dig[];  // [N * t][GT]
+    const int g0 = blockIdx.x * GT;
+    const uint32_t prec = 1u << (32 - (1 + bb * t));
+    const uint32_t mask = (1u << bb) - 1;
+    for (int e = threadIdx.x; e < GT * N; e += blockDim.x) {
+        const int g = e / N, i = e % N;
+        uint32_t a = 0;
+        bool live = g0 + g < G;
+        if (live && types) live = gate_ok(types, idx, num_in, g0 + g);
+        if (live) {
+            const uint32_t *A = acc + (size_t)(g0 + g) * 2 * N;
+            a = (i == 0) ? A[0] : 0u - A[N - i];
+        }
+        const uint32_t ab = a + prec;
+        for (int j = 0; j < t; j++)
+            dig[((size_t)i * t + j) * GT + g] = live ? (uint8_t)((ab >> (32 - (j + 1) * bb)) & mask) : 0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    const int ncol = n_pad >> 2;
+    if (c >= ncol) return;
+    uint4 res[GT];
+#pragma unroll
+    for (int g = 0; g < GT; g++) res[g] = make_uint4(0, 0, 0, 0);
+    const int base1 = (1 << bb) - 1;
+    const int rows = N * t;
+    for (int ij = 0; ij < rows; ij++) {
+        uint8_t d[GT];
+        if (GT == 8) {
+            const uint64_t w = *(const uint64_t *)(dig + (size_t)ij * GT);
+#pragma unroll
+            for (int g = 0; g < GT; g++) d[g] = (uint8_t)(w >> (8 * g));
+        } else {
+#pragma unroll
+            for (int g = 0; g < GT; g++) d[g] = dig[(size_t)ij * GT + g];
+        }
+        const uint4 *rowbase = ksk + ((size_t)ij * base1) * ncol + c;
+#pragma unroll
+        for (int g = 0; g < GT; g++) {
+            if (d[g]) {
+                const uint4 k = __ldg(rowbase + (size_t)(d[g] - 1) * ncol);
+                res[g].x += k.x;
+                res[g].y += k.y;
+                res[g].z += k.z;
+                res[g].w += k.w;
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < GT; g++) {
+        const int gg = g0 + g;
+        if (gg >= G) break;
+        bool live = true;
+        if (types) live = gate_ok(types, idx, num_in, gg);
+        const uint32_t bprime = live ? acc[(size_t)gg * 2 * N + N] : 0u;
+        uint32_t *o = out + (size_t)gg * (n + 1);
+        const uint32_t v[4] = {res[g].x, res[g].y, res[g].z, res[g].w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int k = 4 * c + q;
+            if (k <= n) o[k] = live ? ((k == n ? bprime : 0u) - v[q]) : 0u;
+        }
+    }
+}
+
+static constexpr int KS_GT = 8;
+
+static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
+                                    const uint8_t *types, const int32_t *idx, int64_t num_in,
+                                    cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (G == 0) return TFHE_OK;
+    const size_t smem = (size_t)p.N * p.ks_t * KS_GT;
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_extract_keyswitch<KS_GT>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    if (ctx->n_pad / 4 > 160)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "key switch: n + 1 > 640");
+    const int blocks = (G + KS_GT - 1) / KS_GT;
+    StageTimer tm(ctx, TFHE_STAGE_KEYSWITCH, st);
+    k_extract_keyswitch<KS_GT><<<blocks, 160, smem, st>>>(
+        p.n, p.N, p.ks_t, p.ks_basebit, ctx->n_pad, acc, (const uint4 *)ctx->ksk, out, G, types,
+        idx, num_in);
+    tm.stop();
+    return tfhe_check_launch(ctx, "extract_keyswitch");
+}
+
+static int check_form(tfhe_ctx *ctx, int form) {
+    if (form == TFHE_FORM_NTT) return TFHE_OK;
+    if (form == TFHE_FORM_TC) {
+        if (!tfhe_tc_supported(ctx))
+            return tfhe_set_error(ctx, TFHE_EUNSUPPORTED,
+                                  "tensor-core form needs N = 1024, l * 2 <= 6, Bgbit <= 6");
+        return TFHE_OK;
+    }
+    return tfhe_set_error(ctx, TFHE_EINVAL, "unknown form");
+}
+
+static int blind_rotate_dispatch(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                                 int form, cudaStream_t st) {
+    if (form == TFHE_FORM_TC) return tfhe_blind_rotate_tc(ctx, bar, acc, G, st);
+    return tfhe_blind_rotate_ntt(ctx, bar, acc, G, st);
+}
+
+extern "C" int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                               const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
+                               int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (G < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch: G < 0");
+    if (G == 0) return TFHE_OK;
+    if (!in || !types || !in_idx || !out || num_in < 1)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch: null pointer or num_in < 1");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "gate_batch: keys not set");
+    int rc = check_form(ctx, form);
+    if (rc != TFHE_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = tfhe_ensure_workspace(ctx, G);
+    if (rc != TFHE_OK) return rc;
+    const tfhe_params &p = ctx->p;
+    const int shift = 32 - (ctx->logN + 1);
+    StageTimer tm(ctx, TFHE_STAGE_COMBINE, st);
+    k_combine_modswitch<<<G, 256, 0, st>>>(p.n, shift, in, num_in, types, in_idx, ctx->ws_bar,
+                                           ctx->d_err);
+    tm.stop();
+    rc = tfhe_check_launch(ctx, "combine_modswitch");
+    if (rc != TFHE_OK) return rc;
+    rc = blind_rotate_dispatch(ctx, ctx->ws_bar, ctx->ws_acc, G, form, st);
+    if (rc != TFHE_OK) return rc;
+    return launch_extract_keyswitch(ctx, ctx->ws_acc, out, G, types, in_idx, num_in, st);
+}
+
+extern "C" int tfhe_blind_rotate(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                                 int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (G < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "blind_rotate: G < 0");
+    if (G == 0) return TFHE_OK;
+    if (!bar || !acc) return tfhe_set_error(ctx, TFHE_EINVAL, "blind_rotate: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "blind_rotate: keys not set");
+    int rc = check_form(ctx, form);
+    if (rc != TFHE_OK) return rc;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return blind_rotate_dispatch(ctx, bar, acc, G, form, (cudaStream_t)stream);
+}
+
+extern "C" int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
+                                      void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (G < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "extract_keyswitch: G < 0");
+    if (G == 0) return TFHE_OK;
+    if (!acc || !out) return tfhe_set_error(ctx, TFHE_EINVAL, "extract_keyswitch: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "extract_keyswitch: no keys");
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return launch_extract_keyswitch(ctx, acc, out, G, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+extern "C" int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group,
+                               const uint32_t *d1, const uint32_t *d0, uint32_t *out, int B,
+                               int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (B < 0 || group < 1) return tfhe_set_error(ctx, TFHE_EINVAL, "cmux_batch: B < 0 or group < 1");
+    if (B == 0) return TFHE_OK;
+    if (!trgsw || !d1 || !d0 || !out)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "cmux_batch: null pointer");
+    int rc = check_form(ctx, form);
+    if (rc != TFHE_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int64_t N2 = 2 * (int64_t)ctx->p.N;
+    const int gx = group < B ? group : B;
+    const int ny = (B + group - 1) / group;
+    CmuxGeom g{d1, d0, out, N2, (int64_t)group * N2, N2, (int64_t)group * N2, 1, gx, ny, B};
+    if (form == TFHE_FORM_TC) return tfhe_cmux_tc(ctx, trgsw, g, st);
+    rc = tfhe_ensure_trgsw_ws(ctx, (size_t)ny);
+    if (rc != TFHE_OK) return rc;
+    rc = tfhe_trgsw_to_ntt(ctx, trgsw, ctx->ws_trgsw_ntt, (size_t)ny, st);
+    if (rc != TFHE_OK) return rc;
+    return tfhe_cmux_ntt(ctx, ctx->ws_trgsw_ntt, g, st);
+}
+
+static int grow(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need) {
+    if (need <= *cap) return TFHE_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, need) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "host-API staging allocation");
+    *cap = need;
+    return TFHE_OK;
+}
+
+extern "C" int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                                    const uint8_t *types, const int32_t *in_idx, uint32_t *out,
+                                    int G, int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (G < 0 || num_in < 1) return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch_host: sizes");
+    if (G == 0) return TFHE_OK;
+    if (!in || !types || !in_idx || !out)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch_host: null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t w = (size_t)ctx->p.n + 1;
+    size_t in_cap = ctx->st_in_cap, gate_cap = ctx->st_gate_cap, tcap = ctx->st_gate_cap,
+           icap = ctx->st_gate_cap;
+    int rc = grow(ctx, (void **)&ctx->st_in, &in_cap, (size_t)num_in * w * 4);
+    if (rc != TFHE_OK) return rc;
+    ctx->st_in_cap = in_cap;
+    if ((size_t)G * w * 4 > ctx->st_gate_cap) {
+        rc = grow(ctx, (void **)&ctx->st_out, &gate_cap, (size_t)G * w * 4);
+        if (rc == TFHE_OK) rc = grow(ctx, (void **)&ctx->st_types, &tcap, (size_t)G * w * 4);
+        if (rc == TFHE_OK) rc = grow(ctx, (void **)&ctx->st_idx, &icap, (size_t)G * w * 4);
+        if (rc != TFHE_OK) {
+            ctx->st_gate_cap = 0;
+            return rc;
+        }
+        ctx->st_gate_cap = gate_cap;
+    }
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->st_in, in, (size_t)num_in * w * 4,
+                                       cudaMemcpyHostToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->st_types, types, (size_t)G, cudaMemcpyHostToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->st_idx, in_idx, (size_t)G * 8, cudaMemcpyHostToDevice,
+                                       st));
+    rc = tfhe_gate_batch(ctx, ctx->st_in, num_in, ctx->st_types, ctx->st_idx, ctx->st_out, G, form,
+                         stream);
+    if (rc != TFHE_OK) return rc;
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->st_out, (size_t)G * w * 4,
+                                       cudaMemcpyDeviceToHost, st));
+    TFHE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return TFHE_OK;
+}

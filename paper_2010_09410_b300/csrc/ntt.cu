@@ -1,0 +1,302 @@
+// ntt.cu -- the plain per-gate form: BlindRotate and CMUX with each external product
+// computed by an exact negacyclic NTT over P = 2^64 - 2^32 + 1 (the GPU TFHE library
+// form of Section 6.2(a)).  One thread block owns one gate (or one CMUX): its
+// accumulator, digit polynomials and transforms live in shared memory for all n steps.
+//
+// Exactness: a product sum_r d_r * k_r with |d| <= Bg/2, key words < 2^32 and 2l rows
+// of N terms is below 2l * N * (Bg/2) * 2^32 (< 2^50 for l = 3, N = 1024, Bg = 64) <
+// P/2 in magnitude, so its residue mod P identifies the integer, which is then
+// reduced mod 2^32 (gl_lift_u32).
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// Host: twiddles
+// ---------------------------------------------------------------------------
+
+static uint64_t h_mulmod(uint64_t a, uint64_t b) {
+    return (uint64_t)((unsigned __int128)a * b % GL_P);
+}
+
+static uint64_t h_powmod(uint64_t a, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = h_mulmod(r, a);
+        a = h_mulmod(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+
+static int bitrev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+int tfhe_ntt_setup(tfhe_ctx *ctx) {
+    const int N = ctx->p.N, logN = ctx->logN;
+    // 7 generates the multiplicative group of Z_P (order 2^32 (2^32 - 1)).
+    const uint64_t psi = h_powmod(7, (GL_P - 1) / (2 * (uint64_t)N));
+    if (h_powmod(psi, N) != GL_P - 1)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no primitive 2N-th root of unity");
+    const uint64_t psi_inv = h_powmod(psi, GL_P - 2);
+    std::vector<uint64_t> f(N), g(N);
+    for (int k = 0; k < N; k++) {
+        f[k] = h_powmod(psi, (uint64_t)bitrev(k, logN));
+        g[k] = h_powmod(psi_inv, (uint64_t)bitrev(k, logN));
+    }
+    ctx->n_inv = h_powmod((uint64_t)N, GL_P - 2);
+    if (cudaMalloc(&ctx->psi_fwd, N * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->psi_inv, N * 8) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "twiddle tables");
+    TFHE_CUDA_TRY(ctx, cudaMemcpy(ctx->psi_fwd, f.data(), N * 8, cudaMemcpyHostToDevice));
+    TFHE_CUDA_TRY(ctx, cudaMemcpy(ctx->psi_inv, g.data(), N * 8, cudaMemcpyHostToDevice));
+    return TFHE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device: in-place negacyclic transforms of `np` polynomials a[np][N] in shared memory
+// ---------------------------------------------------------------------------
+
+// Cooley-Tukey butterflies with twiddles psi^{brv(m+i)}: natural order in,
+// evaluations at the odd powers of psi (bit-reversed order) out.
+__device__ __forceinline__ void ntt_fwd(uint64_t *a, int np, int N, int logN,
+                                        const uint64_t *__restrict__ psi) {
+    const int half = N >> 1;
+    for (int s = 0; s < logN; s++) {
+        const int m = 1 << s, logt = logN - 1 - s, t = 1 << logt;
+        for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+            const int poly = idx >> (logN - 1), b = idx & (half - 1);
+            const int i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
+            uint64_t *x = a + (size_t)poly * N;
+            const uint64_t S = __ldg(psi + m + i);
+            const uint64_t U = x[j], V = gl_mul(x[j + t], S);
+            x[j] = gl_add(U, V);
+            x[j + t] = gl_sub(U, V);
+        }
+        __syncthreads();
+    }
+}
+
+// Gentleman-Sande butterflies with psi^{-brv(h+i)}: bit-reversed in, natural out.
+// The factor N^{-1} is folded into the NTT-domain keys.
+__device__ __forceinline__ void ntt_inv(uint64_t *a, int np, int N, int logN,
+                                        const uint64_t *__restrict__ psi_inv) {
+    const int half = N >> 1;
+    for (int s = 0; s < logN; s++) {
+        const int logt = s, t = 1 << s, h = N >> (s + 1);
+        for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+            const int poly = idx >> (logN - 1), b = idx & (half - 1);
+            const int i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
+            uint64_t *x = a + (size_t)poly * N;
+            const uint64_t S = __ldg(psi_inv + h + i);
+            const uint64_t U = x[j], V = x[j + t];
+            x[j] = gl_add(U, V);
+            x[j + t] = gl_mul(gl_sub(U, V), S);
+        }
+        __syncthreads();
+    }
+}
+
+// Polynomials (u32 words as integers in [0, 2^32)) -> NTT domain scaled by N^{-1}.
+__global__ void k_polys_to_ntt(const uint32_t *__restrict__ src, uint64_t *__restrict__ dst,
+                               int N, int logN, uint64_t n_inv,
+                               const uint64_t *__restrict__ psi) {
+    extern __shared__ uint64_t sm[];
+    const size_t poly = blockIdx.x;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[k] = src[poly * N + k];
+    __syncthreads();
+    ntt_fwd(sm, 1, N, logN, psi);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[poly * N + k] = gl_mul(sm[k], n_inv);
+}
+
+// External product of the TRLWE `d` (u32[2][N] in shared memory) by an NTT-domain
+// TRGSW `key` (u64[2l][2][N]): prod (u64[2][N], shared) receives C (.) d in
+// coefficient form, as residues.  `dig` is u64[2l][N] shared scratch.  Digit rows:
+// j < l from the a-polynomial (paired with TRGSW row j), l + j from b.
+__device__ __forceinline__ void extprod_ntt(const uint32_t *d, const uint64_t *__restrict__ key,
+                                            uint64_t *dig, uint64_t *prod, int N, int logN,
+                                            int l, int Bgbit, const uint64_t *__restrict__ psi_f,
+                                            const uint64_t *__restrict__ psi_i) {
+    const uint32_t off = gadget_offset(l, Bgbit);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        for (int c = 0; c < 2; c++) {
+            const uint32_t u = d[c * N + j] + off;
+            for (int r = 0; r < l; r++)
+                dig[(size_t)(c * l + r) * N + j] = gl_from_i32(gadget_digit(u, r + 1, Bgbit));
+        }
+    }
+    __syncthreads();
+    ntt_fwd(dig, 2 * l, N, logN, psi_f);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        uint64_t s0 = 0, s1 = 0;
+        for (int r = 0; r < 2 * l; r++) {
+            const uint64_t dv = dig[(size_t)r * N + k];
+            s0 = gl_add(s0, gl_mul(dv, __ldg(key + (size_t)(r * 2 + 0) * N + k)));
+            s1 = gl_add(s1, gl_mul(dv, __ldg(key + (size_t)(r * 2 + 1) * N + k)));
+        }
+        prod[k] = s0;
+        prod[N + k] = s1;
+    }
+    __syncthreads();
+    ntt_inv(prod, 2, N, logN, psi_i);
+}
+
+// One block per gate: BlindRotate of the test vector by (a~, b~) = bar[g].
+__global__ void __launch_bounds__(256) k_blind_rotate_ntt(
+    int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
+    uint32_t *__restrict__ acc_out, const uint64_t *__restrict__ bsk,
+    const uint64_t *__restrict__ psi_f, const uint64_t *__restrict__ psi_i) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *dig = sm;                                  // [2l][N]
+    uint64_t *prod = sm + (size_t)2 * l * N;             // [2][N]
+    uint32_t *acc = (uint32_t *)(prod + (size_t)2 * N);  // [2][N]
+    uint32_t *diff = acc + 2 * N;                        // [2][N]
+    const size_t g = blockIdx.x;
+    const uint32_t *mb = bar + g * (n + 1);
+    const uint32_t mu = 1u << 29;
+    const int N2 = 2 * N;
+    const int bb = (int)(mb[n] % (uint32_t)N2);
+    // ACC = X^{-b~} (0, v): coefficient j of X^{-b~} v is +mu when (j + b~) mod 2N < N.
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        acc[j] = 0;
+        acc[N + j] = ((j + bb) % N2) < N ? mu : 0u - mu;
+    }
+    __syncthreads();
+    const size_t per = (size_t)2 * l * 2 * N;
+    for (int i = 0; i < n; i++) {
+        const int a = (int)(mb[i] % (uint32_t)N2);
+        if (a == 0) continue;  // X^0 ACC - ACC = 0 has all-zero digits: the step is the identity
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            diff[j] = rot_coef(acc, N, a, j) - acc[j];
+            diff[N + j] = rot_coef(acc + N, N, a, j) - acc[N + j];
+        }
+        __syncthreads();
+        extprod_ntt(diff, bsk + (size_t)i * per, dig, prod, N, logN, l, Bgbit, psi_f, psi_i);
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            acc[j] += gl_lift_u32(prod[j]);
+            acc[N + j] += gl_lift_u32(prod[N + j]);
+        }
+        __syncthreads();
+    }
+    uint32_t *o = acc_out + g * 2 * N;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = acc[j];
+}
+
+// One block per CMUX (x, y) = (blockIdx.x, blockIdx.y) of the geometry g:
+// out = d0 + C_y (.) (d1 - d0).  out may alias d0 or d1 of the same CMUX.
+__global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bgbit,
+                                                  const uint64_t *__restrict__ sel, CmuxGeom g,
+                                                  const uint64_t *__restrict__ psi_f,
+                                                  const uint64_t *__restrict__ psi_i) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *dig = sm;
+    uint64_t *prod = sm + (size_t)2 * l * N;
+    uint32_t *diff = (uint32_t *)(prod + (size_t)2 * N);
+    uint32_t *base = diff + 2 * N;
+    const int64_t x = blockIdx.x, y = blockIdx.y;
+    if (y * g.nx + x >= g.count) return;
+    const uint32_t *a1 = g.d1 + x * g.dx + y * g.dy, *a0 = g.d0 + x * g.dx + y * g.dy;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+        const uint32_t x0 = a0[j];
+        base[j] = x0;
+        diff[j] = a1[j] - x0;
+    }
+    __syncthreads();
+    const size_t per = (size_t)2 * l * 2 * N;
+    extprod_ntt(diff, sel + (size_t)y * g.sy * per, dig, prod, N, logN, l, Bgbit, psi_f, psi_i);
+    uint32_t *o = g.out + x * g.ox + y * g.oy;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = base[j] + gl_lift_u32(prod[j]);
+}
+
+// One block per RAM cell c (write bar, Section 8.2): r = new; for j < v:
+// r = CMUX(S_j, r, cell_c) with S_j = C_j when bit j of c is 1 and G - C_j otherwise.
+__global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, int Bgbit, int v,
+                                                       const uint64_t *__restrict__ c_ntt,
+                                                       const uint64_t *__restrict__ gmc_ntt,
+                                                       const uint32_t *__restrict__ new_cell,
+                                                       uint32_t *cells,
+                                                       const uint64_t *__restrict__ psi_f,
+                                                       const uint64_t *__restrict__ psi_i) {
+    extern __shared__ uint64_t sm[];
+    uint64_t *dig = sm;
+    uint64_t *prod = sm + (size_t)2 * l * N;
+    uint32_t *diff = (uint32_t *)(prod + (size_t)2 * N);
+    uint32_t *r = diff + 2 * N;
+    uint32_t *old = r + 2 * N;
+    const size_t c = blockIdx.x;
+    uint32_t *cell = cells + c * 2 * N;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+        r[j] = new_cell[j];
+        old[j] = cell[j];
+    }
+    __syncthreads();
+    const size_t per = (size_t)2 * l * 2 * N;
+    for (int b = 0; b < v; b++) {
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) diff[j] = r[j] - old[j];
+        __syncthreads();
+        const uint64_t *S = (((c >> b) & 1) ? c_ntt : gmc_ntt) + (size_t)b * per;
+        extprod_ntt(diff, S, dig, prod, N, logN, l, Bgbit, psi_f, psi_i);
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) r[j] = old[j] + gl_lift_u32(prod[j]);
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) cell[j] = r[j];
+}
+
+int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
+                      cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    const size_t polys = count * 2 * p.l * 2;
+    if (polys == 0) return TFHE_OK;
+    k_polys_to_ntt<<<(unsigned)polys, 256, p.N * 8, st>>>(trgsw, out, p.N, ctx->logN, ctx->n_inv,
+                                                         ctx->psi_fwd);
+    return tfhe_check_launch(ctx, "polys_to_ntt");
+}
+
+int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                          cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (G == 0) return TFHE_OK;
+    const size_t smem = (size_t)2 * p.l * p.N * 8 + (size_t)2 * p.N * 8 + (size_t)4 * p.N * 4;
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_NTT, st);
+    k_blind_rotate_ntt<<<G, 256, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar, acc,
+                                             ctx->bsk_ntt, ctx->psi_fwd, ctx->psi_inv);
+    tm.stop();
+    return tfhe_check_launch(ctx, "blind_rotate_ntt");
+}
+
+static size_t cmux_smem(const tfhe_params &p) {
+    return (size_t)2 * p.l * p.N * 8 + (size_t)2 * p.N * 8 + (size_t)6 * p.N * 4;
+}
+
+int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (g.count == 0) return TFHE_OK;
+    const size_t smem = cmux_smem(p);
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_cmux_ntt,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    dim3 grid(g.nx, g.ny);
+    StageTimer tm(ctx, TFHE_STAGE_CMUX, st);
+    k_cmux_ntt<<<grid, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, sel_ntt, g, ctx->psi_fwd,
+                                        ctx->psi_inv);
+    tm.stop();
+    return tfhe_check_launch(ctx, "cmux_ntt");
+}
+
+int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
+                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    const size_t smem = cmux_smem(p) + (size_t)2 * p.N * 4;
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_ram_write_ntt,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    StageTimer tm(ctx, TFHE_STAGE_CMUX, st);
+    k_ram_write_ntt<<<1u << v, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, v, c_ntt, gmc_ntt,
+                                               new_cell, cells, ctx->psi_fwd, ctx->psi_inv);
+    tm.stop();
+    return tfhe_check_launch(ctx, "ram_write_ntt");
+}

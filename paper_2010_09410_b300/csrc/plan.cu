@@ -1,0 +1,243 @@
+// plan.cu -- level scheduler (Section 6.2(d)): circuits -> DAG -> levels of independent
+// gates; level k of every circuit runs as one tfhe_gate_batch; the whole level
+// schedule is optionally captured into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+struct tfhe_plan {
+    tfhe_ctx *ctx = nullptr;
+    int num_levels = 0;
+    int64_t total_inputs = 0, total_gates = 0, total_wires = 0;
+    std::vector<int64_t> level_off;   // [num_levels + 1] offsets into the level-major gate list
+    std::vector<int> level_form;      // form per level
+    std::vector<int> circuit_last;    // last level of each circuit
+    uint8_t *d_types = nullptr;       // level-major gate types
+    int32_t *d_idx = nullptr;         // level-major input wire indices (internal numbering)
+    int64_t *d_perm = nullptr;        // output slot (circuit order) -> internal wire
+    uint32_t *d_wires = nullptr;      // [total_wires][n+1]
+    // graph cache
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint32_t *g_in = nullptr;
+    uint32_t *g_out = nullptr;
+    cudaStream_t g_stream = nullptr;
+};
+
+// gate_out[s] = wires[perm[s]] for every output slot s; one block per slot.
+__global__ void k_gather_rows(const uint32_t *__restrict__ wires, const int64_t *__restrict__ perm,
+                              uint32_t *__restrict__ out, int w) {
+    const int64_t s = blockIdx.x;
+    const uint32_t *src = wires + perm[s] * w;
+    uint32_t *dst = out + s * w;
+    for (int k = threadIdx.x; k < w; k += blockDim.x) dst[k] = src[k];
+}
+
+extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
+    if (!plan) return;
+    if (plan->ctx) cudaSetDevice(plan->ctx->device);
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    if (plan->d_types) cudaFree(plan->d_types);
+    if (plan->d_idx) cudaFree(plan->d_idx);
+    if (plan->d_perm) cudaFree(plan->d_perm);
+    if (plan->d_wires) cudaFree(plan->d_wires);
+    delete plan;
+}
+
+// Form for a level of `width` gates when the caller lets the plan choose (form = -1):
+// the tensor-core form once the batch is wide enough to fill its 128-gate tiles.
+static int tfhe_plan_pick_form(tfhe_ctx *ctx, int64_t width) {
+    if (!tfhe_tc_supported(ctx)) return TFHE_FORM_NTT;
+    return width >= ctx->tc_min_width ? TFHE_FORM_TC : TFHE_FORM_NTT;
+}
+
+extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, int num_circuits,
+                                 int form, tfhe_plan **out) {
+    if (!ctx || !out) return TFHE_EINVAL;
+    *out = nullptr;
+    if (!circuits || num_circuits < 1)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: no circuits");
+    if (form != -1 && form != TFHE_FORM_NTT && form != TFHE_FORM_TC)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: unknown form");
+    if (form == TFHE_FORM_TC && !tfhe_tc_supported(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "circuit_plan: tensor-core form unsupported");
+    // levels per gate: level(g) = 1 + max(level of its input wires), primaries at -1
+    std::vector<std::vector<int>> lvl(num_circuits);
+    int64_t total_in = 0, total_g = 0;
+    int num_levels = 0;
+    for (int c = 0; c < num_circuits; c++) {
+        const tfhe_circuit &C = circuits[c];
+        if (C.num_inputs < 0 || C.num_gates < 0 || (C.num_gates > 0 && (!C.types || !C.in_idx)))
+            return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: bad circuit arrays");
+        lvl[c].assign(C.num_gates, 0);
+        for (int g = 0; g < C.num_gates; g++) {
+            if (C.types[g] >= 10)
+                return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: bad gate type");
+            int L = 0;
+            for (int s = 0; s < 2; s++) {
+                const int32_t w = C.in_idx[2 * g + s];
+                if (w < 0 || w >= C.num_inputs + g)
+                    return tfhe_set_error(ctx, TFHE_EINVAL,
+                                          "circuit_plan: gate input is not an earlier wire");
+                if (w >= C.num_inputs) L = std::max(L, lvl[c][w - C.num_inputs] + 1);
+            }
+            lvl[c][g] = L;
+            num_levels = std::max(num_levels, L + 1);
+        }
+        total_in += C.num_inputs;
+        total_g += C.num_gates;
+    }
+    tfhe_plan *plan = new tfhe_plan();
+    plan->ctx = ctx;
+    plan->num_levels = num_levels;
+    plan->total_inputs = total_in;
+    plan->total_gates = total_g;
+    plan->total_wires = total_in + total_g;
+    // level-major order: level, then circuit, then original gate index
+    std::vector<int64_t> count(num_levels + 1, 0);
+    for (int c = 0; c < num_circuits; c++)
+        for (int g = 0; g < circuits[c].num_gates; g++) count[lvl[c][g] + 1]++;
+    plan->level_off.assign(num_levels + 1, 0);
+    for (int L = 0; L < num_levels; L++) plan->level_off[L + 1] = plan->level_off[L] + count[L + 1];
+    std::vector<int64_t> fill(plan->level_off.begin(), plan->level_off.end() - 1);
+    std::vector<std::vector<int64_t>> internal(num_circuits);  // gate -> internal wire
+    std::vector<int64_t> in_off(num_circuits, 0);
+    for (int c = 1; c < num_circuits; c++) in_off[c] = in_off[c - 1] + circuits[c - 1].num_inputs;
+    std::vector<uint8_t> h_types(total_g);
+    std::vector<int32_t> h_idx(2 * total_g);
+    plan->circuit_last.assign(num_circuits, -1);
+    for (int c = 0; c < num_circuits; c++) {
+        internal[c].resize(circuits[c].num_gates);
+        for (int g = 0; g < circuits[c].num_gates; g++) {
+            const int64_t pos = fill[lvl[c][g]]++;
+            internal[c][g] = total_in + pos;
+            plan->circuit_last[c] = std::max(plan->circuit_last[c], lvl[c][g]);
+        }
+    }
+    if (plan->total_wires >= INT32_MAX) {
+        tfhe_plan_destroy(plan);
+        return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: too many wires");
+    }
+    std::vector<int64_t> perm(total_g);
+    int64_t slot = 0;
+    for (int c = 0; c < num_circuits; c++) {
+        const tfhe_circuit &C = circuits[c];
+        for (int g = 0; g < C.num_gates; g++) {
+            const int64_t pos = internal[c][g] - total_in;
+            h_types[pos] = C.types[g];
+            for (int s = 0; s < 2; s++) {
+                const int32_t w = C.in_idx[2 * g + s];
+                h_idx[2 * pos + s] = (int32_t)(w < C.num_inputs ? in_off[c] + w
+                                                                 : internal[c][w - C.num_inputs]);
+            }
+            perm[slot++] = internal[c][g];
+        }
+    }
+    plan->level_form.assign(num_levels, form);
+    int64_t max_w = 0;
+    for (int L = 0; L < num_levels; L++) {
+        const int64_t w = plan->level_off[L + 1] - plan->level_off[L];
+        max_w = std::max(max_w, w);
+        if (form == -1) plan->level_form[L] = tfhe_plan_pick_form(ctx, w);
+    }
+    const size_t wb = (size_t)ctx->p.n + 1;
+    if (cudaSetDevice(ctx->device) != cudaSuccess ||
+        cudaMalloc(&plan->d_types, std::max<int64_t>(total_g, 1)) != cudaSuccess ||
+        cudaMalloc(&plan->d_idx, std::max<int64_t>(2 * total_g, 1) * 4) != cudaSuccess ||
+        cudaMalloc(&plan->d_perm, std::max<int64_t>(total_g, 1) * 8) != cudaSuccess ||
+        cudaMalloc(&plan->d_wires, std::max<int64_t>(plan->total_wires, 1) * wb * 4) != cudaSuccess) {
+        tfhe_plan_destroy(plan);
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "circuit_plan: device allocation");
+    }
+    if (total_g > 0 &&
+        (cudaMemcpy(plan->d_types, h_types.data(), total_g, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(plan->d_idx, h_idx.data(), 2 * total_g * 4, cudaMemcpyHostToDevice) !=
+             cudaSuccess ||
+         cudaMemcpy(plan->d_perm, perm.data(), total_g * 8, cudaMemcpyHostToDevice) != cudaSuccess)) {
+        tfhe_plan_destroy(plan);
+        return tfhe_set_error(ctx, TFHE_ECUDA, "circuit_plan: upload");
+    }
+    int rc = tfhe_ensure_workspace(ctx, (int)max_w);
+    if (rc != TFHE_OK) {
+        tfhe_plan_destroy(plan);
+        return rc;
+    }
+    *out = plan;
+    return TFHE_OK;
+}
+
+extern "C" int tfhe_plan_num_levels(const tfhe_plan *plan) { return plan ? plan->num_levels : -1; }
+
+extern "C" int tfhe_plan_circuit_last_level(const tfhe_plan *plan, int c) {
+    if (!plan || c < 0 || c >= (int)plan->circuit_last.size()) return -1;
+    return plan->circuit_last[c];
+}
+
+// Enqueue the whole schedule on `st`.
+static int plan_enqueue(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out,
+                        void **events, cudaStream_t st) {
+    tfhe_ctx *ctx = plan->ctx;
+    const size_t wb = (size_t)ctx->p.n + 1;
+    if (plan->total_inputs > 0)
+        TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(plan->d_wires, primary_in,
+                                           plan->total_inputs * wb * 4,
+                                           cudaMemcpyDeviceToDevice, st));
+    for (int L = 0; L < plan->num_levels; L++) {
+        const int64_t off = plan->level_off[L];
+        const int G = (int)(plan->level_off[L + 1] - off);
+        int rc = tfhe_gate_batch(ctx, plan->d_wires, plan->total_wires, plan->d_types + off,
+                                 plan->d_idx + 2 * off,
+                                 plan->d_wires + (plan->total_inputs + off) * wb, G,
+                                 plan->level_form[L], st);
+        if (rc != TFHE_OK) return rc;
+        if (events && events[L]) TFHE_CUDA_TRY(ctx, cudaEventRecord((cudaEvent_t)events[L], st));
+    }
+    if (plan->total_gates > 0) {
+        k_gather_rows<<<(unsigned)plan->total_gates, 128, 0, st>>>(plan->d_wires, plan->d_perm,
+                                                                   gate_out, (int)wb);
+        return tfhe_check_launch(ctx, "gather_rows");
+    }
+    return TFHE_OK;
+}
+
+extern "C" int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out,
+                             int use_graph, void **level_events, void *stream) {
+    if (!plan) return TFHE_EINVAL;
+    tfhe_ctx *ctx = plan->ctx;
+    if ((plan->total_inputs > 0 && !primary_in) || (plan->total_gates > 0 && !gate_out))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "plan_run: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "plan_run: keys not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (!use_graph) return plan_enqueue(plan, primary_in, gate_out, level_events, st);
+    if (!plan->exec || plan->g_in != primary_in || plan->g_out != gate_out) {
+        if (plan->exec) cudaGraphExecDestroy(plan->exec);
+        if (plan->graph) cudaGraphDestroy(plan->graph);
+        plan->exec = nullptr;
+        plan->graph = nullptr;
+        if (!plan->cap_stream)
+            TFHE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+        TFHE_CUDA_TRY(ctx, cudaStreamBeginCapture(plan->cap_stream,
+                                                  cudaStreamCaptureModeThreadLocal));
+        int rc = plan_enqueue(plan, primary_in, gate_out, nullptr, plan->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (rc != TFHE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess)
+            return tfhe_set_error(ctx, TFHE_ECUDA,
+                                  std::string("plan graph capture: ") + cudaGetErrorString(e));
+        plan->graph = g;
+        TFHE_CUDA_TRY(ctx, cudaGraphInstantiate(&plan->exec, g, 0));
+        plan->g_in = primary_in;
+        plan->g_out = gate_out;
+    }
+    TFHE_CUDA_TRY(ctx, cudaGraphLaunch(plan->exec, st));
+    return TFHE_OK;
+}

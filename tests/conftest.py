@@ -45,3 +45,55 @@ def pins_lib():
     for f in (lib.chk_decompose, lib.chk_ks_digits, lib.chk_modswitch):
         f.restype = u64
     return lib
+
+
+# ---- GPU fixtures ------------------------------------------------------------------
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    return _cuda()
+
+
+_CTX = {}
+
+
+def gpu_context(params, seed):
+    """A library context on cuda:0 with the seeded keys of (params, seed) loaded."""
+    key = (params, seed)
+    if key not in _CTX:
+        torch = _cuda()
+        import paper_2010_09410_b300 as tb
+        import tfhe_inputs as ti
+        from paper_2010_09410_b300 import build as tbuild
+        tbuild.build()
+        k = ti.keys(params, seed)
+        ctx = tb.Context(params, 0)
+        bsk = torch.from_numpy(k.bsk.view("int32")).cuda()
+        ksk = torch.from_numpy(k.ksk.view("int32")).cuda()
+        ctx.set_keys(bsk, ksk)
+        ctx.sync()
+        _CTX[key] = (ctx, k)
+    return _CTX[key]
+
+
+def to_dev(a):
+    """numpy uint32/uint8/int32 array -> CUDA tensor with the same bytes."""
+    import numpy as np
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def from_dev(t):
+    """CUDA int32 tensor -> numpy uint32."""
+    import numpy as np
+    return t.cpu().numpy().view(np.uint32)

@@ -1,0 +1,130 @@
+"""GPU parity of bootstrapped gates, BlindRotate and key switching against the CPU
+oracle: every output word bit-exact (all arithmetic is mod 2^32)."""
+import numpy as np
+import pytest
+
+import oracle as orc
+import tfhe_inputs as ti
+from conftest import from_dev, gpu_context, to_dev
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [0]
+
+
+def empty(torch, *shape):
+    return torch.zeros(shape, dtype=torch.int32, device="cuda")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_toy_gates_bit_exact(torch_cuda, form):
+    b = ti.toy_gates()
+    ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
+    out = empty(torch_cuda, b.types.size, ti.TOY.n + 1)
+    ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=form)
+    ctx.sync()
+    got = from_dev(out)
+    want = orc.gate_batch(ti.TOY, k.bsk, k.ksk, b.inp, b.types, b.idx)
+    assert np.array_equal(got, want)
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, got), b.expected)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_blind_rotate_stage_toy(torch_cuda, form):
+    p = ti.TOY
+    ctx, k = gpu_context(p, ti.SEED_TOY)
+    rng = np.random.default_rng(1)
+    G = 19
+    bar = rng.integers(0, 2 * p.N, (G, p.n + 1)).astype(np.uint32)
+    bar[3, :] = 0                  # all rotations zero
+    bar[4, :-1] = 0                # only b~ nonzero
+    bar[5, -1] = 2 * p.N - 1
+    acc = empty(torch_cuda, G, 2, p.N)
+    ctx.blind_rotate(to_dev(bar), acc, form=form)
+    ctx.sync()
+    got = from_dev(acc)
+    for g in range(G):
+        assert np.array_equal(got[g], orc.blind_rotate(p, k.bsk, bar[g])), g
+
+
+def test_extract_keyswitch_stage_toy(torch_cuda):
+    p = ti.TOY
+    ctx, k = gpu_context(p, ti.SEED_TOY)
+    rng = np.random.default_rng(2)
+    G = 21                          # not a multiple of the 8-gate key-switch tile
+    acc = rng.integers(0, 2**32, (G, 2, p.N), dtype=np.uint64).astype(np.uint32)
+    out = empty(torch_cuda, G, p.n + 1)
+    ctx.extract_keyswitch(to_dev(acc), out)
+    ctx.sync()
+    got = from_dev(out)
+    for g in range(G):
+        want = orc.keyswitch(p, k.ksk, orc.sample_extract(acc[g]))
+        assert np.array_equal(got[g], want), g
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_tfhe_like_gates_ragged_batch(torch_cuda, form):
+    """37 gates at n=630, N=1024: spans several key-switch tiles plus a ragged tail;
+    every output word compared with the oracle."""
+    b = ti.flat_level(37)
+    ctx, k = gpu_context(ti.STD, ti.SEED_FLAT)
+    out = empty(torch_cuda, 37, ti.STD.n + 1)
+    ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=form)
+    ctx.sync()
+    got = from_dev(out)
+    want = orc.gate_batch(ti.STD, k.bsk, k.ksk, b.inp, b.types, b.idx)
+    assert np.array_equal(got, want)
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, got), b.expected)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_flat_level_4096_sampled(torch_cuda, form):
+    """The full 4096-gate level in the benchmark's launch configuration: all outputs
+    decrypt to the plaintext gates, and sampled gates match the oracle word for word."""
+    b = ti.flat_level(4096)
+    ctx, k = gpu_context(ti.STD, ti.SEED_FLAT)
+    out = empty(torch_cuda, 4096, ti.STD.n + 1)
+    ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=form)
+    ctx.sync()
+    got = from_dev(out)
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, got), b.expected)
+    sample = [0, 1, 127, 128, 2047, 4095] + list(np.random.default_rng(3).integers(0, 4096, 4))
+    want = orc.gate_batch(ti.STD, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=sample)
+    assert np.array_equal(got[sample], want)
+
+
+def test_zero_gates_is_noop(torch_cuda):
+    ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
+    t = empty(torch_cuda, 0)
+    ctx.gate_batch(empty(torch_cuda, 1, ti.TOY.n + 1), t.to(torch_cuda.uint8), t, t)
+    ctx.sync()
+
+
+def test_bad_type_and_index_reported_on_device(torch_cuda):
+    b = ti.toy_gates()
+    ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
+    types = b.types.copy()
+    idx = b.idx.copy()
+    types[2] = 10
+    idx[5, 1] = 1000
+    out = empty(torch_cuda, types.size, ti.TOY.n + 1)
+    ctx.gate_batch(to_dev(b.inp), to_dev(types), to_dev(idx), out)
+    import paper_2010_09410_b300 as tb
+    with pytest.raises(tb.TfheError) as e:
+        ctx.sync()
+    assert e.value.code == -1
+    got = from_dev(out)
+    assert not got[2].any() and not got[5].any()
+    good = [g for g in range(types.size) if g not in (2, 5)]
+    want = orc.gate_batch(ti.TOY, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=good)
+    assert np.array_equal(got[good], want)
+    ctx.sync()                          # the error word was cleared
+
+
+def test_host_buffer_entry_point_matches_device(torch_cuda):
+    b = ti.toy_gates()
+    ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
+    out = np.zeros((b.types.size, ti.TOY.n + 1), np.uint32)
+    ctx.gate_batch_host(b.inp, b.types, np.ascontiguousarray(b.idx), out)
+    want = orc.gate_batch(ti.TOY, k.bsk, k.ksk, b.inp, b.types, b.idx)
+    assert np.array_equal(out, want)

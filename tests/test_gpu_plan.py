@@ -1,0 +1,47 @@
+"""GPU level scheduler: a layered circuit evaluated level by level (and replayed from
+a captured CUDA graph) matches the oracle gate for gate."""
+import numpy as np
+import pytest
+
+import oracle as orc
+import tfhe_inputs as ti
+from conftest import from_dev, gpu_context, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_circuit(p, k, c, inp):
+    wires = np.zeros((c.num_inputs + c.num_gates, p.n + 1), np.uint32)
+    wires[: c.num_inputs] = inp
+    for L in range(int(c.level.max()) + 1):
+        gs = np.nonzero(c.level == L)[0]
+        out = orc.gate_batch(p, k.bsk, k.ksk, wires, c.types, c.idx, gates=gs)
+        wires[c.num_inputs + gs] = out
+    return wires[c.num_inputs:]
+
+
+@pytest.mark.parametrize("form", [-1, 0])
+def test_toy_dag_matches_oracle(torch_cuda, form):
+    import paper_2010_09410_b300 as tb
+    p = ti.TOY
+    ctx, k = gpu_context(p, ti.SEED_TOY)
+    circs = [ti.layered_dag(ti.SEED_TOY, total=150, levels=8, num_inputs=16, lo=5, hi=40, stream=s)
+             for s in (1, 2)]
+    ins = [ti.encrypt_tlwe0_bits(p, ti.SEED_TOY, 50 + i, k.s0,
+                                 ti.random_bits(ti.SEED_TOY, 60 + i, c.num_inputs))
+           for i, c in enumerate(circs)]
+    plan = ctx.plan(circs, form)
+    assert 1 <= plan.num_levels <= 8
+    out = torch_cuda.zeros((sum(c.num_gates for c in circs), p.n + 1), dtype=torch_cuda.int32,
+                           device="cuda")
+    plan.run(to_dev(np.concatenate(ins)), out)
+    ctx.sync()
+    got = from_dev(out)
+    want = np.concatenate([oracle_circuit(p, k, c, x) for c, x in zip(circs, ins)])
+    assert np.array_equal(got, want)
+    out2 = torch_cuda.zeros_like(out)
+    dev_in = to_dev(np.concatenate(ins))
+    plan.run(dev_in, out2, use_graph=True)
+    plan.run(dev_in, out2, use_graph=True)
+    ctx.sync()
+    assert np.array_equal(from_dev(out2), want)
