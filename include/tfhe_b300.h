@@ -155,6 +155,27 @@ int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
                          const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
                          int form, void *stream);
 
+/* tfhe_gate_batch (NTT form) without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not call cudaMalloc
+ * while they run -- for example a process whose device memory is all owned by
+ * another allocator (a framework's caching pool, or an arena reserved at start-up),
+ * where a fresh allocation can fail even though the work fits, or a serving loop that
+ * cannot let an allocation or free stall the device in the middle of a request.
+ * Arguments and results are those of tfhe_gate_batch with form TFHE_FORM_NTT; the
+ * context must already hold its keys (created and loaded beforehand, when allocating
+ * is still allowed).  Instead of the context's workspaces, the call uses a fixed
+ * 2 MiB scratch array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  It therefore accepts at most
+ * G * ((n+1) + 2N) * 4 bytes (rounded) of scratch: 195 gates at n = 630, N = 1024;
+ * larger batches return TFHE_EINVAL without enqueueing anything.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls on a device share the one array: calls
+ * whose work overlaps on the GPU (other streams, other contexts) race and must be
+ * serialised by the caller.  Calls no cudaMalloc, cudaFree or allocating routine. */
+int tfhe_gate_batch_noalloc(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                            const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
+                            void *stream);
+
 /* The stages of tfhe_gate_batch, exposed for testing and for callers that build
  * their own schedules.
  *   tfhe_blind_rotate: bar device u32[G][n+1] with values in [0, 2N) (ModSwitched

@@ -32,7 +32,7 @@ EXPORTS = [
     "tfhe_gate_batch_host", "tfhe_blind_rotate", "tfhe_extract_keyswitch", "tfhe_cmux_batch",
     "tfhe_cmux_tree_read", "tfhe_ram_write", "tfhe_circuit_plan", "tfhe_plan_num_levels",
     "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_destroy",
-    "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times",
+    "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times", "tfhe_gate_batch_noalloc",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "decompose_tc", "extprod_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -84,6 +84,7 @@ def lib():
         "tfhe_plan_destroy": (None, [vp]),
         "tfhe_ctx_enable_timing": (i32, [vp, i32]),
         "tfhe_ctx_stage_times": (i32, [vp, vp, vp]),
+        "tfhe_gate_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -164,6 +165,13 @@ class Context:
         self._check(lib().tfhe_gate_batch(self.h, _ptr(inp), inp.shape[0], _ptr(types),
                                           _ptr(idx), _ptr(out), G, form, _stream(stream)),
                     "gate_batch")
+        return out
+
+    def gate_batch_noalloc(self, inp, types, idx, out, stream=None):
+        """tfhe_gate_batch_noalloc: NTT form, scratch in the library's fixed device array."""
+        self._check(lib().tfhe_gate_batch_noalloc(self.h, _ptr(inp), inp.shape[0], _ptr(types),
+                                                  _ptr(idx), _ptr(out), types.numel(),
+                                                  _stream(stream)), "gate_batch_noalloc")
         return out
 
     def gate_batch_host(self, inp, types, idx, out, form=FORM_NTT, stream=None):

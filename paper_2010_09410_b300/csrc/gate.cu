@@ -286,3 +286,21 @@ extern "C" int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t n
     TFHE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     return TFHE_OK;
 }
+
+// Launch helpers for entry points that supply their own scratch (noalloc.cu): the
+// same launches tfhe_gate_batch makes, on caller-chosen buffers.
+int tfhe_launch_combine(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
+                        const int32_t *in_idx, uint32_t *bar, int G, cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    const int shift = 32 - (ctx->logN + 1);
+    StageTimer tm(ctx, TFHE_STAGE_COMBINE, st);
+    k_combine_modswitch<<<G, 256, 0, st>>>(p.n, shift, in, num_in, types, in_idx, bar, ctx->d_err);
+    tm.stop();
+    return tfhe_check_launch(ctx, "combine_modswitch");
+}
+
+int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
+                                  const uint8_t *types, const int32_t *idx, int64_t num_in,
+                                  cudaStream_t st) {
+    return launch_extract_keyswitch(ctx, acc, out, G, types, idx, num_in, st);
+}
