@@ -41,7 +41,8 @@ constexpr int A_STAGE_BYTES = TILE_M * KS * 2;            // 32 KB
 constexpr int B_UNITS = NB + KS;                          // units per plane and stage
 constexpr int B_PLANE_BYTES = B_UNITS * 16;               // 4 KB
 constexpr int B_STAGE_BYTES = PLANES * B_PLANE_BYTES;     // 16 KB
-constexpr int SMEM_BYTES = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + 1024;
+constexpr int KEY_BYTES_MAX = 6 * 1024 * 4;                // 2l x N key words (l*N <= 3072)
+constexpr int SMEM_BYTES = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + KEY_BYTES_MAX + 1024;
 constexpr int THREADS = 192;
 constexpr long long WAIT_CYCLES = 4000000000LL;           // ~2 s at 2 GHz
 
@@ -186,10 +187,11 @@ __device__ __forceinline__ void byte_planes(uint32_t q, int (&pl)[PLANES]) {
     }
 }
 
-// r_vec[x] of the key polynomial q (zero past 2N: never read by an MMA).
-__device__ __forceinline__ uint32_t rvec(const uint32_t *__restrict__ q, int N, int x) {
-    if (x < N) return __ldg(q + (N - 1 - x));
-    if (x < 2 * N) return 0u - __ldg(q + (2 * N - 1 - x));
+// r_vec[x] of the key polynomial q held in shared memory (zero past 2N: never read by
+// an MMA).
+__device__ __forceinline__ uint32_t rvec(const uint32_t *q, int N, int x) {
+    if (x < N) return q[N - 1 - x];
+    if (x < 2 * N) return 0u - q[2 * N - 1 - x];
     return 0u;
 }
 
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *a_st = smem;                                   // STAGES x 32 KB
     uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;          // STAGES x 16 KB
+    uint32_t *key_s = (uint32_t *)(b_st + STAGES * B_STAGE_BYTES);  // [2l][N], column c
     __shared__ __align__(8) uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, drain;
     __shared__ uint32_t tmem_slot;
@@ -372,6 +375,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
         const int tid = threadIdx.x;  // 0..127, also the TMEM lane = gate of the tile
         const int g = tile * TILE_M + tid;
         uint32_t *acc_row = acc + (size_t)g * 2 * N + (size_t)c * N;
+        // the 2l key polynomials of column c, into shared memory (named barrier 1 = warps 0-3)
+        for (int w = tid; w < 2 * l * N / 4; w += 128) {
+            const int r = (w * 4) / N, k = (w * 4) % N;
+            *(uint4 *)(key_s + r * N + k) = __ldg((const uint4 *)(keys + ((size_t)r * 2 + c) * N + k));
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
         bool ok = true;
         for (int h = 0; h < 2 && ok; h++) {
             // build the key windows of this half (and, for h = 0, run ahead into h = 1)
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
                     break;
                 }
                 const int r = t / kstages, ks = t % kstages;
-                const uint32_t *q = keys + ((size_t)r * 2 + c) * N;
+                const uint32_t *q = key_s + (size_t)r * N;
                 const int U0 = P0 + ks * KS;
                 uint8_t *bs = b_st + s * B_STAGE_BYTES;
                 for (int v = tid; v < B_UNITS; v += 128) {
@@ -407,14 +416,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
                 mbar_arrive(&full_b[s]);
             }
             if (!ok) break;
-            // read-out of half h
+            // read-out of half h: chunk j holds columns idx = 32j..32j+31, i.e. the words
+            // n = nb..nb+31 (nb = c0 - 32j - 31, a multiple of 32) of this gate's row, word
+            // n = nb + w taking the sum of column 31 - w.  The old words of the next chunk
+            // are loaded before this chunk's TMEM values are needed.
+            uint4 cur[8];
+            const bool live = g < G;
+            if (live) {
+                const uint4 *src = (const uint4 *)(acc_row + (c0 - 31));
+#pragma unroll
+                for (int q = 0; q < 8; q++) cur[q] = src[q];
+            }
             if (!mbar_wait(&acc_full, h, abort, err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             const uint32_t lane_base = tmem + (((uint32_t)(warp * 32)) << 16);
+#pragma unroll 1
             for (int j = 0; j < NB / 32; j++) {
+                uint4 nxt[8];
+                if (live && j + 1 < NB / 32) {
+                    const uint4 *src = (const uint4 *)(acc_row + (c0 - 32 * (j + 1) - 31));
+#pragma unroll
+                    for (int q = 0; q < 8; q++) nxt[q] = src[q];
+                }
                 uint32_t sum[32];
 #pragma unroll
                 for (int e = 0; e < 32; e++) sum[e] = 0;
@@ -426,12 +452,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
                     for (int e = 0; e < 32; e++)
                         sum[e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
                 }
-                if (g < G) {
+                if (live) {
+                    uint4 *dst = (uint4 *)(acc_row + (c0 - 32 * j - 31));
 #pragma unroll
-                    for (int e = 0; e < 32; e++) {
-                        const int n = c0 - (j * 32 + e);
-                        acc_row[n] += sum[e];
+                    for (int q = 0; q < 8; q++) {
+                        uint4 o = cur[q];
+                        o.x += sum[31 - (4 * q + 0)];
+                        o.y += sum[31 - (4 * q + 1)];
+                        o.z += sum[31 - (4 * q + 2)];
+                        o.w += sum[31 - (4 * q + 3)];
+                        dst[q] = o;
                     }
+#pragma unroll
+                    for (int q = 0; q < 8; q++) cur[q] = nxt[q];
                 }
             }
             tc_fence_before();
@@ -456,7 +489,7 @@ struct TcWorkspace {
 int tfhe_tc_supported(const tfhe_ctx *ctx) {
     const tfhe_params &p = ctx->p;
     return p.N >= 256 && p.N <= 1024 && p.N % NB == 0 && p.N % KS == 0 && p.Bgbit <= 6 &&
-           (int64_t)p.l * p.N * 32 * 128 <= (1 << 24);
+           (int64_t)p.l * p.N * 32 * 128 <= (1 << 24) && 2 * p.l * p.N * 4 <= KEY_BYTES_MAX;
 }
 
 void tfhe_tc_free(tfhe_ctx *ctx) {
