@@ -317,8 +317,9 @@ def roofline(form, r, G, p):
     4 32-bit multiplies and 4 more for the high halves, so it is counted as 8 32-bit
     integer multiply instructions.  Peak = 148 SMs x 128 lanes x the max SM clock.
 
-    TC form: the tensor-core external product, bound by the bf16 tensor pipe: per gate
-    and step 2 * (2lN) * (2N) * planes flops (planes = 4 byte planes of the key).
+    TC form: the persistent tensor-core BlindRotate (one launch per level), bound by the
+    bf16 tensor pipe: per gate and step 2 * (2lN) * (2N) * planes flops (planes = 4 byte
+    planes of the key), n steps per launch.
     """
     mp, kind = peaks()
     logN = p.N.bit_length() - 1
@@ -337,13 +338,14 @@ def roofline(form, r, G, p):
     ms, launches = r["stages"]["extprod_tc"]
     per_launch_s = ms / 1e3 / max(launches, 1)
     planes = 4
-    flops = G * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
+    # one launch of k_tc_blind_rotate runs all n steps of the level
+    flops = G * steps * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
     achieved = flops / per_launch_s / 1e12
     peak = mp["bf16_tflops_sustained"]
-    return {"bound": "tensor", "kernel": "k_extprod_tc", "achieved": achieved, "peak": peak,
+    return {"bound": "tensor", "kernel": "k_tc_blind_rotate", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "peak_kind": f"{kind} bf16 sustained (cuBLAS loop)",
-            "work": f"2*(2lN)*(2N)*{planes} flops per gate per launch"}
+            "work": f"n*2*(2lN)*(2N)*{planes} flops per gate per launch (dense Toeplitz form)"}
 
 
 def main():

@@ -128,6 +128,8 @@ extern "C" int tfhe_ctx_set_keys(tfhe_ctx *ctx, const uint32_t *bsk, const uint3
     k_ksk_relayout<<<4096, 256, 0, st>>>(ksk, ctx->ksk, p.N, p.ks_t, base, p.n + 1, ctx->n_pad);
     rc = tfhe_check_launch(ctx, "ksk relayout");
     if (rc != TFHE_OK) return rc;
+    rc = tfhe_tc_prepare_keys(ctx, bsk, st);
+    if (rc != TFHE_OK) return rc;
     ctx->has_keys = true;
     return TFHE_OK;
 }

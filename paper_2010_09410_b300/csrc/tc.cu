@@ -21,12 +21,14 @@
 // descriptor reads row idx's 8-element core-matrix row at base + 16*idx and the next
 // 8 k's at +128 B, so LBO = SBO = 128 B walk the windows directly.
 //
-// Kernels per BlindRotate step: k_tc_digits (rotation X^{a} ACC - ACC and gadget
-// digits, written in the A-operand layout) then k_tc_extprod (tensor-core product,
-// ACC += Y).  Warp roles in k_tc_extprod (192 threads): warps 0-3 build the key
-// windows and read out TMEM (warp w owns TMEM lanes 32w..32w+31 = gates), warp 4
-// streams the digit tiles with cp.async.bulk, warp 5 allocates TMEM and one lane
-// issues the MMAs.  Every wait polls a bounded number of times; on time-out the block
+// The units of every key polynomial and byte plane (2N units of 16 B each) are expanded
+// once when the keys are loaded (k_tc_windows: 1 GB for the n = 630, N = 1024 BSK), so a
+// B stage is four contiguous bulk copies, like the digit (A) stage.
+//
+// The digits of X^{a_i} ACC - ACC are written per 128-gate tile in the A-operand layout:
+// [tile][row r < 2l][stage s < N/KS] blocks of 32 KB, each [mg < 16][kb < 16][m8 < 8]
+// [8 bf16] for gate m = 8 mg + m8 and digit index k = s*KS + 8 kb + e.  One launch of
+// k_tc_blind_rotate runs all n steps (see below).  Every wait polls a bounded number of times; on time-out the block
 // records TFHE_ETIMEOUT in the context's error word and winds down.
 #include "common.cuh"
 
@@ -41,9 +43,7 @@ constexpr int A_STAGE_BYTES = TILE_M * KS * 2;            // 32 KB
 constexpr int B_UNITS = NB + KS;                          // units per plane and stage
 constexpr int B_PLANE_BYTES = B_UNITS * 16;               // 4 KB
 constexpr int B_STAGE_BYTES = PLANES * B_PLANE_BYTES;     // 16 KB
-constexpr int KEY_BYTES_MAX = 6 * 1024 * 4;                // 2l x N key words (l*N <= 3072)
-constexpr int SMEM_BYTES = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + KEY_BYTES_MAX + 1024;
-constexpr int THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + 1024;
 constexpr long long WAIT_CYCLES = 4000000000LL;           // ~2 s at 2 GHz
 
 // ---- PTX wrappers ----------------------------------------------------------------
@@ -156,18 +156,17 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -187,66 +186,31 @@ __device__ __forceinline__ void byte_planes(uint32_t q, int (&pl)[PLANES]) {
     }
 }
 
-// r_vec[x] of the key polynomial q held in shared memory (zero past 2N: never read by
-// an MMA).
-__device__ __forceinline__ uint32_t rvec(const uint32_t *q, int N, int x) {
-    if (x < N) return q[N - 1 - x];
-    if (x < 2 * N) return 0u - q[2 * N - 1 - x];
+// r_vec[x] of the key polynomial q (zero past 2N: never read by an MMA).
+__device__ __forceinline__ uint32_t rvec(const uint32_t *__restrict__ q, int N, int x) {
+    if (x < N) return __ldg(q + (N - 1 - x));
+    if (x < 2 * N) return 0u - __ldg(q + (2 * N - 1 - x));
     return 0u;
 }
 
-// ---------------------------------------------------------------------------
-// Step kernel 1: digits of X^{a_g} ACC_g - ACC_g in the A-operand layout.
-// Layout of the digit buffer: [tile][row r < 2l][stage s < N/KS] blocks of 32 KB,
-// each block [mg < 16][kb < 16][m8 < 8][8 bf16]: gate m = 8 mg + m8 of the tile,
-// digit index k = s*KS + 8 kb + e.  One thread produces 8 consecutive k of one gate
-// and one polynomial (c) for all l digit rows.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_tc_digits(int N, int l, int Bgbit, int n1, int G,
-                                                   int step, const uint32_t *__restrict__ bar,
-                                                   const uint32_t *__restrict__ acc,
-                                                   uint4 *__restrict__ digits,
-                                                   const uint32_t *__restrict__ d1,
-                                                   const uint32_t *__restrict__ d0,
-                                                   const CmuxGeom *geom) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int kstages = N / KS;
-    // thread -> (tile, c, stage, kb, mg, m8), m8 fastest so 8 threads write 128 B
-    int t = tid;
-    const int m8 = t & 7; t >>= 3;
-    const int mg = t & 15; t >>= 4;
-    const int kb = t & 15; t >>= 4;
-    const int s = t % kstages; t /= kstages;
-    const int c = t & 1; t >>= 1;
-    const int tile = t;
-    const int ntiles = (G + TILE_M - 1) / TILE_M;
-    if (tile >= ntiles) return;
-    const int m = mg * 8 + m8;
-    const int g = tile * TILE_M + m;
-    const int k0 = s * KS + kb * 8;
-    uint32_t x[8];
-    if (g < G) {
-        const uint32_t *p = acc + (size_t)g * 2 * N + (size_t)c * N;
-        const int a = (int)(bar[(size_t)g * n1 + step] % (uint32_t)(2 * N));
-#pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = rot_coef(p, N, a, k0 + e) - p[k0 + e];
-    } else {
-#pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = 0;
-    }
-    const uint32_t off = gadget_offset(l, Bgbit);
-    for (int j = 0; j < l; j++) {
-        uint32_t w[4];
+// Window units of `npoly` key polynomials: win[(poly * 4 + p) * 2N + u] holds byte plane p
+// of r_vec[u .. u+7] as 8 bf16.  One block per polynomial.
+__global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, uint4 *__restrict__ win) {
+    const size_t poly = blockIdx.x;
+    const uint32_t *q = polys + poly * N;
+    for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
+        uint32_t w[PLANES][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            const uint32_t lo = bf16_bits(gadget_digit(x[e] + off, j + 1, Bgbit));
-            const uint32_t hi = bf16_bits(gadget_digit(x[e + 1] + off, j + 1, Bgbit));
-            w[e / 2] = lo | (hi << 16);
+            int pl0[PLANES], pl1[PLANES];
+            byte_planes(rvec(q, N, u + e), pl0);
+            byte_planes(rvec(q, N, u + e + 1), pl1);
+#pragma unroll
+            for (int p = 0; p < PLANES; p++) w[p][e / 2] = bf16_bits(pl0[p]) | (bf16_bits(pl1[p]) << 16);
         }
-        const int r = c * l + j;
-        const size_t blk = ((size_t)tile * 2 * l + r) * kstages + s;
-        digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
-            make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int p = 0; p < PLANES; p++)
+            win[(poly * PLANES + p) * 2 * N + u] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
     }
 }
 
@@ -267,45 +231,124 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Step kernel 2: ACC[tile gates][c][block columns] += sum over the 2l rows of digits x
-// Toeplitz(key), on the tensor cores.  blockIdx.x = gate tile, blockIdx.y = column
-// block (c = y / (N/NB), columns [b*NB, b*NB + NB)).
-// keys: the 2l x 2 key polynomials of this step, key(r, c) = keys + (r*2 + c)*N.
+// Persistent BlindRotate: all n steps in one launch, one block per SM.
+//
+// Jobs: D(i, gt, part) writes the digits of gates 8*part .. 8*part+7 of gate tile gt for
+// step i (16 parts per tile); E(i, gt, cb) is the tensor-core product of column block
+// cb (ACC += Y).  Order: all D(0, ., .), then for each step i and tile gt:
+// E(i, gt, 0..cbs-1) followed by D(i+1, gt, 0..15).  Blocks take jobs from a global
+// counter, so a job only ever waits for jobs with smaller indices, which running
+// blocks hold: E(i, gt, .) waits for done_D[gt] >= 16 (i+1); D(i+1, gt, .) waits for
+// done_E[gt] >= cbs (i+1).  Every wait is bounded.
+//
+// Warp roles (320 threads): warps 0-3 read TMEM out (warp w owns lanes 32w..32w+31),
+// warp 4 fetches jobs and streams stages with cp.async.bulk, warp 5 owns TMEM and one
+// lane issues the MMAs, warps 6-9 compute digits.  The four planes of TMEM are handed
+// back one by one after each K-half's read-out, so the next half's MMAs on plane p start
+// as soon as plane p has been read; both halves of a job accumulate in registers and the
+// accumulator row is updated once per job.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
-                                                           const uint4 *__restrict__ digits,
-                                                           const uint32_t *__restrict__ keys,
-                                                           uint32_t *__restrict__ acc, int *err) {
+constexpr int P_THREADS = 320;
+constexpr int JQ = 8;  // job ring depth
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_count(const uint32_t *p, uint32_t target, volatile int *abort,
+                                           int *err) {
+    const long long t0 = clock64();
+    while (ld_acquire(p) < target) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort = 1;
+            atomicCAS(err, 0, TFHE_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
+
+struct BrArgs {
+    int N, l, Bgbit, G, n, n1;
+    int tiles, cbs;             // gate tiles, column blocks (2N / NB)
+    long long total_jobs;
+    const uint32_t *bar;        // [G][n+1]
+    uint32_t *acc;              // [G][2][N]
+    uint4 *digits;              // [tiles][2l][N/KS] x 32 KB
+    const uint4 *win;           // [n][2l][2][4][2N] units
+    uint32_t *sync;             // [0] job counter, [1 .. tiles] done_D, [1+tiles ..] done_E
+    int *err;
+};
+
+struct Job {
+    int kind;  // 0 = stop, 1 = digits D(i, gt, part), 2 = product E(i, gt, cb)
+    int i, gt, sub;
+};
+
+__device__ __forceinline__ Job decode_job(const BrArgs &a, int job) {
+    Job J{0, 0, 0, 0};
+    if (job < 0) return J;
+    const int d0 = a.tiles * DPARTS;
+    if (job < d0) {
+        J.kind = 1; J.i = 0; J.gt = job / DPARTS; J.sub = job % DPARTS;
+        return J;
+    }
+    int j = job - d0;
+    const int per = a.tiles * (a.cbs + DPARTS);
+    int i = j / per;
+    if (i < a.n - 1) {
+        j %= per;
+        J.gt = j / (a.cbs + DPARTS);
+        const int x = j % (a.cbs + DPARTS);
+        if (x < a.cbs) { J.kind = 2; J.i = i; J.sub = x; }
+        else { J.kind = 1; J.i = i + 1; J.sub = x - a.cbs; }
+        return J;
+    }
+    j -= (a.n - 1) * per;  // last step: products only
+    J.kind = 2; J.i = a.n - 1; J.gt = j / a.cbs; J.sub = j % a.cbs;
+    return J;
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *a_st = smem;                                   // STAGES x 32 KB
-    uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;          // STAGES x 16 KB
-    uint32_t *key_s = (uint32_t *)(b_st + STAGES * B_STAGE_BYTES);  // [2l][N], column c
-    __shared__ __align__(8) uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
-    __shared__ __align__(8) uint64_t acc_full, acc_empty, drain;
+    uint8_t *a_st = smem;
+    uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    __shared__ __align__(8) uint64_t acc_full, acc_empty[PLANES], drain;
+    __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
+    __shared__ int jobs[JQ];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x;
-    const int blocks_per_poly = N / NB;
-    const int c = blockIdx.y / blocks_per_poly;
-    const int bcol = blockIdx.y % blocks_per_poly;
-    const int c0 = bcol * NB + NB - 1;    // highest output column of the block
-    const int P0 = N - 1 - c0;
+    const int N = a.N, l = a.l;
     const int kstages = N / KS;
-    const int half_stages = l * kstages;  // stages per K-half (one polynomial's l rows)
+    const int half_stages = l * kstages;
     const int total_stages = 2 * half_stages;
+    const long long total_jobs = a.total_jobs;
+    uint32_t *job_counter = a.sync;
+    uint32_t *done_D = a.sync + 1;
+    uint32_t *done_E = a.sync + 1 + a.tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
-            mbar_init(&full_a[s], 1);
-            mbar_init(&full_b[s], 128);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, 128);
+        for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], 128);
         mbar_init(&drain, 1);
+        for (int q = 0; q < JQ; q++) {
+            mbar_init(&job_full[q], 1);
+            mbar_init(&job_empty[q], 3);  // MMA lane, read-out leader, digit leader
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -321,154 +364,238 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abort = &abort_flag;
+    int *err = a.err;
 
     if (warp == 4) {
-        // ---- digit tiles: one 32 KB bulk copy per stage ----
+        // ---- job fetch + stage loads ----
         if (lane == 0) {
-            int issued = 0;
-            for (int t = 0; t < total_stages; t++) {
-                const int s = t % STAGES;
-                if (t >= STAGES && !mbar_wait(&empty[s], ((t / STAGES) - 1) & 1, abort, err)) break;
-                const int r = t / kstages, ks = t % kstages;
-                const size_t blk = ((size_t)tile * 2 * l + r) * kstages + ks;
-                mbar_arrive_tx(&full_a[s], A_STAGE_BYTES);
-                bulk_g2s(a_st + s * A_STAGE_BYTES, digits + blk * (A_STAGE_BYTES / 16),
-                         A_STAGE_BYTES, &full_a[s]);
-                issued = t + 1;
+            int t_global = 0, issued = 0;
+            for (int q = 0;; q++) {
+                const int slot = q % JQ;
+                if (q >= JQ && !mbar_wait(&job_empty[slot], ((q / JQ) - 1) & 1, abort, err)) break;
+                const unsigned j = atomicAdd(job_counter, 1u);
+                const int job = (long long)j < total_jobs ? (int)j : -1;
+                jobs[slot] = job;
+                mbar_arrive(&job_full[slot]);
+                if (job < 0) break;
+                const Job J = decode_job(a, job);
+                if (J.kind != 2) continue;  // digit job: nothing to load
+                const int i = J.i, gt = J.gt, cb = J.sub;
+                const int c = cb / (N / NB), bcol = cb % (N / NB);
+                const int P0 = N - NB - bcol * NB;
+                if (!wait_count(&done_D[gt], (uint32_t)(DPARTS * (i + 1)), abort, err)) break;
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                const uint4 *win = a.win + (size_t)i * (2 * l * 2) * PLANES * 2 * N;
+                bool ok = true;
+                for (int ts = 0; ts < total_stages; ts++, t_global++) {
+                    const int s = t_global % STAGES;
+                    if (t_global >= STAGES &&
+                        !mbar_wait(&empty[s], ((t_global / STAGES) - 1) & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const int r = ts / kstages, ks = ts % kstages;
+                    const size_t blk = ((size_t)gt * 2 * l + r) * kstages + ks;
+                    mbar_arrive_tx(&full[s], A_STAGE_BYTES + B_STAGE_BYTES);
+                    bulk_g2s(a_st + s * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
+                             A_STAGE_BYTES, &full[s]);
+                    const uint4 *wsrc = win + ((size_t)(r * 2 + c) * PLANES) * 2 * N + (P0 + ks * KS);
+#pragma unroll
+                    for (int p = 0; p < PLANES; p++)
+                        bulk_g2s(b_st + s * B_STAGE_BYTES + p * B_PLANE_BYTES,
+                                 wsrc + (size_t)p * 2 * N, B_PLANE_BYTES, &full[s]);
+                    issued = t_global + 1;
+                }
+                if (!ok) break;
             }
-            // let this block's last copies land before it can exit
             for (int t = issued - STAGES; t < issued; t++)
-                if (t >= 0) mbar_wait_settle(&full_a[t % STAGES], (t / STAGES) & 1);
+                if (t >= 0) mbar_wait_settle(&full[t % STAGES], (t / STAGES) & 1);
         }
     } else if (warp == 5) {
         // ---- MMA issue ----
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc(TILE_M, NB);
-            for (int t = 0; t < total_stages; t++) {
-                const int s = t % STAGES;
-                const uint32_t par = (t / STAGES) & 1;
-                if (t == half_stages && !mbar_wait(&acc_empty, 0, abort, err)) break;
-                if (!mbar_wait(&full_a[s], par, abort, err)) break;
-                if (!mbar_wait(&full_b[s], par, abort, err)) break;
-                tc_fence_after();
-                const uint32_t a_addr = smem_u32(a_st + s * A_STAGE_BYTES);
-                const uint32_t b_addr = smem_u32(b_st + s * B_STAGE_BYTES);
-                const bool first = (t % half_stages) == 0;
+            int t_global = 0, khalf = 0;
+            bool ok = true;
+            for (int q = 0; ok; q++) {
+                const int slot = q % JQ;
+                if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+                const int job = jobs[slot];
+                mbar_arrive(&job_empty[slot]);
+                if (job < 0) break;
+                if (decode_job(a, job).kind != 2) continue;  // digit job
+                for (int ts = 0; ts < total_stages && ok; ts++, t_global++) {
+                    const int s = t_global % STAGES;
+                    if (!mbar_wait(&full[s], (t_global / STAGES) & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(a_st + s * A_STAGE_BYTES);
+                    const uint32_t b_addr = smem_u32(b_st + s * B_STAGE_BYTES);
+                    if (ts % half_stages == 0) {
+                        // first stage of a half: plane p starts once its previous contents
+                        // have been read out
 #pragma unroll
-                for (int kk = 0; kk < KS / 16; kk++) {
-                    const uint64_t ad = make_desc(a_addr + kk * 256, 128, 2048);
+                        for (int p = 0; p < PLANES; p++) {
+                            if (khalf > 0 && !mbar_wait(&acc_empty[p], (khalf - 1) & 1, abort, err)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
 #pragma unroll
-                    for (int p = 0; p < PLANES; p++) {
-                        const uint64_t bd = make_desc(b_addr + p * B_PLANE_BYTES + kk * 256, 128, 128);
-                        mma_bf16(tmem + p * NB, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                            for (int kk = 0; kk < KS / 16; kk++)
+                                mma_bf16(tmem + p * NB, make_desc(a_addr + kk * 256, 128, 2048),
+                                         make_desc(b_addr + p * B_PLANE_BYTES + kk * 256, 128, 128),
+                                         idesc, kk == 0 ? 0u : 1u);
+                        }
+                        if (!ok) break;
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < KS / 16; kk++) {
+                            const uint64_t ad = make_desc(a_addr + kk * 256, 128, 2048);
+#pragma unroll
+                            for (int p = 0; p < PLANES; p++)
+                                mma_bf16(tmem + p * NB, ad,
+                                         make_desc(b_addr + p * B_PLANE_BYTES + kk * 256, 128, 128),
+                                         idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if ((ts + 1) % half_stages == 0) {
+                        mma_commit(&acc_full);
+                        khalf++;
                     }
                 }
-                mma_commit(&empty[s]);
-                if ((t + 1) % half_stages == 0) mma_commit(&acc_full);
             }
-            // drain: wait until every MMA issued above has finished with TMEM
             mma_commit(&drain);
             mbar_wait_settle(&drain, 0);
         }
-    } else {
-        // ---- warps 0-3: key windows, then TMEM read-out per K-half ----
-        const int tid = threadIdx.x;  // 0..127, also the TMEM lane = gate of the tile
-        const int g = tile * TILE_M + tid;
-        uint32_t *acc_row = acc + (size_t)g * 2 * N + (size_t)c * N;
-        // the 2l key polynomials of column c, into shared memory (named barrier 1 = warps 0-3)
-        for (int w = tid; w < 2 * l * N / 4; w += 128) {
-            const int r = (w * 4) / N, k = (w * 4) % N;
-            *(uint4 *)(key_s + r * N + k) = __ldg((const uint4 *)(keys + ((size_t)r * 2 + c) * N + k));
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        bool ok = true;
-        for (int h = 0; h < 2 && ok; h++) {
-            // build the key windows of this half (and, for h = 0, run ahead into h = 1)
-            const int t_begin = (h == 0) ? 0 : half_stages + STAGES;
-            const int t_end = (h == 0) ? min(total_stages, half_stages + STAGES) : total_stages;
-            for (int t = t_begin; t < t_end && ok; t++) {
-                const int s = t % STAGES;
-                if (t >= STAGES && !mbar_wait(&empty[s], ((t / STAGES) - 1) & 1, abort, err)) {
+    } else if (warp < 4) {
+        // ---- TMEM read-out: thread = TMEM lane = gate of the tile ----
+        const int tid = threadIdx.x;
+        const uint32_t lane_base = tmem + (((uint32_t)(warp * 32)) << 16);
+        int khalf = 0;
+        for (int q = 0;; q++) {
+            const int slot = q % JQ;
+            if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+            const int job = jobs[slot];
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (tid == 0) mbar_arrive(&job_empty[slot]);
+            if (job < 0) break;
+            const Job J = decode_job(a, job);
+            if (J.kind != 2) continue;
+            const int i = J.i, gt = J.gt, cb = J.sub;
+            const int c = cb / (N / NB), bcol = cb % (N / NB);
+            const int c0 = bcol * NB + NB - 1;
+            uint32_t sum[NB];
+#pragma unroll
+            for (int e = 0; e < NB; e++) sum[e] = 0;
+            bool ok = true;
+            for (int h = 0; h < 2 && ok; h++, khalf++) {
+                if (!mbar_wait(&acc_full, khalf & 1, abort, err)) {
                     ok = false;
                     break;
                 }
-                const int r = t / kstages, ks = t % kstages;
-                const uint32_t *q = key_s + (size_t)r * N;
-                const int U0 = P0 + ks * KS;
-                uint8_t *bs = b_st + s * B_STAGE_BYTES;
-                for (int v = tid; v < B_UNITS; v += 128) {
-                    uint32_t w[PLANES][4];
-#pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        int pl0[PLANES], pl1[PLANES];
-                        byte_planes(rvec(q, N, U0 + v + e), pl0);
-                        byte_planes(rvec(q, N, U0 + v + e + 1), pl1);
-#pragma unroll
-                        for (int p = 0; p < PLANES; p++)
-                            w[p][e / 2] = bf16_bits(pl0[p]) | (bf16_bits(pl1[p]) << 16);
-                    }
-#pragma unroll
-                    for (int p = 0; p < PLANES; p++)
-                        *(uint4 *)(bs + p * B_PLANE_BYTES + v * 16) =
-                            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-                }
-                fence_proxy_async();
-                mbar_arrive(&full_b[s]);
-            }
-            if (!ok) break;
-            // read-out of half h: chunk j holds columns idx = 32j..32j+31, i.e. the words
-            // n = nb..nb+31 (nb = c0 - 32j - 31, a multiple of 32) of this gate's row, word
-            // n = nb + w taking the sum of column 31 - w.  The old words of the next chunk
-            // are loaded before this chunk's TMEM values are needed.
-            uint4 cur[8];
-            const bool live = g < G;
-            if (live) {
-                const uint4 *src = (const uint4 *)(acc_row + (c0 - 31));
-#pragma unroll
-                for (int q = 0; q < 8; q++) cur[q] = src[q];
-            }
-            if (!mbar_wait(&acc_full, h, abort, err)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t lane_base = tmem + (((uint32_t)(warp * 32)) << 16);
-#pragma unroll 1
-            for (int j = 0; j < NB / 32; j++) {
-                uint4 nxt[8];
-                if (live && j + 1 < NB / 32) {
-                    const uint4 *src = (const uint4 *)(acc_row + (c0 - 32 * (j + 1) - 31));
-#pragma unroll
-                    for (int q = 0; q < 8; q++) nxt[q] = src[q];
-                }
-                uint32_t sum[32];
-#pragma unroll
-                for (int e = 0; e < 32; e++) sum[e] = 0;
+                tc_fence_after();
 #pragma unroll
                 for (int p = 0; p < PLANES; p++) {
-                    uint32_t v[32];
-                    tmem_ld32(lane_base + p * NB + j * 32, v);
 #pragma unroll
-                    for (int e = 0; e < 32; e++)
-                        sum[e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
-                }
-                if (live) {
-                    uint4 *dst = (uint4 *)(acc_row + (c0 - 32 * j - 31));
+                    for (int j = 0; j < NB / 16; j += 2) {
+                        uint32_t v[32];
+                        tmem_ld16(lane_base + p * NB + j * 16, v);
+                        tmem_ld16(lane_base + p * NB + (j + 1) * 16, v + 16);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        uint4 o = cur[q];
-                        o.x += sum[31 - (4 * q + 0)];
-                        o.y += sum[31 - (4 * q + 1)];
-                        o.z += sum[31 - (4 * q + 2)];
-                        o.w += sum[31 - (4 * q + 3)];
-                        dst[q] = o;
+                        for (int e = 0; e < 32; e++)
+                            sum[j * 16 + e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
                     }
-#pragma unroll
-                    for (int q = 0; q < 8; q++) cur[q] = nxt[q];
+                    tc_fence_before();
+                    mbar_arrive(&acc_empty[p]);
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&acc_empty);
+            if (!ok) break;
+            // ACC row update: word n = c0 - idx receives column idx.  The leader's acquire of
+            // done_D (already satisfied) orders these accesses after the previous step's
+            // updates of the same words by other blocks.
+            if (tid == 0) wait_count(&done_D[gt], (uint32_t)(DPARTS * (i + 1)), abort, err);
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int g = gt * TILE_M + tid;
+            if (g < a.G) {
+                uint4 *row = (uint4 *)(a.acc + (size_t)g * 2 * N + (size_t)c * N + (c0 - NB + 1));
+#pragma unroll
+                for (int q4 = 0; q4 < NB / 4; q4++) {
+                    uint4 o = row[q4];
+                    o.x += sum[NB - 1 - (4 * q4 + 0)];
+                    o.y += sum[NB - 1 - (4 * q4 + 1)];
+                    o.z += sum[NB - 1 - (4 * q4 + 2)];
+                    o.w += sum[NB - 1 - (4 * q4 + 3)];
+                    row[q4] = o;
+                }
+            }
+            __threadfence();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (tid == 0) atomicAdd(&done_E[gt], 1u);
+        }
+    } else {
+        // ---- warps 6-9: digit jobs ----
+        const int tid = threadIdx.x - 192;
+        const uint32_t off = gadget_offset(l, a.Bgbit);
+        for (int q = 0;; q++) {
+            const int slot = q % JQ;
+            if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+            const int job = jobs[slot];
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (tid == 0) mbar_arrive(&job_empty[slot]);
+            if (job < 0) break;
+            const Job J = decode_job(a, job);
+            if (J.kind != 1) continue;
+            const int i = J.i, gt = J.gt, mg = J.sub;
+            if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.cbs * i), abort, err);
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (*abort) break;
+            // items of this part: (c, stage s, kb, m8), m8 fastest so 8 threads write 128 B
+            const int items = 2 * kstages * 16 * 8;
+#pragma unroll 4
+            for (int it = tid; it < items; it += 128) {
+                int t = it;
+                const int m8 = t & 7; t >>= 3;
+                const int kb = t & 15; t >>= 4;
+                const int s = t % kstages;
+                const int c = t / kstages;
+                const int g = gt * TILE_M + mg * 8 + m8;
+                const int k0 = s * KS + kb * 8;
+                uint32_t xv[8];
+                if (g < a.G) {
+                    const uint32_t *pr = a.acc + (size_t)g * 2 * N + (size_t)c * N;
+                    const int rot = (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N));
+                    const uint4 own0 = *(const uint4 *)(pr + k0);
+                    const uint4 own1 = *(const uint4 *)(pr + k0 + 4);
+                    const uint32_t own[8] = {own0.x, own0.y, own0.z, own0.w,
+                                             own1.x, own1.y, own1.z, own1.w};
+#pragma unroll
+                    for (int e = 0; e < 8; e++) xv[e] = rot_coef(pr, N, rot, k0 + e) - own[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; e++) xv[e] = 0;
+                }
+                for (int jd = 0; jd < l; jd++) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const uint32_t lo = bf16_bits(gadget_digit(xv[e] + off, jd + 1, a.Bgbit));
+                        const uint32_t hi = bf16_bits(gadget_digit(xv[e + 1] + off, jd + 1, a.Bgbit));
+                        w[e / 2] = lo | (hi << 16);
+                    }
+                    const int r = c * l + jd;
+                    const size_t blk = ((size_t)gt * 2 * l + r) * kstages + s;
+                    a.digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            __threadfence();
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (tid == 0) atomicAdd(&done_D[gt], 1u);
         }
     }
     tc_fence_before();
@@ -484,17 +611,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_extprod(int N, int l, int G,
 struct TcWorkspace {
     uint4 *digits = nullptr;
     size_t digits_cap = 0;  // bytes
+    uint4 *win = nullptr;   // BSK window units, [n][2l][2][4 planes][2N]
+    uint32_t *sync = nullptr;  // job counter and per-tile progress counters
+    size_t sync_cap = 0;       // words
+    int sms = 0;
 };
 
 int tfhe_tc_supported(const tfhe_ctx *ctx) {
     const tfhe_params &p = ctx->p;
     return p.N >= 256 && p.N <= 1024 && p.N % NB == 0 && p.N % KS == 0 && p.Bgbit <= 6 &&
-           (int64_t)p.l * p.N * 32 * 128 <= (1 << 24) && 2 * p.l * p.N * 4 <= KEY_BYTES_MAX;
+           (int64_t)p.l * p.N * 32 * 128 <= (1 << 24);
 }
 
 void tfhe_tc_free(tfhe_ctx *ctx) {
     if (!ctx->tc) return;
     if (ctx->tc->digits) cudaFree(ctx->tc->digits);
+    if (ctx->tc->win) cudaFree(ctx->tc->win);
+    if (ctx->tc->sync) cudaFree(ctx->tc->sync);
     delete ctx->tc;
     ctx->tc = nullptr;
 }
@@ -503,6 +636,15 @@ static int ensure_digits(tfhe_ctx *ctx, int G) {
     if (!ctx->tc) ctx->tc = new TcWorkspace();
     const size_t tiles = (size_t)(G + TILE_M - 1) / TILE_M;
     const size_t bytes = tiles * 2 * ctx->p.l * ctx->p.N * TILE_M * 2;
+    const size_t words = 1 + 2 * tiles;
+    if (words > ctx->tc->sync_cap) {
+        if (ctx->tc->sync) cudaFree(ctx->tc->sync);
+        ctx->tc->sync = nullptr;
+        ctx->tc->sync_cap = 0;
+        if (cudaMalloc(&ctx->tc->sync, words * 4) != cudaSuccess)
+            return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core progress counters");
+        ctx->tc->sync_cap = words;
+    }
     if (bytes <= ctx->tc->digits_cap) return TFHE_OK;
     if (ctx->tc->digits) cudaFree(ctx->tc->digits);
     ctx->tc->digits = nullptr;
@@ -513,17 +655,29 @@ static int ensure_digits(tfhe_ctx *ctx, int G) {
     return TFHE_OK;
 }
 
+// Expand the window units of the whole BSK (called when the keys are loaded).
+int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st) {
+    if (!tfhe_tc_supported(ctx)) return TFHE_OK;
+    const tfhe_params &p = ctx->p;
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    const size_t npoly = (size_t)p.n * 2 * p.l * 2;
+    if (!ctx->tc->win &&
+        cudaMalloc(&ctx->tc->win, npoly * PLANES * 2 * p.N * sizeof(uint4)) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core key windows");
+    k_tc_windows<<<(unsigned)npoly, 256, 0, st>>>(bsk, p.N, ctx->tc->win);
+    return tfhe_check_launch(ctx, "tc_windows");
+}
+
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                          cudaStream_t st) {
     const tfhe_params &p = ctx->p;
     if (G == 0) return TFHE_OK;
     if (!tfhe_tc_supported(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
+    if (!ctx->tc || !ctx->tc->win)
+        return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
     int rc = ensure_digits(ctx, G);
     if (rc != TFHE_OK) return rc;
-    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_extprod,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            SMEM_BYTES));
     const int n1 = p.n + 1;
     {
         const size_t total = (size_t)G * 2 * p.N;
@@ -532,28 +686,38 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         if (rc != TFHE_OK) return rc;
     }
     const int tiles = (G + TILE_M - 1) / TILE_M;
-    const size_t dig_threads = (size_t)tiles * 2 * (p.N / KS) * 16 * 16 * 8;
-    const unsigned dig_blocks = (unsigned)((dig_threads + 255) / 256);
-    const dim3 grid(tiles, 2 * p.N / NB);
-    const size_t per = (size_t)2 * p.l * 2 * p.N;
-    for (int i = 0; i < p.n; i++) {
-        {
-            StageTimer tm(ctx, TFHE_STAGE_DECOMPOSE_TC, st);
-            k_tc_digits<<<dig_blocks, 256, 0, st>>>(p.N, p.l, p.Bgbit, n1, G, i, bar, acc,
-                                                    ctx->tc->digits, nullptr, nullptr, nullptr);
-            tm.stop();
-        }
-        {
-            StageTimer tm(ctx, TFHE_STAGE_EXTPROD_TC, st);
-            k_tc_extprod<<<grid, THREADS, SMEM_BYTES, st>>>(p.N, p.l, G, ctx->tc->digits,
-                                                            ctx->bsk_raw + (size_t)i * per, acc,
-                                                            ctx->d_err);
-            tm.stop();
-        }
-        rc = tfhe_check_launch(ctx, "tc step");
-        if (rc != TFHE_OK) return rc;
+    if (!ctx->tc->sms) {
+        int sms = 0;
+        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        ctx->tc->sms = sms;
     }
-    return TFHE_OK;
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_blind_rotate,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            SMEM_BYTES));
+    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->tc->sync, 0, (1 + 2 * (size_t)tiles) * 4, st));
+    BrArgs args;
+    args.N = p.N;
+    args.l = p.l;
+    args.Bgbit = p.Bgbit;
+    args.G = G;
+    args.n = p.n;
+    args.n1 = n1;
+    args.tiles = tiles;
+    args.cbs = 2 * p.N / NB;
+    args.bar = bar;
+    args.acc = acc;
+    args.digits = ctx->tc->digits;
+    args.win = ctx->tc->win;
+    args.sync = ctx->tc->sync;
+    args.err = ctx->d_err;
+    args.total_jobs = (long long)tiles * DPARTS +
+                      (long long)(p.n - 1) * tiles * (args.cbs + DPARTS) + (long long)tiles * args.cbs;
+    const long long jobs = args.total_jobs;
+    const int grid = (int)(jobs < ctx->tc->sms ? jobs : ctx->tc->sms);
+    StageTimer tm(ctx, TFHE_STAGE_EXTPROD_TC, st);
+    k_tc_blind_rotate<<<grid, P_THREADS, SMEM_BYTES, st>>>(args);
+    tm.stop();
+    return tfhe_check_launch(ctx, "tc blind rotate");
 }
 
 int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *, const CmuxGeom &, cudaStream_t) {
