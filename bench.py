@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--form", default="best", choices=["best", "ntt", "tc"])
     ap.add_argument("--gates", type=int, default=GATES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-level", type=int, default=-1,
+                    help="Karatsuba levels of the tensor-core form (-1: library default)")
     return ap.parse_args()
 
 
@@ -179,6 +181,8 @@ def run_ours(args):
     ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
                  torch.from_numpy(k.ksk.view(np.int32)).cuda())
     ctx.reserve(args.gates)
+    if args.tc_level >= 0:
+        ctx.set_tc_level(args.tc_level)
     ctx.sync()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(
         np.int32 if a.dtype == np.uint32 else a.dtype)).cuda()

@@ -115,6 +115,14 @@ int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates);
  * device error word. */
 int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
 
+/* Karatsuba levels of the tensor-core form (0, 1 or 2; -1 selects the default: 1 for
+ * N >= 512, else 0).  Level L computes each negacyclic product as 3^L Toeplitz products of
+ * size N / 2^L (3/4 of the multiply-adds per level); results are identical for every
+ * level.  Needs N / 2^L >= 128.  If keys are loaded, re-expands the key windows on the
+ * legacy default stream.  TFHE_EUNSUPPORTED if the tensor-core form or level is not
+ * available for these parameters. */
+int tfhe_ctx_set_tc_level(tfhe_ctx *ctx, int levels);
+
 /* Per-kernel timing (tracing).  When enabled, the context brackets each of its kernel
  * launches with CUDA events on the launching stream (not while the stream is being
  * captured into a graph).  tfhe_ctx_stage_times waits for the recorded events, writes

@@ -33,6 +33,7 @@ EXPORTS = [
     "tfhe_cmux_tree_read", "tfhe_ram_write", "tfhe_circuit_plan", "tfhe_plan_num_levels",
     "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_destroy",
     "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times", "tfhe_gate_batch_noalloc",
+    "tfhe_ctx_set_tc_level",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "decompose_tc", "extprod_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -85,6 +86,7 @@ def lib():
         "tfhe_ctx_enable_timing": (i32, [vp, i32]),
         "tfhe_ctx_stage_times": (i32, [vp, vp, vp]),
         "tfhe_gate_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, i32, vp]),
+        "tfhe_ctx_set_tc_level": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -143,6 +145,10 @@ class Context:
     def set_keys(self, bsk, ksk, stream=None):
         self._check(lib().tfhe_ctx_set_keys(self.h, _ptr(bsk), _ptr(ksk), _stream(stream)),
                     "set_keys")
+
+    def set_tc_level(self, levels: int):
+        """Karatsuba levels of the tensor-core form (0, 1, 2; -1 = default)."""
+        self._check(lib().tfhe_ctx_set_tc_level(self.h, levels), "set_tc_level")
 
     def enable_timing(self, on: bool = True):
         self._check(lib().tfhe_ctx_enable_timing(self.h, 1 if on else 0), "enable_timing")

@@ -106,6 +106,7 @@ int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc
 // tc.cu
 int tfhe_tc_supported(const tfhe_ctx *ctx);
 int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st);
+int tfhe_tc_set_level(tfhe_ctx *ctx, int level);
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                          cudaStream_t st);
 int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);

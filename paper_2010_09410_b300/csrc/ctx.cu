@@ -239,3 +239,9 @@ extern "C" int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches
     }
     return rc;
 }
+
+extern "C" int tfhe_ctx_set_tc_level(tfhe_ctx *ctx, int levels) {
+    if (!ctx) return TFHE_EINVAL;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return tfhe_tc_set_level(ctx, levels);
+}

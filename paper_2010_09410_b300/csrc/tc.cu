@@ -1,35 +1,45 @@
-// tc.cu -- the tensor-core form of BlindRotate (and of batched CMUXes).
+// tc.cu -- the tensor-core form of BlindRotate.
 //
-// One BlindRotate step over a tile of 128 gates is the dense contraction
-//   Y[g][c][n] = sum_{r < 2l} sum_{k < N} D_g[r][k] * T_{r,c}[n][k]   (mod 2^32)
-// of the gadget digits D (|d| <= Bg/2 <= 32) by the negacyclic Toeplitz matrices of the
-// key polynomials q = BSK_i[r][c]: T[n][k] = q[n-k] for n >= k, -q[n-k+N] otherwise.
+// One BlindRotate step over a tile of 128 gates is a dense contraction of the gadget
+// digits D (|d| <= Bg/2 <= 32) by the negacyclic Toeplitz matrices of the key
+// polynomials q = BSK_i[r][c] (T[n][k] = q[n-k] for n >= k, -q[n-k+N] otherwise):
+//   Y[g][c][n] = sum_{r < 2l} sum_{k < N} D_g[r][k] * T_{r,c}[n][k]   (mod 2^32).
 // It runs on the sm_103a tensor cores (tcgen05.mma kind::f16, bf16 operands, fp32
-// accumulators in TMEM).  bf16 holds the digits and signed byte planes of the key
-// (q = sum_p 2^{8p} q_p, q_p in [-128, 128)) exactly; one K-half covers the l rows of one
-// polynomial of the TRLWE (l*N <= 4096 terms), so every partial sum is an integer below
-// l*N*32*128 <= 2^24 and the fp32 accumulation is exact.  Each half is read out of TMEM,
+// accumulators in TMEM).  bf16 holds small integers exactly: the (combined) digits and
+// the signed byte planes of the key, q = sum_p 2^{8p} q_p with q_p in [-128, 128).  Each
+// accumulation covers the l rows of one polynomial of the TRLWE and is read out of TMEM,
 // rounded to int32 and recombined mod 2^32 as sum_p 2^{8p} Y_p.
 //
-// The Toeplitz operand is never materialised.  Row n of T (as a function of k) is the
-// window r_vec[N-1-n+k] of one vector of length 2N,
-//   r_vec[x] = q[N-1-x]  (x < N),   r_vec[x] = -q[2N-1-x]  (N <= x < 2N).
-// Shared memory holds "units": unit u is the 16 bytes r_vec[u .. u+7] (one byte plane,
-// bf16).  For an output block n in [c0-NB+1, c0] (column idx = c0 - n) and digits
-// k in [k0, k0+KS), the element (idx, k) is r_vec[P0 + idx + k] with P0 = N-1-c0, i.e.
-// element t of unit (P0 + k0) + idx + (k - k0 - t).  A K-major, no-swizzle UMMA
-// descriptor reads row idx's 8-element core-matrix row at base + 16*idx and the next
-// 8 k's at +128 B, so LBO = SBO = 128 B walk the windows directly.
+// Karatsuba terms.  A negacyclic matrix of size N has the block form [[A, -B], [B, A]]
+// with Toeplitz halves A, B, so y = T x is y0 = P1 - P3, y1 = P1 + P2 with the three
+// half-size products P1 = (A+B) x0, P2 = A (x1 - x0), P3 = B (x0 + x1).  A Toeplitz
+// product splits the same way ([[T00, T01], [T10, T00]]: P = T00 (x0 + x1),
+// y0 = P + (T01 - T00) x1, y1 = P + (T10 - T00) x0).  After L levels a step is 3^L
+// Toeplitz products of size s = N / 2^L, each with a signed combination of digit blocks
+// (|x| <= 32 * 2^L), a key generator that is a signed sum of shifted key segments, and
+// signed output blocks; the host builds this plan (build_plan).  Every accumulation
+// then sums l*s terms below 32 * 2^L * 128 = l*N*32*128 <= 2^24, so it stays exact.
 //
-// The units of every key polynomial and byte plane (2N units of 16 B each) are expanded
-// once when the keys are loaded (k_tc_windows: 1 GB for the n = 630, N = 1024 BSK), so a
-// B stage is four contiguous bulk copies, like the digit (A) stage.
+// The Toeplitz operand is never materialised.  Row n' of a size-s Toeplitz matrix with
+// generator t (T[n'][k'] = t[n'-k']) is the window r_vec[s-1-n'+k'] of
+// r_vec[x] = t[s-1-x] (x < 2s-1, zero beyond).  Shared memory holds "units": unit u is
+// the 16 bytes r_vec[u .. u+7] of one byte plane (bf16).  For an output block n' in
+// [c0-NB+1, c0] (column idx = c0 - n') and digits k' in [k0, k0+KS), element (idx, k')
+// is r_vec[P0 + idx + k'] with P0 = s-1-c0, i.e. element t of unit (P0 + k0) + idx +
+// (k' - k0 - t).  A K-major, no-swizzle UMMA descriptor reads row idx's 8-element
+// core-matrix row at base + 16*idx and the next 8 k's at +128 B, so LBO = SBO = 128 B
+// walk the windows directly.  The units of every step, term, key polynomial and plane
+// are expanded once when the keys are loaded (k_tc_windows), so a key (B) stage is four
+// contiguous bulk copies, like the digit (A) stage.
 //
-// The digits of X^{a_i} ACC - ACC are written per 128-gate tile in the A-operand layout:
-// [tile][row r < 2l][stage s < N/KS] blocks of 32 KB, each [mg < 16][kb < 16][m8 < 8]
-// [8 bf16] for gate m = 8 mg + m8 and digit index k = s*KS + 8 kb + e.  One launch of
-// k_tc_blind_rotate runs all n steps (see below).  Every wait polls a bounded number of times; on time-out the block
-// records TFHE_ETIMEOUT in the context's error word and winds down.
+// Digits of term j are written per 128-gate tile in the A-operand layout:
+// [tile][term j][row r < 2l][stage < s/KS] blocks of 32 KB, each [mg < 16][kb < 16]
+// [m8 < 8][8 bf16] for gate m = 8 mg + m8 and digit index k' = stage*KS + 8 kb + e.
+// One launch of k_tc_blind_rotate runs all n steps.  Every wait polls a bounded number
+// of times; on time-out the block records TFHE_ETIMEOUT in the context's error word and
+// winds down.
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -43,7 +53,10 @@ constexpr int A_STAGE_BYTES = TILE_M * KS * 2;            // 32 KB
 constexpr int B_UNITS = NB + KS;                          // units per plane and stage
 constexpr int B_PLANE_BYTES = B_UNITS * 16;               // 4 KB
 constexpr int B_STAGE_BYTES = PLANES * B_PLANE_BYTES;     // 16 KB
-constexpr int SMEM_BYTES = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + 1024;
+// digit staging: one accumulator polynomial of 8 gates, rows padded by 4 words
+__host__ __device__ constexpr int smem_bytes(int N) {
+    return STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + 8 * (N + 4) * 4;
+}
 constexpr long long WAIT_CYCLES = 4000000000LL;           // ~2 s at 2 GHz
 
 // ---- PTX wrappers ----------------------------------------------------------------
@@ -98,6 +111,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     return true;
 }
 
+// mbar_wait for a whole warp: lane 0 polls, the others sleep in the shuffle, so 32 threads
+// do not compete for issue slots with the MMA and copy threads while they wait.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                               int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, err);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    return ok && mbar_test(bar, parity);
+}
+
 // Bounded wait that ignores the abort flag: used to let this block's own asynchronous
 // work (copies, MMAs) finish before it exits.
 __device__ __forceinline__ void mbar_wait_settle(uint64_t *bar, uint32_t parity) {
@@ -113,6 +136,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the destination with 0.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -186,31 +219,60 @@ __device__ __forceinline__ void byte_planes(uint32_t q, int (&pl)[PLANES]) {
     }
 }
 
-// r_vec[x] of the key polynomial q (zero past 2N: never read by an MMA).
-__device__ __forceinline__ uint32_t rvec(const uint32_t *__restrict__ q, int N, int x) {
-    if (x < N) return __ldg(q + (N - 1 - x));
-    if (x < 2 * N) return 0u - __ldg(q + (2 * N - 1 - x));
-    return 0u;
+// ---------------------------------------------------------------------------
+// Karatsuba term plan
+// ---------------------------------------------------------------------------
+
+constexpr int MAX_TERMS = 9;  // 3^L, L <= 2
+
+struct KTerm {
+    int n_in, in_blk[4], in_sgn[4];      // digit combination: sum sgn * block (size s)
+    int n_out, out_blk[4], out_sgn[4];   // output blocks (size s) receiving sgn * P
+    int n_key, key_off[4], key_coef[4];  // generator t_j[d] = sum coef * t[d + off]
+    int phase;                           // terms of one phase write disjoint blocks
+    int in_coef[4];                      // the digit combination as dense block weights
+};
+
+// Negacyclic generator of the key polynomial q: t[e] = q[e] (e >= 0), -q[e+N] (e < 0).
+__device__ __forceinline__ uint32_t neg_gen(const uint32_t *__restrict__ q, int N, int e) {
+    return e >= 0 ? __ldg(q + e) : 0u - __ldg(q + e + N);
 }
 
-// Window units of `npoly` key polynomials: win[(poly * 4 + p) * 2N + u] holds byte plane p
-// of r_vec[u .. u+7] as 8 bf16.  One block per polynomial.
-__global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, uint4 *__restrict__ win) {
+// Window units of term T for every (step, row, column) key polynomial:
+// win[((poly * nterms + j) * 4 + p) * 2s + u] holds byte plane p of r_vec_j[u .. u+7].
+// blockIdx.x = key polynomial (BSK order), blockIdx.y = term.
+__global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, int s, int nterms,
+                             const KTerm *__restrict__ terms, uint4 *__restrict__ win) {
     const size_t poly = blockIdx.x;
+    const int j = blockIdx.y;
     const uint32_t *q = polys + poly * N;
-    for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
+    const KTerm T = terms[j];
+    for (int u = threadIdx.x; u < 2 * s; u += blockDim.x) {
         uint32_t w[PLANES][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
+            uint32_t val[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int x = u + e + h;
+                uint32_t v = 0;
+                if (x < 2 * s - 1) {
+                    const int d = s - 1 - x;
+                    for (int m = 0; m < T.n_key; m++)
+                        v += (uint32_t)T.key_coef[m] * neg_gen(q, N, d + T.key_off[m]);
+                }
+                val[h] = v;
+            }
             int pl0[PLANES], pl1[PLANES];
-            byte_planes(rvec(q, N, u + e), pl0);
-            byte_planes(rvec(q, N, u + e + 1), pl1);
+            byte_planes(val[0], pl0);
+            byte_planes(val[1], pl1);
 #pragma unroll
             for (int p = 0; p < PLANES; p++) w[p][e / 2] = bf16_bits(pl0[p]) | (bf16_bits(pl1[p]) << 16);
         }
 #pragma unroll
         for (int p = 0; p < PLANES; p++)
-            win[(poly * PLANES + p) * 2 * N + u] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            win[((poly * nterms + j) * PLANES + p) * 2 * s + u] =
+                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
     }
 }
 
@@ -233,23 +295,42 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 // ---------------------------------------------------------------------------
 // Persistent BlindRotate: all n steps in one launch, one block per SM.
 //
-// Jobs: D(i, gt, part) writes the digits of gates 8*part .. 8*part+7 of gate tile gt for
-// step i (16 parts per tile); E(i, gt, cb) is the tensor-core product of column block
-// cb (ACC += Y).  Order: all D(0, ., .), then for each step i and tile gt:
-// E(i, gt, 0..cbs-1) followed by D(i+1, gt, 0..15).  Blocks take jobs from a global
-// counter, so a job only ever waits for jobs with smaller indices, which running
-// blocks hold: E(i, gt, .) waits for done_D[gt] >= 16 (i+1); D(i+1, gt, .) waits for
-// done_E[gt] >= cbs (i+1).  Every wait is bounded.
+// Jobs: D(i, gt, part) writes the digits (all terms) of gates 8*part .. 8*part+7 of gate
+// tile gt for step i (16 parts per tile); E(i, gt, j, c, b) is the tensor-core product of
+// term j for column block b of output polynomial c, added (with signs) into ACC.
+// Two job streams, each taken in order from its own global counter: digit jobs (step,
+// tile, part) by the digit warps of any block, product jobs (step, then a per-step table:
+// phase by phase, all tiles per phase) by the loaders.  With D(i) < E(i) < D(i+1) a job
+// only waits for jobs earlier in that order, each stream is handed out in order, and no
+// role holds anything a later job needs, so the schedule cannot deadlock:
+//   stages of E(i, gt, ...) wait for done_D[gt] >= 16 (i+1);
+//   the accumulator update of a phase-p product waits for the products of gt in earlier
+//   phases (done_E[gt] >= E_per_tile * i + dep);
+//   D(i, gt, .) waits for done_E[gt] >= E_per_tile * i.
+// Every wait is bounded.
 //
 // Warp roles (320 threads): warps 0-3 read TMEM out (warp w owns lanes 32w..32w+31),
 // warp 4 fetches jobs and streams stages with cp.async.bulk, warp 5 owns TMEM and one
 // lane issues the MMAs, warps 6-9 compute digits.  The four planes of TMEM are handed
 // back one by one after each K-half's read-out, so the next half's MMAs on plane p start
 // as soon as plane p has been read; both halves of a job accumulate in registers and the
-// accumulator row is updated once per job.
+// accumulator rows are updated once per job.
 // ---------------------------------------------------------------------------
 constexpr int P_THREADS = 320;
-constexpr int JQ = 8;  // job ring depth
+constexpr int JQ = 8;       // job ring depth
+constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
+
+enum { JOB_STOP = 0, JOB_D = 1, JOB_E = 2, JOB_NOP = 3 };
+
+// packed job-table entry: kind (2 bits) | gt (12) | term (4) | c (1) | sub (5) | dep (8)
+__host__ __device__ constexpr uint32_t pack_job(int kind, int gt, int j, int c, int sub, int dep) {
+    return (uint32_t)kind | ((uint32_t)gt << 2) | ((uint32_t)j << 14) | ((uint32_t)c << 18) |
+           ((uint32_t)sub << 19) | ((uint32_t)dep << 24);
+}
+
+struct Job {
+    int kind, i, gt, j, c, sub, dep;
+};
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
@@ -272,82 +353,77 @@ __device__ __forceinline__ bool wait_count(const uint32_t *p, uint32_t target, v
     return true;
 }
 
-constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
-
 struct BrArgs {
     int N, l, Bgbit, G, n, n1;
-    int tiles, cbs;             // gate tiles, column blocks (2N / NB)
-    long long total_jobs;
+    int s, nterms;              // term size N / 2^L and count 3^L
+    int tiles, cbs;             // gate tiles, column blocks per term output (2 * s / NB)
+    int e_per_tile;             // product jobs per tile and step
+    int step_len;               // entries of the per-step product-job table
+    long long total_e, total_d;
+    const uint32_t *table;      // per-step job table
+    const KTerm *terms;
     const uint32_t *bar;        // [G][n+1]
     uint32_t *acc;              // [G][2][N]
-    uint4 *digits;              // [tiles][2l][N/KS] x 32 KB
-    const uint4 *win;           // [n][2l][2][4][2N] units
-    uint32_t *sync;             // [0] job counter, [1 .. tiles] done_D, [1+tiles ..] done_E
+    uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
+    const uint4 *win;           // [n][2l][2][nterms][4][2s] units
+    uint32_t *sync;             // [0] product-job counter, [1] digit-job counter,
+                                // [2 .. 2+tiles) done_D, [2+tiles ..) done_E
     int *err;
 };
 
-struct Job {
-    int kind;  // 0 = stop, 1 = digits D(i, gt, part), 2 = product E(i, gt, cb)
-    int i, gt, sub;
-};
-
-__device__ __forceinline__ Job decode_job(const BrArgs &a, int job) {
-    Job J{0, 0, 0, 0};
+__device__ __forceinline__ Job decode_e(const BrArgs &a, int job) {
+    Job J{JOB_STOP, 0, 0, 0, 0, 0, 0};
     if (job < 0) return J;
-    const int d0 = a.tiles * DPARTS;
-    if (job < d0) {
-        J.kind = 1; J.i = 0; J.gt = job / DPARTS; J.sub = job % DPARTS;
-        return J;
-    }
-    int j = job - d0;
-    const int per = a.tiles * (a.cbs + DPARTS);
-    int i = j / per;
-    if (i < a.n - 1) {
-        j %= per;
-        J.gt = j / (a.cbs + DPARTS);
-        const int x = j % (a.cbs + DPARTS);
-        if (x < a.cbs) { J.kind = 2; J.i = i; J.sub = x; }
-        else { J.kind = 1; J.i = i + 1; J.sub = x - a.cbs; }
-        return J;
-    }
-    j -= (a.n - 1) * per;  // last step: products only
-    J.kind = 2; J.i = a.n - 1; J.gt = j / a.cbs; J.sub = j % a.cbs;
+    const uint32_t e = __ldg(a.table + job % a.step_len);
+    J.kind = JOB_E;
+    J.i = job / a.step_len;
+    J.gt = (int)((e >> 2) & 0xFFF);
+    J.j = (int)((e >> 14) & 0xF);
+    J.c = (int)((e >> 18) & 1);
+    J.sub = (int)((e >> 19) & 0x1F);
+    J.dep = (int)(e >> 24);
     return J;
 }
 
+template <int L>
 __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int NBLK = 1 << L;                      // size-s blocks per polynomial
+    constexpr int NT = L == 0 ? 1 : (L == 1 ? 3 : 9);  // terms
+    extern __shared__ __align__(128) uint8_t smem[];  // no swizzle: 16-byte alignment suffices
     uint8_t *a_st = smem;
     uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;
+    uint32_t *d_rows = (uint32_t *)(b_st + STAGES * B_STAGE_BYTES);  // [8][N + 4]
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     __shared__ __align__(8) uint64_t acc_full, acc_empty[PLANES], drain;
     __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
     __shared__ int jobs[JQ];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ KTerm terms[NT];
+    if (threadIdx.x < NT) terms[threadIdx.x] = a.terms[threadIdx.x];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int N = a.N, l = a.l;
-    const int kstages = N / KS;
+    const int N = a.N, l = a.l, s = a.s;
+    const int kstages = s / KS;
     const int half_stages = l * kstages;
     const int total_stages = 2 * half_stages;
-    const long long total_jobs = a.total_jobs;
-    uint32_t *job_counter = a.sync;
-    uint32_t *done_D = a.sync + 1;
-    uint32_t *done_E = a.sync + 1 + a.tiles;
+    const int bpp = s / NB;  // column blocks per term output polynomial
+    uint32_t *e_counter = a.sync;
+    uint32_t *d_counter = a.sync + 1;
+    uint32_t *done_D = a.sync + 2;
+    uint32_t *done_E = a.sync + 2 + a.tiles;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int q = 0; q < STAGES; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
         }
         mbar_init(&acc_full, 1);
         for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], 128);
         mbar_init(&drain, 1);
         for (int q = 0; q < JQ; q++) {
             mbar_init(&job_full[q], 1);
-            mbar_init(&job_empty[q], 3);  // MMA lane, read-out leader, digit leader
+            mbar_init(&job_empty[q], 2);  // MMA lane, read-out leader
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -373,37 +449,36 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             for (int q = 0;; q++) {
                 const int slot = q % JQ;
                 if (q >= JQ && !mbar_wait(&job_empty[slot], ((q / JQ) - 1) & 1, abort, err)) break;
-                const unsigned j = atomicAdd(job_counter, 1u);
-                const int job = (long long)j < total_jobs ? (int)j : -1;
+                const unsigned jn = atomicAdd(e_counter, 1u);
+                const int job = (long long)jn < a.total_e ? (int)jn : -1;
                 jobs[slot] = job;
                 mbar_arrive(&job_full[slot]);
                 if (job < 0) break;
-                const Job J = decode_job(a, job);
-                if (J.kind != 2) continue;  // digit job: nothing to load
-                const int i = J.i, gt = J.gt, cb = J.sub;
-                const int c = cb / (N / NB), bcol = cb % (N / NB);
-                const int P0 = N - NB - bcol * NB;
-                if (!wait_count(&done_D[gt], (uint32_t)(DPARTS * (i + 1)), abort, err)) break;
+                const Job J = decode_e(a, job);
+                const int bcol = J.sub % bpp;
+                const int P0 = s - NB - bcol * NB;
+                if (!wait_count(&done_D[J.gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err)) break;
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                const uint4 *win = a.win + (size_t)i * (2 * l * 2) * PLANES * 2 * N;
                 bool ok = true;
                 for (int ts = 0; ts < total_stages; ts++, t_global++) {
-                    const int s = t_global % STAGES;
+                    const int st = t_global % STAGES;
                     if (t_global >= STAGES &&
-                        !mbar_wait(&empty[s], ((t_global / STAGES) - 1) & 1, abort, err)) {
+                        !mbar_wait(&empty[st], ((t_global / STAGES) - 1) & 1, abort, err)) {
                         ok = false;
                         break;
                     }
                     const int r = ts / kstages, ks = ts % kstages;
-                    const size_t blk = ((size_t)gt * 2 * l + r) * kstages + ks;
-                    mbar_arrive_tx(&full[s], A_STAGE_BYTES + B_STAGE_BYTES);
-                    bulk_g2s(a_st + s * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
-                             A_STAGE_BYTES, &full[s]);
-                    const uint4 *wsrc = win + ((size_t)(r * 2 + c) * PLANES) * 2 * N + (P0 + ks * KS);
+                    const size_t blk = (((size_t)J.gt * a.nterms + J.j) * 2 * l + r) * kstages + ks;
+                    mbar_arrive_tx(&full[st], A_STAGE_BYTES + B_STAGE_BYTES);
+                    bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
+                             A_STAGE_BYTES, &full[st]);
+                    const size_t poly = ((size_t)J.i * 2 * l + r) * 2 + J.c;
+                    const uint4 *wsrc = a.win + ((poly * a.nterms + J.j) * PLANES) * 2 * s +
+                                        (P0 + ks * KS);
 #pragma unroll
                     for (int p = 0; p < PLANES; p++)
-                        bulk_g2s(b_st + s * B_STAGE_BYTES + p * B_PLANE_BYTES,
-                                 wsrc + (size_t)p * 2 * N, B_PLANE_BYTES, &full[s]);
+                        bulk_g2s(b_st + st * B_STAGE_BYTES + p * B_PLANE_BYTES,
+                                 wsrc + (size_t)p * 2 * s, B_PLANE_BYTES, &full[st]);
                     issued = t_global + 1;
                 }
                 if (!ok) break;
@@ -423,16 +498,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 const int job = jobs[slot];
                 mbar_arrive(&job_empty[slot]);
                 if (job < 0) break;
-                if (decode_job(a, job).kind != 2) continue;  // digit job
                 for (int ts = 0; ts < total_stages && ok; ts++, t_global++) {
-                    const int s = t_global % STAGES;
-                    if (!mbar_wait(&full[s], (t_global / STAGES) & 1, abort, err)) {
+                    const int st = t_global % STAGES;
+                    if (!mbar_wait(&full[st], (t_global / STAGES) & 1, abort, err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(a_st + s * A_STAGE_BYTES);
-                    const uint32_t b_addr = smem_u32(b_st + s * B_STAGE_BYTES);
+                    const uint32_t a_addr = smem_u32(a_st + st * A_STAGE_BYTES);
+                    const uint32_t b_addr = smem_u32(b_st + st * B_STAGE_BYTES);
                     if (ts % half_stages == 0) {
                         // first stage of a half: plane p starts once its previous contents
                         // have been read out
@@ -461,7 +535,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                          idesc, 1u);
                         }
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&empty[st]);
                     if ((ts + 1) % half_stages == 0) {
                         mma_commit(&acc_full);
                         khalf++;
@@ -478,22 +552,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
         int khalf = 0;
         for (int q = 0;; q++) {
             const int slot = q % JQ;
-            if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+            if (!mbar_wait_warp(&job_full[slot], (q / JQ) & 1, abort, err)) break;
             const int job = jobs[slot];
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (tid == 0) mbar_arrive(&job_empty[slot]);
             if (job < 0) break;
-            const Job J = decode_job(a, job);
-            if (J.kind != 2) continue;
-            const int i = J.i, gt = J.gt, cb = J.sub;
-            const int c = cb / (N / NB), bcol = cb % (N / NB);
-            const int c0 = bcol * NB + NB - 1;
+            const Job J = decode_e(a, job);
+            const int bcol = J.sub % bpp;
             uint32_t sum[NB];
 #pragma unroll
             for (int e = 0; e < NB; e++) sum[e] = 0;
             bool ok = true;
             for (int h = 0; h < 2 && ok; h++, khalf++) {
-                if (!mbar_wait(&acc_full, khalf & 1, abort, err)) {
+                if (!mbar_wait_warp(&acc_full, khalf & 1, abort, err)) {
                     ok = false;
                     break;
                 }
@@ -501,96 +572,141 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 #pragma unroll
                 for (int p = 0; p < PLANES; p++) {
 #pragma unroll
-                    for (int j = 0; j < NB / 16; j += 2) {
+                    for (int jc = 0; jc < NB / 16; jc += 2) {
                         uint32_t v[32];
-                        tmem_ld16(lane_base + p * NB + j * 16, v);
-                        tmem_ld16(lane_base + p * NB + (j + 1) * 16, v + 16);
+                        tmem_ld16(lane_base + p * NB + jc * 16, v);
+                        tmem_ld16(lane_base + p * NB + (jc + 1) * 16, v + 16);
                         tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 32; e++)
-                            sum[j * 16 + e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
+                            sum[jc * 16 + e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
                     }
                     tc_fence_before();
                     mbar_arrive(&acc_empty[p]);
                 }
             }
             if (!ok) break;
-            // ACC row update: word n = c0 - idx receives column idx.  The leader's acquire of
-            // done_D (already satisfied) orders these accesses after the previous step's
-            // updates of the same words by other blocks.
-            if (tid == 0) wait_count(&done_D[gt], (uint32_t)(DPARTS * (i + 1)), abort, err);
+            // accumulator update: column idx of the term output is word n' = c0 - idx of
+            // each of the term's output blocks.  The leader's acquires order these accesses
+            // after the digit job of this step and after this tile's earlier phases.
+            if (tid == 0) {
+                wait_count(&done_D[J.gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
+                if (J.dep) wait_count(&done_E[J.gt], (uint32_t)(a.e_per_tile * J.i + J.dep), abort, err);
+            }
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            const int g = gt * TILE_M + tid;
+            if (*abort) break;
+            const KTerm &T = terms[J.j];
+            const int g = J.gt * TILE_M + tid;
             if (g < a.G) {
-                uint4 *row = (uint4 *)(a.acc + (size_t)g * 2 * N + (size_t)c * N + (c0 - NB + 1));
+                for (int o = 0; o < T.n_out; o++) {
+                    const uint32_t sg = (uint32_t)T.out_sgn[o];
+                    uint4 *row = (uint4 *)(a.acc + (size_t)g * 2 * N + (size_t)J.c * N +
+                                           (size_t)T.out_blk[o] * s + bcol * NB);
 #pragma unroll
-                for (int q4 = 0; q4 < NB / 4; q4++) {
-                    uint4 o = row[q4];
-                    o.x += sum[NB - 1 - (4 * q4 + 0)];
-                    o.y += sum[NB - 1 - (4 * q4 + 1)];
-                    o.z += sum[NB - 1 - (4 * q4 + 2)];
-                    o.w += sum[NB - 1 - (4 * q4 + 3)];
-                    row[q4] = o;
+                    for (int q4 = 0; q4 < NB / 4; q4++) {
+                        uint4 v = __ldcg(row + q4);  // L2 only: rows move between blocks
+                        v.x += sg * sum[NB - 1 - (4 * q4 + 0)];
+                        v.y += sg * sum[NB - 1 - (4 * q4 + 1)];
+                        v.z += sg * sum[NB - 1 - (4 * q4 + 2)];
+                        v.w += sg * sum[NB - 1 - (4 * q4 + 3)];
+                        __stcg(row + q4, v);
+                    }
                 }
             }
             __threadfence();
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (tid == 0) atomicAdd(&done_E[gt], 1u);
+            if (tid == 0) atomicAdd(&done_E[J.gt], 1u);
         }
     } else {
         // ---- warps 6-9: digit jobs ----
         const int tid = threadIdx.x - 192;
         const uint32_t off = gadget_offset(l, a.Bgbit);
-        for (int q = 0;; q++) {
-            const int slot = q % JQ;
-            if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
-            const int job = jobs[slot];
+        __shared__ int d_job;
+        for (;;) {
+            if (tid == 0) {
+                const unsigned jn = atomicAdd(d_counter, 1u);
+                d_job = (long long)jn < a.total_d ? (int)jn : -1;
+            }
             asm volatile("bar.sync 2, 128;" ::: "memory");
-            if (tid == 0) mbar_arrive(&job_empty[slot]);
-            if (job < 0) break;
-            const Job J = decode_job(a, job);
-            if (J.kind != 1) continue;
-            const int i = J.i, gt = J.gt, mg = J.sub;
-            if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.cbs * i), abort, err);
+            const int job = d_job;
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (job < 0 || *abort) break;
+            const int i = job / (a.tiles * DPARTS);
+            const int gt = (job / DPARTS) % a.tiles, mg = job % DPARTS;
+            if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * i), abort, err);
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (*abort) break;
-            // items of this part: (c, stage s, kb, m8), m8 fastest so 8 threads write 128 B
-            const int items = 2 * kstages * 16 * 8;
-#pragma unroll 4
-            for (int it = tid; it < items; it += 128) {
-                int t = it;
-                const int m8 = t & 7; t >>= 3;
-                const int kb = t & 15; t >>= 4;
-                const int s = t % kstages;
-                const int c = t / kstages;
+            // One accumulator polynomial of the part's 8 gates at a time: the rows are copied
+            // into shared memory (16-byte asynchronous copies), then thread (m8 = tid & 7,
+            // kb = tid >> 3) digitises positions kp = kc*KS + 8 kb .. + 7 of every size-s block
+            // of gate m8, so 8 consecutive threads write 128 contiguous bytes of the A-operand
+            // layout (stage kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
+            const int pitch = N + 4;
+            int rot8[8];
+#pragma unroll
+            for (int m8 = 0; m8 < 8; m8++) {
                 const int g = gt * TILE_M + mg * 8 + m8;
-                const int k0 = s * KS + kb * 8;
-                uint32_t xv[8];
-                if (g < a.G) {
-                    const uint32_t *pr = a.acc + (size_t)g * 2 * N + (size_t)c * N;
-                    const int rot = (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N));
-                    const uint4 own0 = *(const uint4 *)(pr + k0);
-                    const uint4 own1 = *(const uint4 *)(pr + k0 + 4);
-                    const uint32_t own[8] = {own0.x, own0.y, own0.z, own0.w,
-                                             own1.x, own1.y, own1.z, own1.w};
-#pragma unroll
-                    for (int e = 0; e < 8; e++) xv[e] = rot_coef(pr, N, rot, k0 + e) - own[e];
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; e++) xv[e] = 0;
+                rot8[m8] = g < a.G ? (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
+            }
+            const int m8 = tid & 7, kb = tid >> 3;
+            const int rot = rot8[m8];
+            const int rk = rot >= N ? rot - N : rot;      // X^rot = (-1)^{rot >= N} X^rk
+            const uint32_t rneg = rot >= N ? 0xFFFFFFFFu : 0u;
+            const uint32_t *row = d_rows + m8 * pitch;
+            for (int c = 0; c < 2; c++) {
+                asm volatile("bar.sync 2, 128;" ::: "memory");  // previous polynomial consumed
+                for (int v = tid; v < 8 * (N / 4); v += 128) {
+                    const int mm = v / (N / 4), q4 = v % (N / 4);
+                    const int g = gt * TILE_M + mg * 8 + mm;
+                    const uint32_t *src = a.acc + (size_t)(g < a.G ? g : 0) * 2 * N + (size_t)c * N + q4 * 4;
+                    cp_async16(d_rows + mm * pitch + q4 * 4, src, g < a.G ? 16u : 0u);
                 }
-                for (int jd = 0; jd < l; jd++) {
-                    uint32_t w[4];
+                cp_async_wait_all();
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+                for (int kc = 0; kc < kstages; kc++) {
+                    const int kp = kc * KS + kb * 8;
+                    uint32_t xv[NBLK][8];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        const uint32_t lo = bf16_bits(gadget_digit(xv[e] + off, jd + 1, a.Bgbit));
-                        const uint32_t hi = bf16_bits(gadget_digit(xv[e + 1] + off, jd + 1, a.Bgbit));
-                        w[e / 2] = lo | (hi << 16);
+                    for (int b = 0; b < NBLK; b++) {
+                        const int k0 = b * s + kp;
+                        const uint4 o0 = *(const uint4 *)(row + k0);
+                        const uint4 o1 = *(const uint4 *)(row + k0 + 4);
+                        const uint32_t own[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int k = k0 + e;
+                            const int src = k - rk;
+                            uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
+                            v = (v ^ rneg) - rneg;  // negate when rot >= N
+                            xv[b][e] = v - own[e];
+                        }
                     }
-                    const int r = c * l + jd;
-                    const size_t blk = ((size_t)gt * 2 * l + r) * kstages + s;
-                    a.digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
-                        make_uint4(w[0], w[1], w[2], w[3]);
+                    for (int jd = 0; jd < l; jd++) {
+                        int dg[NBLK][8];
+#pragma unroll
+                        for (int b = 0; b < NBLK; b++)
+#pragma unroll
+                            for (int e = 0; e < 8; e++) dg[b][e] = gadget_digit(xv[b][e] + off, jd + 1, a.Bgbit);
+                        const int r = c * l + jd;
+#pragma unroll
+                        for (int j = 0; j < NT; j++) {
+                            int x[8];
+#pragma unroll
+                            for (int e = 0; e < 8; e++) x[e] = 0;
+#pragma unroll
+                            for (int b = 0; b < NBLK; b++) {
+                                const int cf = terms[j].in_coef[b];
+#pragma unroll
+                                for (int e = 0; e < 8; e++) x[e] += cf * dg[b][e];
+                            }
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2) w[e / 2] = bf16_bits(x[e]) | (bf16_bits(x[e + 1]) << 16);
+                            const size_t blk = (((size_t)gt * NT + j) * 2 * l + r) * kstages + kc;
+                            a.digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
+                                make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
                 }
             }
             __threadfence();
@@ -608,13 +724,115 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+// Terms of the L-level split (see the top of this file), in a deterministic order.
+static void build_plan(int N, int L, std::vector<KTerm> &terms) {
+    terms.clear();
+    auto mk = [](int nin, const int *ib, const int *is, int nout, const int *ob, const int *os,
+                 int nk, const int *ko, const int *kc) {
+        KTerm t{};
+        t.n_in = nin;
+        t.n_out = nout;
+        t.n_key = nk;
+        for (int m = 0; m < nin; m++) { t.in_blk[m] = ib[m]; t.in_sgn[m] = is[m]; }
+        for (int m = 0; m < nout; m++) { t.out_blk[m] = ob[m]; t.out_sgn[m] = os[m]; }
+        for (int m = 0; m < nk; m++) { t.key_off[m] = ko[m]; t.key_coef[m] = kc[m]; }
+        return t;
+    };
+    if (L == 0) {
+        const int b0[1] = {0}, p1[1] = {1}, k0[1] = {0};
+        terms.push_back(mk(1, b0, p1, 1, b0, p1, 1, k0, p1));
+    }
+    // level 1: negacyclic split, s = N/2.  A: t[d], B: t[d + s].
+    const int s1 = N / 2;
+    if (L >= 1) {
+        const int in1[1] = {0}, in1s[1] = {1};
+        const int out1[2] = {0, 1}, out1s[2] = {1, 1};
+        const int k1[2] = {0, s1}, k1c[2] = {1, 1};
+        terms.push_back(mk(1, in1, in1s, 2, out1, out1s, 2, k1, k1c));          // P1 = (A+B) x0
+        const int in2[2] = {1, 0}, in2s[2] = {1, -1};
+        const int out2[1] = {1}, out2s[1] = {1};
+        const int k2[1] = {0}, k2c[1] = {1};
+        terms.push_back(mk(2, in2, in2s, 1, out2, out2s, 1, k2, k2c));          // P2 = A (x1 - x0)
+        const int in3[2] = {0, 1}, in3s[2] = {1, 1};
+        const int out3[1] = {0}, out3s[1] = {-1};
+        const int k3[1] = {s1}, k3c[1] = {1};
+        terms.push_back(mk(2, in3, in3s, 1, out3, out3s, 1, k3, k3c));          // P3 = B (x0 + x1)
+    }
+    for (int lev = 2; lev <= L; lev++) {
+        const int h = N >> lev;  // new block size
+        std::vector<KTerm> next;
+        for (const KTerm &P : terms) {
+            KTerm a{}, q0{}, q1{};
+            // inputs: x0 = first halves (2b), x1 = second halves (2b+1)
+            for (int m = 0; m < P.n_in; m++) {
+                a.in_blk[a.n_in] = 2 * P.in_blk[m]; a.in_sgn[a.n_in++] = P.in_sgn[m];
+                a.in_blk[a.n_in] = 2 * P.in_blk[m] + 1; a.in_sgn[a.n_in++] = P.in_sgn[m];
+                q0.in_blk[q0.n_in] = 2 * P.in_blk[m] + 1; q0.in_sgn[q0.n_in++] = P.in_sgn[m];
+                q1.in_blk[q1.n_in] = 2 * P.in_blk[m]; q1.in_sgn[q1.n_in++] = P.in_sgn[m];
+            }
+            // outputs: y0 = P + Q0 (blocks 2b), y1 = P + Q1 (blocks 2b+1)
+            for (int m = 0; m < P.n_out; m++) {
+                a.out_blk[a.n_out] = 2 * P.out_blk[m]; a.out_sgn[a.n_out++] = P.out_sgn[m];
+                a.out_blk[a.n_out] = 2 * P.out_blk[m] + 1; a.out_sgn[a.n_out++] = P.out_sgn[m];
+                q0.out_blk[q0.n_out] = 2 * P.out_blk[m]; q0.out_sgn[q0.n_out++] = P.out_sgn[m];
+                q1.out_blk[q1.n_out] = 2 * P.out_blk[m] + 1; q1.out_sgn[q1.n_out++] = P.out_sgn[m];
+            }
+            // keys: T00 = t[d], T01 = t[d - h], T10 = t[d + h]
+            for (int m = 0; m < P.n_key; m++) {
+                a.key_off[a.n_key] = P.key_off[m]; a.key_coef[a.n_key++] = P.key_coef[m];
+                q0.key_off[q0.n_key] = P.key_off[m] - h; q0.key_coef[q0.n_key++] = P.key_coef[m];
+                q1.key_off[q1.n_key] = P.key_off[m] + h; q1.key_coef[q1.n_key++] = P.key_coef[m];
+            }
+            for (int m = 0; m < P.n_key; m++) {
+                q0.key_off[q0.n_key] = P.key_off[m]; q0.key_coef[q0.n_key++] = -P.key_coef[m];
+                q1.key_off[q1.n_key] = P.key_off[m]; q1.key_coef[q1.n_key++] = -P.key_coef[m];
+            }
+            next.push_back(a);
+            next.push_back(q0);
+            next.push_back(q1);
+        }
+        terms.swap(next);
+    }
+    for (KTerm &t : terms) {
+        for (int b = 0; b < 4; b++) t.in_coef[b] = 0;
+        for (int m = 0; m < t.n_in; m++) t.in_coef[t.in_blk[m]] += t.in_sgn[m];
+    }
+    // phases: greedy, terms of one phase write disjoint output blocks
+    std::vector<std::vector<int>> used;  // per phase, blocks written
+    for (KTerm &t : terms) {
+        int ph = 0;
+        for (;; ph++) {
+            if (ph == (int)used.size()) used.emplace_back();
+            bool clash = false;
+            for (int m = 0; m < t.n_out && !clash; m++)
+                for (int b : used[ph]) if (b == t.out_blk[m]) clash = true;
+            if (!clash) break;
+        }
+        t.phase = ph;
+        for (int m = 0; m < t.n_out; m++) used[ph].push_back(t.out_blk[m]);
+    }
+}
+
 struct TcWorkspace {
+    int level = -1;            // Karatsuba levels of the prepared windows
+    std::vector<KTerm> terms;
+    KTerm *d_terms = nullptr;
+    uint4 *win = nullptr;      // window units for every step
+    size_t win_cap = 0;        // bytes
     uint4 *digits = nullptr;
-    size_t digits_cap = 0;  // bytes
-    uint4 *win = nullptr;   // BSK window units, [n][2l][2][4 planes][2N]
+    size_t digits_cap = 0;     // bytes
     uint32_t *sync = nullptr;  // job counter and per-tile progress counters
     size_t sync_cap = 0;       // words
+    uint32_t *table = nullptr; // per-step job table
+    size_t table_cap = 0;      // entries
+    int table_tiles = -1;
+    int table_len = 0;
     int sms = 0;
+    int want_level = -1;       // requested Karatsuba levels (-1: default)
 };
 
 int tfhe_tc_supported(const tfhe_ctx *ctx) {
@@ -623,49 +841,108 @@ int tfhe_tc_supported(const tfhe_ctx *ctx) {
            (int64_t)p.l * p.N * 32 * 128 <= (1 << 24);
 }
 
+static int default_level(const tfhe_params &p) { return p.N >= 512 ? 1 : 0; }
+
+static bool level_ok(const tfhe_params &p, int L) {
+    if (L < 0 || L > 2) return false;
+    const int s = p.N >> L;
+    return s >= NB && s % NB == 0 && s % KS == 0;
+}
+
 void tfhe_tc_free(tfhe_ctx *ctx) {
     if (!ctx->tc) return;
-    if (ctx->tc->digits) cudaFree(ctx->tc->digits);
-    if (ctx->tc->win) cudaFree(ctx->tc->win);
-    if (ctx->tc->sync) cudaFree(ctx->tc->sync);
-    delete ctx->tc;
+    TcWorkspace *w = ctx->tc;
+    if (w->d_terms) cudaFree(w->d_terms);
+    if (w->win) cudaFree(w->win);
+    if (w->digits) cudaFree(w->digits);
+    if (w->sync) cudaFree(w->sync);
+    if (w->table) cudaFree(w->table);
+    delete w;
     ctx->tc = nullptr;
 }
 
-static int ensure_digits(tfhe_ctx *ctx, int G) {
-    if (!ctx->tc) ctx->tc = new TcWorkspace();
-    const size_t tiles = (size_t)(G + TILE_M - 1) / TILE_M;
-    const size_t bytes = tiles * 2 * ctx->p.l * ctx->p.N * TILE_M * 2;
-    const size_t words = 1 + 2 * tiles;
-    if (words > ctx->tc->sync_cap) {
-        if (ctx->tc->sync) cudaFree(ctx->tc->sync);
-        ctx->tc->sync = nullptr;
-        ctx->tc->sync_cap = 0;
-        if (cudaMalloc(&ctx->tc->sync, words * 4) != cudaSuccess)
-            return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core progress counters");
-        ctx->tc->sync_cap = words;
-    }
-    if (bytes <= ctx->tc->digits_cap) return TFHE_OK;
-    if (ctx->tc->digits) cudaFree(ctx->tc->digits);
-    ctx->tc->digits = nullptr;
-    ctx->tc->digits_cap = 0;
-    if (cudaMalloc(&ctx->tc->digits, bytes) != cudaSuccess)
-        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core digit buffer");
-    ctx->tc->digits_cap = bytes;
+static int grow_dev(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need, const char *what) {
+    if (need <= *cap) return TFHE_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc(ptr, need) != cudaSuccess) return tfhe_set_error(ctx, TFHE_ENOMEM, what);
+    *cap = need;
     return TFHE_OK;
 }
 
-// Expand the window units of the whole BSK (called when the keys are loaded).
-int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st) {
-    if (!tfhe_tc_supported(ctx)) return TFHE_OK;
+// (Re)build the term plan and expand the windows of the whole BSK for `level`.
+static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
-    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    TcWorkspace *w = ctx->tc;
+    build_plan(p.N, level, w->terms);
+    const int T = (int)w->terms.size();
+    const int s = p.N >> level;
+    if (!w->d_terms && cudaMalloc(&w->d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core term plan");
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(w->d_terms, w->terms.data(), sizeof(KTerm) * T,
+                                       cudaMemcpyHostToDevice, st));
     const size_t npoly = (size_t)p.n * 2 * p.l * 2;
-    if (!ctx->tc->win &&
-        cudaMalloc(&ctx->tc->win, npoly * PLANES * 2 * p.N * sizeof(uint4)) != cudaSuccess)
-        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core key windows");
-    k_tc_windows<<<(unsigned)npoly, 256, 0, st>>>(bsk, p.N, ctx->tc->win);
-    return tfhe_check_launch(ctx, "tc_windows");
+    const size_t bytes = npoly * T * PLANES * 2 * (size_t)s * sizeof(uint4);
+    int rc = grow_dev(ctx, (void **)&w->win, &w->win_cap, bytes, "tensor-core key windows");
+    if (rc != TFHE_OK) return rc;
+    k_tc_windows<<<dim3((unsigned)npoly, T), 256, 0, st>>>(ctx->bsk_raw, p.N, s, T, w->d_terms,
+                                                          w->win);
+    rc = tfhe_check_launch(ctx, "tc_windows");
+    if (rc != TFHE_OK) return rc;
+    w->level = level;
+    w->table_tiles = -1;  // job table depends on the plan
+    return TFHE_OK;
+}
+
+// Expand the windows of the whole BSK (called when the keys are loaded).
+int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *, cudaStream_t st) {
+    if (!tfhe_tc_supported(ctx)) return TFHE_OK;
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    const int L = ctx->tc->want_level >= 0 ? ctx->tc->want_level : default_level(ctx->p);
+    return prepare_windows(ctx, L, st);
+}
+
+int tfhe_tc_set_level(tfhe_ctx *ctx, int level) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    if (level < 0) level = default_level(ctx->p);
+    if (!level_ok(ctx->p, level))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba level not supported for this N");
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    ctx->tc->want_level = level;
+    if (ctx->has_keys && ctx->tc->level != level) return prepare_windows(ctx, level, 0);
+    return TFHE_OK;
+}
+
+// Per-step job table for `tiles` gate tiles (see the kernel comment for the order).
+static int prepare_table(tfhe_ctx *ctx, int tiles, cudaStream_t st) {
+    TcWorkspace *w = ctx->tc;
+    if (w->table_tiles == tiles) return TFHE_OK;
+    const int s = ctx->p.N >> w->level;
+    const int bpp = s / NB;
+    int nphase = 0;
+    for (const KTerm &t : w->terms) nphase = t.phase + 1 > nphase ? t.phase + 1 : nphase;
+    std::vector<uint32_t> tab;
+    for (int ph = 0; ph < nphase; ph++) {
+        for (int gt = 0; gt < tiles; gt++) {
+            int dep = 0;  // product jobs of this tile in earlier phases
+            for (const KTerm &t : w->terms)
+                if (t.phase < ph) dep += 2 * bpp;
+            for (int j = 0; j < (int)w->terms.size(); j++) {
+                if (w->terms[j].phase != ph) continue;
+                for (int c = 0; c < 2; c++)
+                    for (int b = 0; b < bpp; b++) tab.push_back(pack_job(JOB_E, gt, j, c, b, dep));
+            }
+
+        }
+    }
+    int rc = grow_dev(ctx, (void **)&w->table, &w->table_cap, tab.size() * 4, "tensor-core job table");
+    if (rc != TFHE_OK) return rc;
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(w->table, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // the host vector goes out of scope
+    w->table_tiles = tiles;
+    w->table_len = (int)tab.size();
+    return TFHE_OK;
 }
 
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
@@ -674,10 +951,25 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     if (G == 0) return TFHE_OK;
     if (!tfhe_tc_supported(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
-    if (!ctx->tc || !ctx->tc->win)
+    TcWorkspace *w = ctx->tc;
+    if (!w || !w->win || w->level < 0)
         return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
-    int rc = ensure_digits(ctx, G);
+    const int tiles = (G + TILE_M - 1) / TILE_M;
+    const int T = (int)w->terms.size();
+    const int s = p.N >> w->level;
+    int rc = grow_dev(ctx, (void **)&w->digits, &w->digits_cap,
+                      (size_t)tiles * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
     if (rc != TFHE_OK) return rc;
+    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles) * 4,
+                  "tensor-core progress counters");
+    if (rc != TFHE_OK) return rc;
+    rc = prepare_table(ctx, tiles, st);
+    if (rc != TFHE_OK) return rc;
+    if (!w->sms) {
+        int sms = 0;
+        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        w->sms = sms;
+    }
     const int n1 = p.n + 1;
     {
         const size_t total = (size_t)G * 2 * p.N;
@@ -685,16 +977,11 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         rc = tfhe_check_launch(ctx, "tc_init_acc");
         if (rc != TFHE_OK) return rc;
     }
-    const int tiles = (G + TILE_M - 1) / TILE_M;
-    if (!ctx->tc->sms) {
-        int sms = 0;
-        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-        ctx->tc->sms = sms;
-    }
-    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_blind_rotate,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            SMEM_BYTES));
-    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->tc->sync, 0, (1 + 2 * (size_t)tiles) * 4, st));
+    auto kern = w->level == 0 ? k_tc_blind_rotate<0>
+              : (w->level == 1 ? k_tc_blind_rotate<1> : k_tc_blind_rotate<2>);
+    const int smem = smem_bytes(p.N);
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 2 * (size_t)tiles) * 4, st));
     BrArgs args;
     args.N = p.N;
     args.l = p.l;
@@ -702,20 +989,25 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.G = G;
     args.n = p.n;
     args.n1 = n1;
+    args.s = s;
+    args.nterms = T;
     args.tiles = tiles;
-    args.cbs = 2 * p.N / NB;
+    args.cbs = 2 * (s / NB);
+    args.e_per_tile = T * 2 * (s / NB);
+    args.step_len = w->table_len;
+    args.total_e = (long long)p.n * w->table_len;
+    args.total_d = (long long)p.n * tiles * DPARTS;
+    args.table = w->table;
+    args.terms = w->d_terms;
     args.bar = bar;
     args.acc = acc;
-    args.digits = ctx->tc->digits;
-    args.win = ctx->tc->win;
-    args.sync = ctx->tc->sync;
+    args.digits = w->digits;
+    args.win = w->win;
+    args.sync = w->sync;
     args.err = ctx->d_err;
-    args.total_jobs = (long long)tiles * DPARTS +
-                      (long long)(p.n - 1) * tiles * (args.cbs + DPARTS) + (long long)tiles * args.cbs;
-    const long long jobs = args.total_jobs;
-    const int grid = (int)(jobs < ctx->tc->sms ? jobs : ctx->tc->sms);
+    const int grid = (int)(args.total_e < w->sms ? args.total_e : w->sms);
     StageTimer tm(ctx, TFHE_STAGE_EXTPROD_TC, st);
-    k_tc_blind_rotate<<<grid, P_THREADS, SMEM_BYTES, st>>>(args);
+    kern<<<grid, P_THREADS, smem, st>>>(args);
     tm.stop();
     return tfhe_check_launch(ctx, "tc blind rotate");
 }

@@ -128,3 +128,23 @@ def test_host_buffer_entry_point_matches_device(torch_cuda):
     ctx.gate_batch_host(b.inp, b.types, np.ascontiguousarray(b.idx), out)
     want = orc.gate_batch(ti.TOY, k.bsk, k.ksk, b.inp, b.types, b.idx)
     assert np.array_equal(out, want)
+
+
+@pytest.mark.parametrize("params,seed,levels,G", [
+    (ti.TOY, ti.SEED_TOY, (0, 1), 40),
+    (ti.STD, ti.SEED_FLAT, (0, 1, 2), 37),
+])
+def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G):
+    """Every Karatsuba level of the tensor-core form gives the oracle's words."""
+    ctx, k = gpu_context(params, seed)
+    b = ti.toy_gates() if params is ti.TOY else ti.flat_level(G)
+    want = orc.gate_batch(params, k.bsk, k.ksk, b.inp, b.types, b.idx)
+    try:
+        for L in levels:
+            ctx.set_tc_level(L)
+            out = empty(torch_cuda, b.types.size, params.n + 1)
+            ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=1)
+            ctx.sync()
+            assert np.array_equal(from_dev(out), want), L
+    finally:
+        ctx.set_tc_level(-1)
