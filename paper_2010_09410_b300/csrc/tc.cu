@@ -309,14 +309,21 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 //   D(i, gt, .) waits for done_E[gt] >= E_per_tile * i.
 // Every wait is bounded.
 //
-// Warp roles (320 threads): warps 0-3 read TMEM out (warp w owns lanes 32w..32w+31),
-// warp 4 fetches jobs and streams stages with cp.async.bulk, warp 5 owns TMEM and one
-// lane issues the MMAs, warps 6-9 compute digits.  The four planes of TMEM are handed
+// Warp roles (448 threads): warps 0-7 read TMEM out (warp w owns lanes 32(w%4)..+31 and
+// columns 64(w/4)..+63 of the block), warp 8 fetches jobs and streams stages with
+// cp.async.bulk, warp 9 owns TMEM and one lane issues the MMAs, warps 10-13 compute
+// digits.  The four planes of TMEM are handed
 // back one by one after each K-half's read-out, so the next half's MMAs on plane p start
 // as soon as plane p has been read; both halves of a job accumulate in registers and the
 // accumulator rows are updated once per job.
 // ---------------------------------------------------------------------------
-constexpr int P_THREADS = 320;
+constexpr int P_THREADS = 448;
+constexpr int EPI_WARPS = 8;                 // read-out warps: 2 per TMEM lane quarter
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int LOAD_WARP = EPI_WARPS;         // job fetch + stage loads
+constexpr int MMA_WARP = EPI_WARPS + 1;      // TMEM owner + MMA issue
+constexpr int DIG_WARP0 = EPI_WARPS + 2;     // 4 digit warps
+constexpr int EPI_COLS = NB / 2;             // columns per read-out warp
 constexpr int JQ = 8;       // job ring depth
 constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
 
@@ -419,7 +426,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             mbar_init(&empty[q], 1);
         }
         mbar_init(&acc_full, 1);
-        for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], 128);
+        for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], EPI_THREADS);
         mbar_init(&drain, 1);
         for (int q = 0; q < JQ; q++) {
             mbar_init(&job_full[q], 1);
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    if (warp == 5) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(512));
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     volatile int *abort = &abort_flag;
     int *err = a.err;
 
-    if (warp == 4) {
+    if (warp == LOAD_WARP) {
         // ---- job fetch + stage loads ----
         if (lane == 0) {
             int t_global = 0, issued = 0;
@@ -486,7 +493,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             for (int t = issued - STAGES; t < issued; t++)
                 if (t >= 0) mbar_wait_settle(&full[t % STAGES], (t / STAGES) & 1);
         }
-    } else if (warp == 5) {
+    } else if (warp == MMA_WARP) {
         // ---- MMA issue ----
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc(TILE_M, NB);
@@ -545,23 +552,25 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             mma_commit(&drain);
             mbar_wait_settle(&drain, 0);
         }
-    } else if (warp < 4) {
-        // ---- TMEM read-out: thread = TMEM lane = gate of the tile ----
+    } else if (warp < EPI_WARPS) {
+        // ---- TMEM read-out: thread = TMEM lane = gate of the tile; this warp's 64 columns
         const int tid = threadIdx.x;
-        const uint32_t lane_base = tmem + (((uint32_t)(warp * 32)) << 16);
+        const int lane_q = warp & 3, colh = warp >> 2;
+        const uint32_t lane_base = tmem + (((uint32_t)(lane_q * 32)) << 16) + colh * EPI_COLS;
+        const int gl = lane_q * 32 + lane;  // gate within the tile
         int khalf = 0;
         for (int q = 0;; q++) {
             const int slot = q % JQ;
             if (!mbar_wait_warp(&job_full[slot], (q / JQ) & 1, abort, err)) break;
             const int job = jobs[slot];
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             if (tid == 0) mbar_arrive(&job_empty[slot]);
             if (job < 0) break;
             const Job J = decode_e(a, job);
             const int bcol = J.sub % bpp;
-            uint32_t sum[NB];
+            uint32_t sum[EPI_COLS];
 #pragma unroll
-            for (int e = 0; e < NB; e++) sum[e] = 0;
+            for (int e = 0; e < EPI_COLS; e++) sum[e] = 0;
             bool ok = true;
             for (int h = 0; h < 2 && ok; h++, khalf++) {
                 if (!mbar_wait_warp(&acc_full, khalf & 1, abort, err)) {
@@ -571,16 +580,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 tc_fence_after();
 #pragma unroll
                 for (int p = 0; p < PLANES; p++) {
+                    uint32_t v[EPI_COLS];
 #pragma unroll
-                    for (int jc = 0; jc < NB / 16; jc += 2) {
-                        uint32_t v[32];
-                        tmem_ld16(lane_base + p * NB + jc * 16, v);
-                        tmem_ld16(lane_base + p * NB + (jc + 1) * 16, v + 16);
-                        tmem_wait_ld();
+                    for (int jc = 0; jc < EPI_COLS / 16; jc++)
+                        tmem_ld16(lane_base + p * NB + jc * 16, v + jc * 16);
+                    tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 32; e++)
-                            sum[jc * 16 + e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
-                    }
+                    for (int e = 0; e < EPI_COLS; e++)
+                        sum[e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
                     tc_fence_before();
                     mbar_arrive(&acc_empty[p]);
                 }
@@ -593,33 +600,36 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 wait_count(&done_D[J.gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
                 if (J.dep) wait_count(&done_E[J.gt], (uint32_t)(a.e_per_tile * J.i + J.dep), abort, err);
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             if (*abort) break;
             const KTerm &T = terms[J.j];
-            const int g = J.gt * TILE_M + tid;
+            const int g = J.gt * TILE_M + gl;
             if (g < a.G) {
+                // this warp's columns idx = 64 colh + e map to words c0 - idx, i.e. the
+                // 64 words starting at bcol*NB + 64 (1 - colh), in reverse order
+                const int w0 = bcol * NB + EPI_COLS * (1 - colh);
                 for (int o = 0; o < T.n_out; o++) {
                     const uint32_t sg = (uint32_t)T.out_sgn[o];
                     uint4 *row = (uint4 *)(a.acc + (size_t)g * 2 * N + (size_t)J.c * N +
-                                           (size_t)T.out_blk[o] * s + bcol * NB);
+                                           (size_t)T.out_blk[o] * s + w0);
 #pragma unroll
-                    for (int q4 = 0; q4 < NB / 4; q4++) {
+                    for (int q4 = 0; q4 < EPI_COLS / 4; q4++) {
                         uint4 v = __ldcg(row + q4);  // L2 only: rows move between blocks
-                        v.x += sg * sum[NB - 1 - (4 * q4 + 0)];
-                        v.y += sg * sum[NB - 1 - (4 * q4 + 1)];
-                        v.z += sg * sum[NB - 1 - (4 * q4 + 2)];
-                        v.w += sg * sum[NB - 1 - (4 * q4 + 3)];
+                        v.x += sg * sum[EPI_COLS - 1 - (4 * q4 + 0)];
+                        v.y += sg * sum[EPI_COLS - 1 - (4 * q4 + 1)];
+                        v.z += sg * sum[EPI_COLS - 1 - (4 * q4 + 2)];
+                        v.w += sg * sum[EPI_COLS - 1 - (4 * q4 + 3)];
                         __stcg(row + q4, v);
                     }
                 }
             }
             __threadfence();
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             if (tid == 0) atomicAdd(&done_E[J.gt], 1u);
         }
     } else {
-        // ---- warps 6-9: digit jobs ----
-        const int tid = threadIdx.x - 192;
+        // ---- warps 10-13: digit jobs ----
+        const int tid = threadIdx.x - DIG_WARP0 * 32;
         const uint32_t off = gadget_offset(l, a.Bgbit);
         __shared__ int d_job;
         for (;;) {
@@ -716,7 +726,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
