@@ -324,6 +324,14 @@ constexpr int LOAD_WARP = EPI_WARPS;         // job fetch + stage loads
 constexpr int MMA_WARP = EPI_WARPS + 1;      // TMEM owner + MMA issue
 constexpr int DIG_WARP0 = EPI_WARPS + 2;     // 4 digit warps
 constexpr int EPI_COLS = NB / 2;             // columns per read-out warp
+// read-out conversion constants: 1.5*2^23 and its bit pattern; the initial sum cancels the
+// bit-pattern offset added by both K-halves of all four planes (mod 2^32)
+constexpr float RO_MAGIC = 12582912.0f;
+constexpr uint32_t RO_MAGIC_BITS = 0x4B400000u;
+constexpr float RO_FAST_LIMIT = 4194304.0f;  // 2^22
+constexpr int RO_COLS = 32;                   // columns per TMEM load slice
+constexpr uint32_t RO_SUM_INIT =
+    0u - 2u * (RO_MAGIC_BITS + (RO_MAGIC_BITS << 8) + (RO_MAGIC_BITS << 16) + (RO_MAGIC_BITS << 24));
 constexpr int JQ = 8;       // job ring depth
 constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
 
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             const int bcol = J.sub % bpp;
             uint32_t sum[EPI_COLS];
 #pragma unroll
-            for (int e = 0; e < EPI_COLS; e++) sum[e] = 0;
+            for (int e = 0; e < EPI_COLS; e++) sum[e] = RO_SUM_INIT;
             bool ok = true;
             for (int h = 0; h < 2 && ok; h++, khalf++) {
                 if (!mbar_wait_warp(&acc_full, khalf & 1, abort, err)) {
@@ -580,14 +588,32 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 tc_fence_after();
 #pragma unroll
                 for (int p = 0; p < PLANES; p++) {
-                    uint32_t v[EPI_COLS];
+                    // exact fp32 -> int: for |x| < 2^22 the sum x + 1.5*2^23 is exact and its
+                    // bit pattern is RO_MAGIC_BITS + x; the constant is removed once through
+                    // the initial value of sum.  A slice holding a larger |x| (possible, never
+                    // typical) takes the rounding conversion instead, so the result stays
+                    // exact either way.  Slices of RO_COLS columns bound the live registers.
 #pragma unroll
-                    for (int jc = 0; jc < EPI_COLS / 16; jc++)
-                        tmem_ld16(lane_base + p * NB + jc * 16, v + jc * 16);
-                    tmem_wait_ld();
+                    for (int c0 = 0; c0 < EPI_COLS; c0 += RO_COLS) {
+                        uint32_t v[RO_COLS];
 #pragma unroll
-                    for (int e = 0; e < EPI_COLS; e++)
-                        sum[e] += (uint32_t)__float2int_rn(__uint_as_float(v[e])) << (8 * p);
+                        for (int jc = 0; jc < RO_COLS / 16; jc++)
+                            tmem_ld16(lane_base + p * NB + c0 + jc * 16, v + jc * 16);
+                        tmem_wait_ld();
+                        float m = 0.f;
+#pragma unroll
+                        for (int e = 0; e < RO_COLS; e++) m = fmaxf(m, fabsf(__uint_as_float(v[e])));
+                        if (m < RO_FAST_LIMIT) {
+#pragma unroll
+                            for (int e = 0; e < RO_COLS; e++)
+                                sum[c0 + e] += __float_as_uint(__uint_as_float(v[e]) + RO_MAGIC) << (8 * p);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < RO_COLS; e++)
+                                sum[c0 + e] +=
+                                    ((uint32_t)__float2int_rn(__uint_as_float(v[e])) + RO_MAGIC_BITS) << (8 * p);
+                        }
+                    }
                     tc_fence_before();
                     mbar_arrive(&acc_empty[p]);
                 }
