@@ -121,9 +121,9 @@ def oracle_gates_per_s(batch, sample_gates):
 
 
 def oracle_sample_size():
-    # ~2.4 s per gate per core: about four rounds of one gate per core (10-30 s of work)
+    # 1.5-2.4 s per gate per core: eight rounds of one gate per core (10-30 s of work)
     cores = os.cpu_count() or 1
-    return max(8, min(4 * cores, 512))
+    return max(8, min(8 * cores, 512))
 
 
 def run_reference(args):
@@ -268,7 +268,7 @@ def run_ours(args):
     h2d = h_in.nbytes + h_types.nbytes + h_idx.nbytes
     d2h = h_out.nbytes
 
-    roof = roofline(best, r, args.gates, p)
+    roof = roofline(best, r, args.gates, p, ctx.tc_level() if best == "tc" else 0)
     line = {
         "metric": METRIC, "value": r["gates_per_s"], "unit": "gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
@@ -311,7 +311,24 @@ def peaks():
                 "sm_max_mhz": 2032.0}, "fallback"
 
 
-def roofline(form, r, G, p):
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+# kernel, from one ncu capture of this bench's 4096-gate level; valid only while the
+# kernel source is byte-identical to the one captured (else reported as null).
+TRAFFIC = {}
+
+
+def kernel_traffic(key, src):
+    rec = TRAFFIC.get(key)
+    if not rec:
+        return None
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2010_09410_b300", "csrc", src), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+            return None
+    return rec["bytes"]
+
+
+def roofline(form, r, G, p, tc_level):
     """Roofline of the dominant kernel of the measured form.
 
     NTT form: k_blind_rotate_ntt, bound by integer ALU throughput.  Algorithmic work per
@@ -322,8 +339,12 @@ def roofline(form, r, G, p):
     integer multiply instructions.  Peak = 148 SMs x 128 lanes x the max SM clock.
 
     TC form: the persistent tensor-core BlindRotate (one launch per level), bound by the
-    bf16 tensor pipe: per gate and step 2 * (2lN) * (2N) * planes flops (planes = 4 byte
-    planes of the key), n steps per launch.
+    bf16 tensor pipe.  Algorithmic work per gate and step: the external product as 2 x 2l
+    dense negacyclic N-products, each N^2 multiply-adds on each of the 4 byte planes of
+    the key, i.e. 2 * (2lN) * (2N) * 4 flops (100.7 M at N = 1024, l = 3); n steps per
+    launch.  With L Karatsuba levels the kernel executes (3/4)^L of that on the tensor
+    pipe, reported as `executed` beside the algorithmic figure.  The launch duration is
+    the stage's event time (accumulator init, a few microseconds, + the kernel).
     """
     mp, kind = peaks()
     logN = p.N.bit_length() - 1
@@ -337,19 +358,25 @@ def roofline(form, r, G, p):
         peak = 148 * 128 * mp.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         return {"bound": "alu", "kernel": "k_blind_rotate_ntt", "achieved": achieved,
                 "peak": peak, "unit": "T int32-mul-op/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": "derived from SM count, lanes and max clock",
+                "traffic": kernel_traffic("k_blind_rotate_ntt", "ntt.cu"),
+                "peak_kind": "derived from SM count, lanes and max clock",
                 "work": f"{mulmods} mulmods/gate-step x 8 int32 multiplies"}
-    ms, launches = r["stages"]["extprod_tc"]
-    per_launch_s = ms / 1e3 / max(launches, 1)
+    ms, kernels = r["stages"]["blind_rotate_tc"]
+    per_launch_s = ms / 1e3 / max(kernels // 2, 1)  # two kernels per BlindRotate
     planes = 4
-    # one launch of k_tc_blind_rotate runs all n steps of the level
     flops = G * steps * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
+    executed = flops * 0.75 ** tc_level
     achieved = flops / per_launch_s / 1e12
     peak = mp["bf16_tflops_sustained"]
-    return {"bound": "tensor", "kernel": "k_tc_blind_rotate", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_kind": f"{kind} bf16 sustained (cuBLAS loop)",
-            "work": f"n*2*(2lN)*(2N)*{planes} flops per gate per launch (dense Toeplitz form)"}
+    return {"bound": "tensor", "kernel": f"k_tc_blind_rotate<{tc_level}>", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": kernel_traffic(f"k_tc_blind_rotate<{tc_level}>", "tc.cu"),
+            "peak_kind": f"bf16 sustained (cuBLAS loop), of {kind}",
+            "work": f"n*2*(2lN)*(2N)*{planes} flops per gate per launch (dense negacyclic "
+                    f"products on 4 key byte planes)",
+            "executed": {"karatsuba_levels": tc_level,
+                         "achieved": executed / per_launch_s / 1e12,
+                         "frac": executed / per_launch_s / 1e12 / peak}}
 
 
 def main():

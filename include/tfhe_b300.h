@@ -123,19 +123,24 @@ int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
  * available for these parameters. */
 int tfhe_ctx_set_tc_level(tfhe_ctx *ctx, int levels);
 
-/* Per-kernel timing (tracing).  When enabled, the context brackets each of its kernel
- * launches with CUDA events on the launching stream (not while the stream is being
+/* The Karatsuba level the tensor-core form runs with (>= 0), or TFHE_EUNSUPPORTED if the
+ * form is not available for these parameters. */
+int tfhe_ctx_tc_level(tfhe_ctx *ctx);
+
+/* Per-kernel timing (tracing).  When enabled, the context brackets the kernel launches of
+ * each stage with CUDA events on the launching stream (not while the stream is being
  * captured into a graph).  tfhe_ctx_stage_times waits for the recorded events, writes
- * the summed device time in milliseconds and the launch count of each stage into
- * ms[TFHE_NUM_STAGES] and launches[TFHE_NUM_STAGES] (either may be NULL), and resets
- * the counters. */
+ * the summed device time in milliseconds and the number of kernel launches of each stage
+ * into ms[TFHE_NUM_STAGES] and launches[TFHE_NUM_STAGES] (either may be NULL), and
+ * resets the counters. */
 enum {
-    TFHE_STAGE_COMBINE = 0,        /* gate linear combination + ModSwitch */
+    TFHE_STAGE_COMBINE = 0,          /* gate linear combination + ModSwitch (one launch) */
     TFHE_STAGE_BLIND_ROTATE_NTT = 1, /* whole BlindRotate, NTT form (one launch) */
-    TFHE_STAGE_DECOMPOSE_TC = 2,   /* rotation + gadget digits, TC form (per step) */
-    TFHE_STAGE_EXTPROD_TC = 3,     /* tensor-core external product, TC form (per step) */
-    TFHE_STAGE_KEYSWITCH = 4,      /* SampleExtract + identity key switch */
-    TFHE_STAGE_CMUX = 5,           /* CMUX batches, tree levels, RAM write */
+    TFHE_STAGE_RESERVED_2 = 2,       /* unused */
+    TFHE_STAGE_BLIND_ROTATE_TC = 3,  /* whole BlindRotate, TC form: accumulator init +
+                                        one persistent launch */
+    TFHE_STAGE_KEYSWITCH = 4,        /* SampleExtract + identity key switch (one launch) */
+    TFHE_STAGE_CMUX = 5,             /* CMUX batches, tree levels, RAM write */
     TFHE_NUM_STAGES = 8
 };
 int tfhe_ctx_enable_timing(tfhe_ctx *ctx, int on);

@@ -34,8 +34,9 @@ EXPORTS = [
     "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_destroy",
     "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times", "tfhe_gate_batch_noalloc",
     "tfhe_ctx_set_tc_level",
+    "tfhe_ctx_tc_level",
 ]
-STAGES = ["combine", "blind_rotate_ntt", "decompose_tc", "extprod_tc", "keyswitch", "cmux"]
+STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
 
 
@@ -87,6 +88,7 @@ def lib():
         "tfhe_ctx_stage_times": (i32, [vp, vp, vp]),
         "tfhe_gate_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, i32, vp]),
         "tfhe_ctx_set_tc_level": (i32, [vp, i32]),
+        "tfhe_ctx_tc_level": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -149,6 +151,12 @@ class Context:
     def set_tc_level(self, levels: int):
         """Karatsuba levels of the tensor-core form (0, 1, 2; -1 = default)."""
         self._check(lib().tfhe_ctx_set_tc_level(self.h, levels), "set_tc_level")
+
+    def tc_level(self) -> int:
+        """Karatsuba level the tensor-core form runs with."""
+        rc = lib().tfhe_ctx_tc_level(self.h)
+        self._check(min(rc, 0), "tc_level")
+        return rc
 
     def enable_timing(self, on: bool = True):
         self._check(lib().tfhe_ctx_enable_timing(self.h, 1 if on else 0), "enable_timing")

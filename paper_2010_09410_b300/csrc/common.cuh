@@ -61,18 +61,23 @@ struct tfhe_ctx {
     // per-kernel timing (tfhe_ctx_enable_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[TFHE_NUM_STAGES];
+    struct StageRecord {
+        cudaEvent_t a, b;
+        int kernels;  // kernel launches between the two events
+    };
+    std::vector<StageRecord> ev_pending[TFHE_NUM_STAGES];
 };
 
-// Brackets one kernel launch with events when timing is on and the stream is not
-// being captured.  Usage: StageTimer t(ctx, stage, st); launch; t.stop();
+// Brackets kernel launches with events when timing is on and the stream is not
+// being captured.  Usage: StageTimer t(ctx, stage, st); launches; t.stop(kernels);
 struct StageTimer {
     tfhe_ctx *ctx;
     int stage;
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
     StageTimer(tfhe_ctx *c, int s, cudaStream_t stream);
-    void stop();
+    void stop(int kernels = 1);
+    ~StageTimer();  // an unstopped timer (error path) returns its events to the pool
 };
 
 // Addressing of a 2-D grid of CMUXes (x within a group sharing one selector, y the
@@ -107,6 +112,7 @@ int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc
 int tfhe_tc_supported(const tfhe_ctx *ctx);
 int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st);
 int tfhe_tc_set_level(tfhe_ctx *ctx, int level);
+int tfhe_tc_level(tfhe_ctx *ctx);
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                          cudaStream_t st);
 int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);

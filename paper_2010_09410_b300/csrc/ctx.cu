@@ -83,8 +83,8 @@ extern "C" void tfhe_ctx_destroy(tfhe_ctx *ctx) {
     free_dev(ctx->d_err);
     for (auto &v : ctx->ev_pending)
         for (auto &pr : v) {
-            cudaEventDestroy(pr.first);
-            cudaEventDestroy(pr.second);
+            cudaEventDestroy(pr.a);
+            cudaEventDestroy(pr.b);
         }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
@@ -205,11 +205,16 @@ StageTimer::StageTimer(tfhe_ctx *c, int s, cudaStream_t stream) : ctx(c), stage(
     if (a && b) cudaEventRecord(a, st);
 }
 
-void StageTimer::stop() {
+void StageTimer::stop(int kernels) {
     if (!a || !b) return;
     cudaEventRecord(b, st);
-    ctx->ev_pending[stage].push_back({a, b});
+    ctx->ev_pending[stage].push_back({a, b, kernels});
     a = b = nullptr;
+}
+
+StageTimer::~StageTimer() {
+    if (a) ctx->ev_pool.push_back(a);
+    if (b) ctx->ev_pool.push_back(b);
 }
 
 extern "C" int tfhe_ctx_enable_timing(tfhe_ctx *ctx, int on) {
@@ -224,17 +229,19 @@ extern "C" int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches
     int rc = TFHE_OK;
     for (int s = 0; s < TFHE_NUM_STAGES; s++) {
         double total = 0;
+        int64_t kernels = 0;
         for (auto &pr : ctx->ev_pending[s]) {
             float t = 0;
-            if (cudaEventSynchronize(pr.second) != cudaSuccess ||
-                cudaEventElapsedTime(&t, pr.first, pr.second) != cudaSuccess)
+            if (cudaEventSynchronize(pr.b) != cudaSuccess ||
+                cudaEventElapsedTime(&t, pr.a, pr.b) != cudaSuccess)
                 rc = tfhe_set_error(ctx, TFHE_ECUDA, "stage_times: event query failed");
             total += t;
-            ctx->ev_pool.push_back(pr.first);
-            ctx->ev_pool.push_back(pr.second);
+            kernels += pr.kernels;
+            ctx->ev_pool.push_back(pr.a);
+            ctx->ev_pool.push_back(pr.b);
         }
         if (ms) ms[s] = total;
-        if (launches) launches[s] = (int64_t)ctx->ev_pending[s].size();
+        if (launches) launches[s] = kernels;
         ctx->ev_pending[s].clear();
     }
     return rc;
@@ -244,4 +251,9 @@ extern "C" int tfhe_ctx_set_tc_level(tfhe_ctx *ctx, int levels) {
     if (!ctx) return TFHE_EINVAL;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     return tfhe_tc_set_level(ctx, levels);
+}
+
+extern "C" int tfhe_ctx_tc_level(tfhe_ctx *ctx) {
+    if (!ctx) return TFHE_EINVAL;
+    return tfhe_tc_level(ctx);
 }

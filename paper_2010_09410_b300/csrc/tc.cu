@@ -950,6 +950,11 @@ int tfhe_tc_set_level(tfhe_ctx *ctx, int level) {
     return TFHE_OK;
 }
 
+int tfhe_tc_level(tfhe_ctx *ctx) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    return ctx->tc && ctx->tc->want_level >= 0 ? ctx->tc->want_level : default_level(ctx->p);
+}
+
 // Per-step job table for `tiles` gate tiles (see the kernel comment for the order).
 static int prepare_table(tfhe_ctx *ctx, int tiles, cudaStream_t st) {
     TcWorkspace *w = ctx->tc;
@@ -1007,12 +1012,6 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         w->sms = sms;
     }
     const int n1 = p.n + 1;
-    {
-        const size_t total = (size_t)G * 2 * p.N;
-        k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, bar, acc);
-        rc = tfhe_check_launch(ctx, "tc_init_acc");
-        if (rc != TFHE_OK) return rc;
-    }
     auto kern = w->level == 0 ? k_tc_blind_rotate<0>
               : (w->level == 1 ? k_tc_blind_rotate<1> : k_tc_blind_rotate<2>);
     const int smem = smem_bytes(p.N);
@@ -1042,9 +1041,15 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.sync = w->sync;
     args.err = ctx->d_err;
     const int grid = (int)(args.total_e < w->sms ? args.total_e : w->sms);
-    StageTimer tm(ctx, TFHE_STAGE_EXTPROD_TC, st);
+    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
+    {
+        const size_t total = (size_t)G * 2 * p.N;
+        k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, bar, acc);
+        rc = tfhe_check_launch(ctx, "tc_init_acc");
+        if (rc != TFHE_OK) return rc;
+    }
     kern<<<grid, P_THREADS, smem, st>>>(args);
-    tm.stop();
+    tm.stop(2);
     return tfhe_check_launch(ctx, "tc blind rotate");
 }
 
