@@ -314,7 +314,11 @@ def peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
 # kernel, from one ncu capture of this bench's 4096-gate level; valid only while the
 # kernel source is byte-identical to the one captured (else reported as null).
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_tc_blind_rotate
+    #   -s 2 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline --form tc
+    "k_tc_blind_rotate<1>": {"bytes": 55.99e9 + 76.61e9, "source_sha256": "13147e6eb8ce6cc77c515422710a19063439b909d3ef4131d1d16efd68e874f1"},
+}
 
 
 def kernel_traffic(key, src):

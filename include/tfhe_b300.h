@@ -106,8 +106,12 @@ const char *tfhe_last_error(const tfhe_ctx *ctx);
 int tfhe_ctx_set_keys(tfhe_ctx *ctx, const uint32_t *bsk, const uint32_t *ksk, void *stream);
 
 /* Pre-size the context's workspaces for batches of up to `max_gates` gates (or
- * CMUXes), so that later calls do not allocate (required before capturing calls
- * in a CUDA graph).  Calls with larger batches grow the workspaces themselves. */
+ * CMUXes), so that later calls do not allocate, and build the tensor-core job table
+ * for exactly `max_gates` gates (tables are per batch size, in tiles of 128 gates).
+ * Required before capturing calls into a CUDA graph yourself: a call that would have
+ * to allocate or upload while its stream is capturing fails with TFHE_ECUDA or
+ * TFHE_EINVAL instead.  Calls with larger batches grow the workspaces themselves;
+ * growing reallocates, so a graph captured earlier must not be replayed after it. */
 int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates);
 
 /* Wait for `stream` and report device-side errors recorded by this context's
@@ -255,7 +259,8 @@ int tfhe_plan_circuit_last_level(const tfhe_plan *plan, int c);
  * order; gate_out: device u32[sum of num_gates][n+1], circuits in order, gates in
  * each circuit's original order.  With use_graph != 0 the level schedule is
  * captured once into a CUDA graph and replayed on later runs with the same
- * pointers and stream.  level_events (optional, may be NULL): array of
+ * pointers; it is re-recorded when the pointers change or when another call has
+ * reallocated a context workspace since (the graph holds their addresses).  level_events (optional, may be NULL): array of
  * tfhe_plan_num_levels() cudaEvent_t (as void*), recorded after each level when
  * use_graph == 0. */
 int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out, int use_graph,

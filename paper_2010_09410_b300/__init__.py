@@ -251,6 +251,9 @@ class Plan:
     def run(self, primary_in, gate_out, use_graph=False, level_events=None, stream=None):
         ev = None
         if level_events is not None:
+            for e in level_events:
+                if not e.cuda_event:  # torch creates the CUDA event at its first record
+                    e.record()
             ev = (ctypes.c_void_p * len(level_events))(*[e.cuda_event for e in level_events])
         self.ctx._check(lib().tfhe_plan_run(self.h, _ptr(primary_in), _ptr(gate_out),
                                             1 if use_graph else 0, ev, _stream(stream)),

@@ -96,11 +96,13 @@ extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
     const tfhe_params &p = ctx->p;
     const size_t per = (size_t)2 * p.l * 2 * p.N;
     if (ctx->ws_gmc_cap < v) {
-        if (ctx->ws_gmc) cudaFree(ctx->ws_gmc);
-        ctx->ws_gmc = nullptr;
-        ctx->ws_gmc_cap = 0;
-        if (cudaMalloc(&ctx->ws_gmc, (size_t)v * per * 4) != cudaSuccess)
-            return tfhe_set_error(ctx, TFHE_ENOMEM, "ram_write: selector workspace");
+        size_t cap = (size_t)ctx->ws_gmc_cap * per * 4;
+        rc = tfhe_grow(ctx, (void **)&ctx->ws_gmc, &cap, (size_t)v * per * 4,
+                       "ram_write: selector workspace");
+        if (rc != TFHE_OK) {
+            if (!ctx->ws_gmc) ctx->ws_gmc_cap = 0;
+            return rc;
+        }
         ctx->ws_gmc_cap = v;
     }
     k_gadget_minus<<<256, 256, 0, st>>>(addr_trgsw, ctx->ws_gmc, v, p.l, p.N, p.Bgbit);

@@ -56,6 +56,12 @@ struct tfhe_ctx {
     TcWorkspace *tc = nullptr;
     int tc_min_width = 128;  // plan autotuner: narrowest level run in the tensor-core form
 
+    // Workspace generation: bumped by every reallocation of a context-owned buffer, so a
+    // captured plan graph (which holds raw addresses) knows to re-record itself.  While
+    // `capturing` is set no buffer may be reallocated.
+    uint64_t mem_gen = 0;
+    bool capturing = false;
+
     int *d_err = nullptr;  // device error word (0 = ok, else a TFHE_E* code)
 
     // per-kernel timing (tfhe_ctx_enable_timing)
@@ -112,6 +118,10 @@ int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc
 int tfhe_tc_supported(const tfhe_ctx *ctx);
 int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st);
 int tfhe_tc_set_level(tfhe_ctx *ctx, int level);
+int tfhe_tc_reserve(tfhe_ctx *ctx, int gates);  // tensor-core buffers + job table for `gates`
+// Reallocate a context-owned device buffer to at least `need` bytes (no copy); refused
+// while a plan graph is being recorded; bumps mem_gen.
+int tfhe_grow(tfhe_ctx *ctx, void **ptr, size_t *cap_bytes, size_t need, const char *what);
 int tfhe_tc_level(tfhe_ctx *ctx);
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                          cudaStream_t st);

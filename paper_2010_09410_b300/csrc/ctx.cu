@@ -134,8 +134,24 @@ extern "C" int tfhe_ctx_set_keys(tfhe_ctx *ctx, const uint32_t *bsk, const uint3
     return TFHE_OK;
 }
 
+int tfhe_grow(tfhe_ctx *ctx, void **ptr, size_t *cap_bytes, size_t need, const char *what) {
+    if (need <= *cap_bytes) return TFHE_OK;
+    if (ctx->capturing)
+        return tfhe_set_error(ctx, TFHE_EINVAL,
+                              std::string(what) + ": buffer too small while recording a graph");
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap_bytes = 0;
+    ctx->mem_gen++;
+    if (cudaMalloc(ptr, need) != cudaSuccess) return tfhe_set_error(ctx, TFHE_ENOMEM, what);
+    *cap_bytes = need;
+    return TFHE_OK;
+}
+
 int tfhe_ensure_workspace(tfhe_ctx *ctx, int gates) {
     if (gates <= ctx->ws_cap) return TFHE_OK;
+    if (ctx->capturing)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "workspace too small while recording a graph");
     const tfhe_params &p = ctx->p;
     const int cap = gates;
     free_dev(ctx->ws_bar);
@@ -143,6 +159,7 @@ int tfhe_ensure_workspace(tfhe_ctx *ctx, int gates) {
     free_dev(ctx->ws_tmp);
     ctx->ws_bar = ctx->ws_acc = ctx->ws_tmp = nullptr;
     ctx->ws_cap = 0;
+    ctx->mem_gen++;
     if (cudaMalloc(&ctx->ws_bar, (size_t)cap * (p.n + 1) * 4) != cudaSuccess ||
         cudaMalloc(&ctx->ws_acc, (size_t)cap * 2 * p.N * 4) != cudaSuccess ||
         cudaMalloc(&ctx->ws_tmp, (size_t)cap * 2 * p.N * 4) != cudaSuccess)
@@ -152,21 +169,23 @@ int tfhe_ensure_workspace(tfhe_ctx *ctx, int gates) {
 }
 
 int tfhe_ensure_trgsw_ws(tfhe_ctx *ctx, size_t count) {
-    if (count <= ctx->ws_trgsw_cap) return TFHE_OK;
-    free_dev(ctx->ws_trgsw_ntt);
-    ctx->ws_trgsw_ntt = nullptr;
-    ctx->ws_trgsw_cap = 0;
-    const size_t words = count * 2 * ctx->p.l * 2 * ctx->p.N;
-    if (cudaMalloc(&ctx->ws_trgsw_ntt, words * 8) != cudaSuccess)
-        return tfhe_set_error(ctx, TFHE_ENOMEM, "TRGSW workspace allocation");
-    ctx->ws_trgsw_cap = count;
+    size_t cap = ctx->ws_trgsw_cap * 2 * ctx->p.l * 2 * ctx->p.N * 8;
+    const size_t need = count * 2 * ctx->p.l * 2 * ctx->p.N * 8;
+    int rc = tfhe_grow(ctx, (void **)&ctx->ws_trgsw_ntt, &cap, need, "TRGSW workspace allocation");
+    if (rc != TFHE_OK) {
+        if (!ctx->ws_trgsw_ntt) ctx->ws_trgsw_cap = 0;
+        return rc;
+    }
+    if (count > ctx->ws_trgsw_cap) ctx->ws_trgsw_cap = count;
     return TFHE_OK;
 }
 
 extern "C" int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates) {
     if (!ctx || max_gates < 0) return TFHE_EINVAL;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    return tfhe_ensure_workspace(ctx, max_gates);
+    const int rc = tfhe_ensure_workspace(ctx, max_gates);
+    if (rc != TFHE_OK) return rc;
+    return tfhe_tc_reserve(ctx, max_gates);
 }
 
 extern "C" int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream) {

@@ -237,14 +237,7 @@ extern "C" int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group,
 }
 
 static int grow(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need) {
-    if (need <= *cap) return TFHE_OK;
-    if (*ptr) cudaFree(*ptr);
-    *ptr = nullptr;
-    *cap = 0;
-    if (cudaMalloc(ptr, need) != cudaSuccess)
-        return tfhe_set_error(ctx, TFHE_ENOMEM, "host-API staging allocation");
-    *cap = need;
-    return TFHE_OK;
+    return tfhe_grow(ctx, ptr, cap, need, "host-API staging allocation");
 }
 
 extern "C" int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,

@@ -23,6 +23,7 @@ struct tfhe_plan {
     cudaGraphExec_t exec = nullptr;
     const uint32_t *g_in = nullptr;
     uint32_t *g_out = nullptr;
+    uint64_t g_gen = 0;  // context workspace generation the graph was recorded with
     cudaStream_t g_stream = nullptr;
 };
 
@@ -53,6 +54,20 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
 static int tfhe_plan_pick_form(tfhe_ctx *ctx, int64_t width) {
     if (!tfhe_tc_supported(ctx)) return TFHE_FORM_NTT;
     return width >= ctx->tc_min_width ? TFHE_FORM_TC : TFHE_FORM_NTT;
+}
+
+// Size the context's workspaces for every level of the plan (a later call of another
+// size may have changed them since the plan was built).
+static int plan_reserve(tfhe_plan *plan) {
+    tfhe_ctx *ctx = plan->ctx;
+    int64_t max_w = 0;
+    for (int L = 0; L < plan->num_levels; L++)
+        max_w = std::max(max_w, plan->level_off[L + 1] - plan->level_off[L]);
+    int rc = tfhe_ensure_workspace(ctx, (int)max_w);
+    for (int L = 0; L < plan->num_levels && rc == TFHE_OK; L++)
+        if (plan->level_form[L] == TFHE_FORM_TC)
+            rc = tfhe_tc_reserve(ctx, (int)(plan->level_off[L + 1] - plan->level_off[L]));
+    return rc;
 }
 
 extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, int num_circuits,
@@ -161,7 +176,7 @@ extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, in
         tfhe_plan_destroy(plan);
         return tfhe_set_error(ctx, TFHE_ECUDA, "circuit_plan: upload");
     }
-    int rc = tfhe_ensure_workspace(ctx, (int)max_w);
+    const int rc = plan_reserve(plan);  // tensor-core levels: a job table for every width
     if (rc != TFHE_OK) {
         tfhe_plan_destroy(plan);
         return rc;
@@ -214,16 +229,22 @@ extern "C" int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32
     cudaStream_t st = (cudaStream_t)stream;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     if (!use_graph) return plan_enqueue(plan, primary_in, gate_out, level_events, st);
-    if (!plan->exec || plan->g_in != primary_in || plan->g_out != gate_out) {
+    if (!plan->exec || plan->g_in != primary_in || plan->g_out != gate_out ||
+        plan->g_gen != ctx->mem_gen) {
         if (plan->exec) cudaGraphExecDestroy(plan->exec);
         if (plan->graph) cudaGraphDestroy(plan->graph);
         plan->exec = nullptr;
         plan->graph = nullptr;
         if (!plan->cap_stream)
             TFHE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+        // size every workspace first: nothing may be reallocated while recording
+        int rc = plan_reserve(plan);
+        if (rc != TFHE_OK) return rc;
         TFHE_CUDA_TRY(ctx, cudaStreamBeginCapture(plan->cap_stream,
                                                   cudaStreamCaptureModeThreadLocal));
-        int rc = plan_enqueue(plan, primary_in, gate_out, nullptr, plan->cap_stream);
+        ctx->capturing = true;
+        rc = plan_enqueue(plan, primary_in, gate_out, nullptr, plan->cap_stream);
+        ctx->capturing = false;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(plan->cap_stream, &g);
         if (rc != TFHE_OK) {
@@ -237,6 +258,7 @@ extern "C" int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32
         TFHE_CUDA_TRY(ctx, cudaGraphInstantiate(&plan->exec, g, 0));
         plan->g_in = primary_in;
         plan->g_out = gate_out;
+        plan->g_gen = ctx->mem_gen;
     }
     TFHE_CUDA_TRY(ctx, cudaGraphLaunch(plan->exec, st));
     return TFHE_OK;

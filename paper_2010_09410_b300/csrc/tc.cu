@@ -38,6 +38,7 @@
 // One launch of k_tc_blind_rotate runs all n steps.  Every wait polls a bounded number
 // of times; on time-out the block records TFHE_ETIMEOUT in the context's error word and
 // winds down.
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -863,10 +864,11 @@ struct TcWorkspace {
     size_t digits_cap = 0;     // bytes
     uint32_t *sync = nullptr;  // job counter and per-tile progress counters
     size_t sync_cap = 0;       // words
-    uint32_t *table = nullptr; // per-step job table
-    size_t table_cap = 0;      // entries
-    int table_tiles = -1;
-    int table_len = 0;
+    struct JobTable {
+        uint32_t *d = nullptr;  // per-step product-job table
+        int len = 0;            // entries
+    };
+    std::map<int, JobTable> tables;  // by gate-tile count (kept: captured graphs use them)
     int sms = 0;
     int want_level = -1;       // requested Karatsuba levels (-1: default)
 };
@@ -892,25 +894,25 @@ void tfhe_tc_free(tfhe_ctx *ctx) {
     if (w->win) cudaFree(w->win);
     if (w->digits) cudaFree(w->digits);
     if (w->sync) cudaFree(w->sync);
-    if (w->table) cudaFree(w->table);
+    for (auto &t : w->tables) cudaFree(t.second.d);
     delete w;
     ctx->tc = nullptr;
 }
 
 static int grow_dev(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need, const char *what) {
-    if (need <= *cap) return TFHE_OK;
-    if (*ptr) cudaFree(*ptr);
-    *ptr = nullptr;
-    *cap = 0;
-    if (cudaMalloc(ptr, need) != cudaSuccess) return tfhe_set_error(ctx, TFHE_ENOMEM, what);
-    *cap = need;
-    return TFHE_OK;
+    return tfhe_grow(ctx, ptr, cap, need, what);
 }
 
 // (Re)build the term plan and expand the windows of the whole BSK for `level`.
 static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
     TcWorkspace *w = ctx->tc;
+    if (ctx->capturing)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core windows: cannot rebuild while recording");
+    // job tables depend on the term plan
+    for (auto &t : w->tables) cudaFree(t.second.d);
+    w->tables.clear();
+    ctx->mem_gen++;
     build_plan(p.N, level, w->terms);
     const int T = (int)w->terms.size();
     const int s = p.N >> level;
@@ -927,7 +929,6 @@ static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     rc = tfhe_check_launch(ctx, "tc_windows");
     if (rc != TFHE_OK) return rc;
     w->level = level;
-    w->table_tiles = -1;  // job table depends on the plan
     return TFHE_OK;
 }
 
@@ -956,9 +957,15 @@ int tfhe_tc_level(tfhe_ctx *ctx) {
 }
 
 // Per-step job table for `tiles` gate tiles (see the kernel comment for the order).
-static int prepare_table(tfhe_ctx *ctx, int tiles, cudaStream_t st) {
+static int prepare_table(tfhe_ctx *ctx, int tiles, const TcWorkspace::JobTable **out) {
     TcWorkspace *w = ctx->tc;
-    if (w->table_tiles == tiles) return TFHE_OK;
+    auto it = w->tables.find(tiles);
+    if (it != w->tables.end()) {
+        *out = &it->second;
+        return TFHE_OK;
+    }
+    if (ctx->capturing)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core job table missing while recording a graph");
     const int s = ctx->p.N >> w->level;
     const int bpp = s / NB;
     int nphase = 0;
@@ -974,16 +981,44 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, cudaStream_t st) {
                 for (int c = 0; c < 2; c++)
                     for (int b = 0; b < bpp; b++) tab.push_back(pack_job(JOB_E, gt, j, c, b, dep));
             }
-
         }
     }
-    int rc = grow_dev(ctx, (void **)&w->table, &w->table_cap, tab.size() * 4, "tensor-core job table");
-    if (rc != TFHE_OK) return rc;
-    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(w->table, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
-    TFHE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // the host vector goes out of scope
-    w->table_tiles = tiles;
-    w->table_len = (int)tab.size();
+    TcWorkspace::JobTable t;
+    if (cudaMalloc(&t.d, tab.size() * 4) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core job table");
+    if (cudaMemcpy(t.d, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t.d);
+        return tfhe_set_error(ctx, TFHE_ECUDA, "tensor-core job table upload");
+    }
+    t.len = (int)tab.size();
+    *out = &(w->tables[tiles] = t);
     return TFHE_OK;
+}
+
+// Buffers and job table of a G-gate BlindRotate, sized before the first launch (and
+// before a graph that contains it is recorded).
+static int reserve_tc(tfhe_ctx *ctx, int G, const TcWorkspace::JobTable **table) {
+    const tfhe_params &p = ctx->p;
+    TcWorkspace *w = ctx->tc;
+    const int tiles = (G + TILE_M - 1) / TILE_M;
+    const int T = (int)w->terms.size();
+    const int s = p.N >> w->level;
+    int rc = grow_dev(ctx, (void **)&w->digits, &w->digits_cap,
+                      (size_t)tiles * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
+    if (rc != TFHE_OK) return rc;
+    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles) * 4,
+                  "tensor-core progress counters");
+    if (rc != TFHE_OK) return rc;
+    const TcWorkspace::JobTable *t = nullptr;
+    rc = prepare_table(ctx, tiles, &t);
+    if (rc == TFHE_OK && table) *table = t;
+    return rc;
+}
+
+int tfhe_tc_reserve(tfhe_ctx *ctx, int gates) {
+    if (gates <= 0 || !tfhe_tc_supported(ctx) || !ctx->tc || !ctx->tc->win || ctx->tc->level < 0)
+        return TFHE_OK;  // nothing to size before the keys are loaded
+    return reserve_tc(ctx, gates, nullptr);
 }
 
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
@@ -998,13 +1033,8 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     const int tiles = (G + TILE_M - 1) / TILE_M;
     const int T = (int)w->terms.size();
     const int s = p.N >> w->level;
-    int rc = grow_dev(ctx, (void **)&w->digits, &w->digits_cap,
-                      (size_t)tiles * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
-    if (rc != TFHE_OK) return rc;
-    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles) * 4,
-                  "tensor-core progress counters");
-    if (rc != TFHE_OK) return rc;
-    rc = prepare_table(ctx, tiles, st);
+    const TcWorkspace::JobTable *table = nullptr;
+    int rc = reserve_tc(ctx, G, &table);
     if (rc != TFHE_OK) return rc;
     if (!w->sms) {
         int sms = 0;
@@ -1029,10 +1059,10 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.tiles = tiles;
     args.cbs = 2 * (s / NB);
     args.e_per_tile = T * 2 * (s / NB);
-    args.step_len = w->table_len;
-    args.total_e = (long long)p.n * w->table_len;
+    args.step_len = table->len;
+    args.total_e = (long long)p.n * table->len;
     args.total_d = (long long)p.n * tiles * DPARTS;
-    args.table = w->table;
+    args.table = table->d;
     args.terms = w->d_terms;
     args.bar = bar;
     args.acc = acc;

@@ -45,3 +45,16 @@ def test_toy_dag_matches_oracle(torch_cuda, form):
     plan.run(dev_in, out2, use_graph=True)
     ctx.sync()
     assert np.array_equal(from_dev(out2), want)
+    # a wider batch reallocates the context's workspaces; the plan must notice and
+    # record its graph again instead of replaying stale addresses
+    G = 5000  # wider than any toy batch of the other tests
+    bits = ti.random_bits(ti.SEED_TOY, 70, 2 * G)
+    b_in = to_dev(ti.encrypt_tlwe0_bits(p, ti.SEED_TOY, 71, k.s0, bits))
+    b_types = to_dev(ti.random_below(ti.SEED_TOY, 72, G, 10).astype(np.uint8))
+    b_idx = to_dev(np.arange(2 * G, dtype=np.int32).reshape(G, 2))
+    b_out = torch_cuda.zeros((G, p.n + 1), dtype=torch_cuda.int32, device="cuda")
+    ctx.gate_batch(b_in, b_types, b_idx, b_out, form=max(form, 0))
+    out3 = torch_cuda.zeros_like(out)
+    plan.run(dev_in, out3, use_graph=True)
+    ctx.sync()
+    assert np.array_equal(from_dev(out3), want)
