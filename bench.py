@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-level", type=int, default=-1,
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
+    ap.add_argument("--tc-variant", type=int, default=-1,
+                    help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
     return ap.parse_args()
 
 
@@ -183,6 +185,8 @@ def run_ours(args):
     ctx.reserve(args.gates)
     if args.tc_level >= 0:
         ctx.set_tc_level(args.tc_level)
+    if args.tc_variant >= 0:
+        ctx.set_tc_variant(args.tc_variant)
     ctx.sync()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(
         np.int32 if a.dtype == np.uint32 else a.dtype)).cuda()
@@ -276,6 +280,9 @@ def run_ours(args):
         "dtype": "u32" if best == "ntt" else "bf16 (exact integer planes) -> u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "gates": args.gates, "form": best,
+                   **({"tc_level": ctx.tc_level(),
+                       "tc_variant": ["single SM", "SM pair"][ctx.tc_variant()]}
+                      if best == "tc" else {}),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "forms": {n: ({"gates_per_s": v["gates_per_s"], "ms_per_step": v["ms_per_step"],
@@ -348,7 +355,8 @@ def roofline(form, r, G, p, tc_level):
     the key, i.e. 2 * (2lN) * (2N) * 4 flops (100.7 M at N = 1024, l = 3); n steps per
     launch.  With L Karatsuba levels the kernel executes (3/4)^L of that on the tensor
     pipe, reported as `executed` beside the algorithmic figure.  The launch duration is
-    the stage's event time (accumulator init, a few microseconds, + the kernel).
+    the stage's event time (accumulator init and final re-layout, tens of microseconds,
+    + the kernel).
     """
     mp, kind = peaks()
     logN = p.N.bit_length() - 1
@@ -366,7 +374,7 @@ def roofline(form, r, G, p, tc_level):
                 "peak_kind": "derived from SM count, lanes and max clock",
                 "work": f"{mulmods} mulmods/gate-step x 8 int32 multiplies"}
     ms, kernels = r["stages"]["blind_rotate_tc"]
-    per_launch_s = ms / 1e3 / max(kernels // 2, 1)  # two kernels per BlindRotate
+    per_launch_s = ms / 1e3 / max(kernels // 3, 1)  # three kernels per BlindRotate
     planes = 4
     flops = G * steps * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
     executed = flops * 0.75 ** tc_level

@@ -119,8 +119,8 @@ int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates);
  * device error word. */
 int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
 
-/* Karatsuba levels of the tensor-core form (0, 1 or 2; -1 selects the default: 1 for
- * N >= 512, else 0).  Level L computes each negacyclic product as 3^L Toeplitz products of
+/* Karatsuba levels of the tensor-core form (0, 1 or 2; -1 selects the default: 2 for
+ * N >= 1024, 1 for N = 512, else 0).  Level L computes each negacyclic product as 3^L Toeplitz products of
  * size N / 2^L (3/4 of the multiply-adds per level); results are identical for every
  * level.  Needs N / 2^L >= 128.  If keys are loaded, re-expands the key windows on the
  * legacy default stream.  TFHE_EUNSUPPORTED if the tensor-core form or level is not
@@ -130,6 +130,18 @@ int tfhe_ctx_set_tc_level(tfhe_ctx *ctx, int levels);
 /* The Karatsuba level the tensor-core form runs with (>= 0), or TFHE_EUNSUPPORTED if the
  * form is not available for these parameters. */
 int tfhe_ctx_tc_level(tfhe_ctx *ctx);
+
+/* How the tensor-core BlindRotate maps onto SMs.  TFHE_TC_SINGLE_SM: each SM multiplies
+ * 128-gate tiles on its own (M = 128 MMAs).  TFHE_TC_SM_PAIR: thread-block clusters of
+ * two SMs multiply 256-gate tile pairs together (M = 256 MMAs over both SMs' shared
+ * memory and TMEM), so each SM stages only half of every key window.  -1 selects the
+ * default, TFHE_TC_SINGLE_SM (faster on B300 at N = 1024).  Results are identical.
+ * Applies to calls made after it (a captured plan graph keeps the variant it was
+ * recorded with until it is recorded again).  tfhe_ctx_tc_variant returns the variant
+ * in use.  TFHE_EUNSUPPORTED if the tensor-core form is not available. */
+enum { TFHE_TC_SINGLE_SM = 0, TFHE_TC_SM_PAIR = 1 };
+int tfhe_ctx_set_tc_variant(tfhe_ctx *ctx, int variant);
+int tfhe_ctx_tc_variant(tfhe_ctx *ctx);
 
 /* Per-kernel timing (tracing).  When enabled, the context brackets the kernel launches of
  * each stage with CUDA events on the launching stream (not while the stream is being

@@ -23,6 +23,8 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPO
 FORM_NTT = 0
 FORM_TC = 1
 FORM_AUTO = -1
+TC_SINGLE_SM = 0
+TC_SM_PAIR = 1
 GATES = ["NAND", "AND", "OR", "NOR", "XOR", "XNOR", "ANDNY", "ANDYN", "ORNY", "ORYN"]
 
 # every symbol the public header declares
@@ -35,6 +37,8 @@ EXPORTS = [
     "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times", "tfhe_gate_batch_noalloc",
     "tfhe_ctx_set_tc_level",
     "tfhe_ctx_tc_level",
+    "tfhe_ctx_set_tc_variant",
+    "tfhe_ctx_tc_variant",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -89,6 +93,8 @@ def lib():
         "tfhe_gate_batch_noalloc": (i32, [vp, vp, i64, vp, vp, vp, i32, vp]),
         "tfhe_ctx_set_tc_level": (i32, [vp, i32]),
         "tfhe_ctx_tc_level": (i32, [vp]),
+        "tfhe_ctx_set_tc_variant": (i32, [vp, i32]),
+        "tfhe_ctx_tc_variant": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -156,6 +162,15 @@ class Context:
         """Karatsuba level the tensor-core form runs with."""
         rc = lib().tfhe_ctx_tc_level(self.h)
         self._check(min(rc, 0), "tc_level")
+        return rc
+
+    def set_tc_variant(self, variant: int):
+        """TC_SINGLE_SM, TC_SM_PAIR or -1 (default) for the tensor-core BlindRotate."""
+        self._check(lib().tfhe_ctx_set_tc_variant(self.h, variant), "set_tc_variant")
+
+    def tc_variant(self) -> int:
+        rc = lib().tfhe_ctx_tc_variant(self.h)
+        self._check(min(rc, 0), "tc_variant")
         return rc
 
     def enable_timing(self, on: bool = True):

@@ -276,3 +276,15 @@ extern "C" int tfhe_ctx_tc_level(tfhe_ctx *ctx) {
     if (!ctx) return TFHE_EINVAL;
     return tfhe_tc_level(ctx);
 }
+
+extern "C" int tfhe_ctx_set_tc_variant(tfhe_ctx *ctx, int variant) {
+    if (!ctx) return TFHE_EINVAL;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return tfhe_tc_set_variant(ctx, variant);
+}
+
+extern "C" int tfhe_ctx_tc_variant(tfhe_ctx *ctx) {
+    if (!ctx) return TFHE_EINVAL;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return tfhe_tc_variant(ctx);
+}

@@ -35,9 +35,19 @@
 // Digits of term j are written per 128-gate tile in the A-operand layout:
 // [tile][term j][row r < 2l][stage < s/KS] blocks of 32 KB, each [mg < 16][kb < 16]
 // [m8 < 8][8 bf16] for gate m = 8 mg + m8 and digit index k' = stage*KS + 8 kb + e.
+// The accumulators live gate-fastest within tiles ([tile][c][word][128 gates]) while the
+// BlindRotate runs, so the read-out warps' read-modify-writes and the digit jobs' loads
+// are whole 128-byte lines; the caller's [G][2][N] layout is written at the end.
 // One launch of k_tc_blind_rotate runs all n steps.  Every wait polls a bounded number
 // of times; on time-out the block records TFHE_ETIMEOUT in the context's error word and
 // winds down.
+//
+// SM pairs (optional): a cluster of two CTAs multiplies a 256-gate tile pair with
+// cta_group::2 MMAs of M = 256; each CTA stages its own tile's digits and half of the key
+// window columns.  CTA 0 fetches the jobs, mirrors them into CTA 1's job ring and issues
+// the MMAs; CTA 1's MMA warp forwards "stage full" to CTA 0; commits arrive on both CTAs'
+// barriers.
+#include <algorithm>
 #include <map>
 #include <vector>
 
@@ -54,9 +64,16 @@ constexpr int A_STAGE_BYTES = TILE_M * KS * 2;            // 32 KB
 constexpr int B_UNITS = NB + KS;                          // units per plane and stage
 constexpr int B_PLANE_BYTES = B_UNITS * 16;               // 4 KB
 constexpr int B_STAGE_BYTES = PLANES * B_PLANE_BYTES;     // 16 KB
-// digit staging: one accumulator polynomial of 8 gates, rows padded by 4 words
-__host__ __device__ constexpr int smem_bytes(int N) {
-    return STAGES * (A_STAGE_BYTES + B_STAGE_BYTES) + 8 * (N + 4) * 4;
+// SM-pair form: each CTA of the pair stages half of the B columns of a column block
+constexpr int PB_COLS = NB / 2;
+constexpr int PB_UNITS = PB_COLS + KS;                     // units per plane and stage
+constexpr int PB_PLANE_BYTES = PB_UNITS * 16;              // 3 KB
+constexpr int PB_STAGE_BYTES = PLANES * PB_PLANE_BYTES;    // 12 KB
+__host__ __device__ constexpr int b_plane_bytes(bool pair) { return pair ? PB_PLANE_BYTES : B_PLANE_BYTES; }
+__host__ __device__ constexpr int b_stage_bytes(bool pair) { return pair ? PB_STAGE_BYTES : B_STAGE_BYTES; }
+// stages + digit staging (one accumulator polynomial of 8 gates, rows padded by 4 words)
+__host__ __device__ constexpr int smem_bytes(int N, bool pair) {
+    return STAGES * (A_STAGE_BYTES + b_stage_bytes(pair)) + 8 * (N + 4) * 4;
 }
 constexpr long long WAIT_CYCLES = 4000000000LL;           // ~2 s at 2 GHz
 
@@ -95,13 +112,51 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with cluster-scope acquire: for barriers that the peer CTA of a pair arrives
+// on, so that the peer's writes before its arrival are visible after the wait.
+__device__ __forceinline__ bool mbar_test_cl(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// ---- thread-block-cluster (SM pair) wrappers ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of this CTA's variable `p` in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+                 : "memory");
+}
+__device__ __forceinline__ void st_remote_u32(uint32_t caddr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
 // Bounded wait for the phase with the given parity to complete.  Returns false (and
 // raises the block's abort flag and the error word) on time-out or when another role
-// has already aborted.
+// has already aborted.  CL: cluster-scope acquire (barriers the peer CTA arrives on).
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
                                           int *err) {
     const long long t0 = clock64();
-    while (!mbar_test(bar, parity)) {
+    while (!(CL ? mbar_test_cl(bar, parity) : mbar_test(bar, parity))) {
         if (*abort) return false;
         if (clock64() - t0 > WAIT_CYCLES) {
             *abort = 1;
@@ -114,12 +169,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 
 // mbar_wait for a whole warp: lane 0 polls, the others sleep in the shuffle, so 32 threads
 // do not compete for issue slots with the MMA and copy threads while they wait.
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort,
                                                int *err) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, err);
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait<CL>(bar, parity, abort, err);
     ok = __shfl_sync(0xffffffffu, ok, 0);
-    return ok && mbar_test(bar, parity);
+    return ok && (CL ? mbar_test_cl(bar, parity) : mbar_test(bar, parity));
 }
 
 // Bounded wait that ignores the abort flag: used to let this block's own asynchronous
@@ -137,16 +193,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the destination with 0.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -181,6 +227,34 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Pair form: one thread of the even CTA issues an M = 256 MMA whose A rows 0-127 and
+// B columns 0 .. N/2-1 come from its own shared memory and A rows 128-255 and B columns
+// N/2 .. N-1 from the odd CTA's (same offsets); rows 0-127 of D go to the even CTA's
+// TMEM, rows 128-255 to the odd CTA's.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+// arrive on `bar` (same offset) in both CTAs of the pair once the issued MMAs are done
+__device__ __forceinline__ void mma_commit_pair_both(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+// arrive on `bar` in the issuing CTA only
+__device__ __forceinline__ void mma_commit_pair_own(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -277,19 +351,46 @@ __global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, int s, i
     }
 }
 
+// The tensor-core path keeps its accumulators gate-fastest within 128-gate tiles:
+// word k of polynomial c of gate g = 128 t + m sits at acc_t[((t * 2 + c) * N + k) * 128 + m],
+// so a warp's 32 gates touch one 128-byte line per word.
+//
 // ACC = X^{-b~} (0, v), v_j = mu: coefficient j of X^{-b~} v is +mu when (j + b~) mod 2N < N.
-__global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__ bar,
-                              uint32_t *__restrict__ acc) {
+// Gates >= G (padding of the last tile) start at zero.
+__global__ void k_tc_init_acc(int N, int n1, int G, int tiles, const uint32_t *__restrict__ bar,
+                              uint32_t *__restrict__ acc_t) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)G * 2 * N) return;
-    const size_t g = e / (2 * N);
-    const int j = (int)(e % (2 * N));
+    if (e >= (size_t)tiles * 2 * N * TILE_M) return;
+    const int m = (int)(e % TILE_M);
+    const size_t r = e / TILE_M;
+    const int k = (int)(r % N);
+    const int c = (int)((r / N) % 2);
+    const size_t g = (r / (2 * (size_t)N)) * TILE_M + m;
     const uint32_t mu = 1u << 29;
-    if (j < N) {
-        acc[e] = 0;
+    if (c == 0 || g >= (size_t)G) {
+        acc_t[e] = 0;
     } else {
         const int bb = (int)(bar[g * n1 + n1 - 1] % (uint32_t)(2 * N));
-        acc[e] = (((j - N) + bb) % (2 * N)) < N ? mu : 0u - mu;
+        acc_t[e] = ((k + bb) % (2 * N)) < N ? mu : 0u - mu;
+    }
+}
+
+// acc[g][c][k] = acc_t word (g, c, k): 32 x 32 blocks through shared memory.
+// grid (N / 32, 4 * tiles, 2), block (32, 8).
+__global__ void k_tc_untile_acc(int N, int G, const uint32_t *__restrict__ acc_t,
+                                uint32_t *__restrict__ acc) {
+    __shared__ uint32_t t[32][33];
+    const int k0 = blockIdx.x * 32, g0 = blockIdx.y * 32, c = blockIdx.z;
+    const int tile = g0 / TILE_M, m0 = g0 % TILE_M;
+    const uint32_t *src = acc_t + ((size_t)(tile * 2 + c) * N + k0) * TILE_M + m0;
+#pragma unroll
+    for (int i = 0; i < 32; i += 8)
+        t[threadIdx.y + i][threadIdx.x] = src[(size_t)(threadIdx.y + i) * TILE_M + threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const int g = g0 + threadIdx.y + i;
+        if (g < G) acc[((size_t)g * 2 + c) * N + k0 + threadIdx.x] = t[threadIdx.x][threadIdx.y + i];
     }
 }
 
@@ -301,7 +402,8 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 // term j for column block b of output polynomial c, added (with signs) into ACC.
 // Two job streams, each taken in order from its own global counter: digit jobs (step,
 // tile, part) by the digit warps of any block, product jobs (step, then a per-step table:
-// phase by phase, all tiles per phase) by the loaders.  With D(i) < E(i) < D(i+1) a job
+// each tile's phases in order, later phases of a tile staggered about one wave of SMs
+// behind its earlier ones) by the loaders.  With D(i) < E(i) < D(i+1) a job
 // only waits for jobs earlier in that order, each stream is handed out in order, and no
 // role holds anything a later job needs, so the schedule cannot deadlock:
 //   stages of E(i, gt, ...) wait for done_D[gt] >= 16 (i+1);
@@ -311,8 +413,8 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 // Every wait is bounded.
 //
 // Warp roles (448 threads): warps 0-7 read TMEM out (warp w owns lanes 32(w%4)..+31 and
-// columns 64(w/4)..+63 of the block), warp 8 fetches jobs and streams stages with
-// cp.async.bulk, warp 9 owns TMEM and one lane issues the MMAs, warps 10-13 compute
+// columns 64(w/4)..+63 of the block), warp 8 owns TMEM and one lane issues the MMAs,
+// warp 12 fetches jobs and streams stages with cp.async.bulk, warps 9-11 and 13 compute
 // digits.  The four planes of TMEM are handed
 // back one by one after each K-half's read-out, so the next half's MMAs on plane p start
 // as soon as plane p has been read; both halves of a job accumulate in registers and the
@@ -321,9 +423,12 @@ __global__ void k_tc_init_acc(int N, int n1, int G, const uint32_t *__restrict__
 constexpr int P_THREADS = 448;
 constexpr int EPI_WARPS = 8;                 // read-out warps: 2 per TMEM lane quarter
 constexpr int EPI_THREADS = EPI_WARPS * 32;
-constexpr int LOAD_WARP = EPI_WARPS;         // job fetch + stage loads
-constexpr int MMA_WARP = EPI_WARPS + 1;      // TMEM owner + MMA issue
-constexpr int DIG_WARP0 = EPI_WARPS + 2;     // 4 digit warps
+// A warp issues on SM sub-partition (warp index mod 4).  The MMA-issuing warp shares its
+// sub-partition only with the loader and two read-out warps; the ALU-heavy digit warps
+// (9, 10, 11, 13) sit on the other three.
+constexpr int MMA_WARP = 8;                  // TMEM owner + MMA issue
+constexpr int LOAD_WARP = 12;                // job fetch + stage loads
+__device__ __forceinline__ int digit_warp_index(int warp) { return warp == 13 ? 3 : warp - 9; }
 constexpr int EPI_COLS = NB / 2;             // columns per read-out warp
 // read-out conversion constants: 1.5*2^23 and its bit pattern; the initial sum cancels the
 // bit-pattern offset added by both K-halves of all four planes (mod 2^32)
@@ -331,6 +436,7 @@ constexpr float RO_MAGIC = 12582912.0f;
 constexpr uint32_t RO_MAGIC_BITS = 0x4B400000u;
 constexpr float RO_FAST_LIMIT = 4194304.0f;  // 2^22
 constexpr int RO_COLS = 32;                   // columns per TMEM load slice
+constexpr int RMW_BATCH = 16;                 // accumulator loads in flight per thread
 constexpr uint32_t RO_SUM_INIT =
     0u - 2u * (RO_MAGIC_BITS + (RO_MAGIC_BITS << 8) + (RO_MAGIC_BITS << 16) + (RO_MAGIC_BITS << 24));
 constexpr int JQ = 8;       // job ring depth
@@ -354,6 +460,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
+// gpu-scope release increment of a progress counter (pairs with ld_acquire)
+__device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool wait_count(const uint32_t *p, uint32_t target, volatile int *abort,
                                            int *err) {
     const long long t0 = clock64();
@@ -373,13 +484,14 @@ struct BrArgs {
     int N, l, Bgbit, G, n, n1;
     int s, nterms;              // term size N / 2^L and count 3^L
     int tiles, cbs;             // gate tiles, column blocks per term output (2 * s / NB)
+    int tiles_pad;              // tiles rounded up to the pair size (pair form) or tiles
     int e_per_tile;             // product jobs per tile and step
     int step_len;               // entries of the per-step product-job table
     long long total_e, total_d;
     const uint32_t *table;      // per-step job table
     const KTerm *terms;
     const uint32_t *bar;        // [G][n+1]
-    uint32_t *acc;              // [G][2][N]
+    uint32_t *acc;              // [tiles_pad][2][N][128] (gate-fastest within a tile)
     uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
     const uint4 *win;           // [n][2l][2][nterms][4][2s] units
     uint32_t *sync;             // [0] product-job counter, [1] digit-job counter,
@@ -401,15 +513,16 @@ __device__ __forceinline__ Job decode_e(const BrArgs &a, int job) {
     return J;
 }
 
-template <int L>
+template <int L, bool PAIR>
 __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     constexpr int NBLK = 1 << L;                      // size-s blocks per polynomial
     constexpr int NT = L == 0 ? 1 : (L == 1 ? 3 : 9);  // terms
+    constexpr int BPL = b_plane_bytes(PAIR), BST = b_stage_bytes(PAIR);
     extern __shared__ __align__(128) uint8_t smem[];  // no swizzle: 16-byte alignment suffices
     uint8_t *a_st = smem;
     uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;
-    uint32_t *d_rows = (uint32_t *)(b_st + STAGES * B_STAGE_BYTES);  // [8][N + 4]
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    uint32_t *d_rows = (uint32_t *)(b_st + STAGES * BST);  // [8][N + 4]
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], pfull[STAGES];
     __shared__ __align__(8) uint64_t acc_full, acc_empty[PLANES], drain;
     __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
     __shared__ int jobs[JQ];
@@ -419,6 +532,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     if (threadIdx.x < NT) terms[threadIdx.x] = a.terms[threadIdx.x];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // pair form: CTA 0 of the cluster fetches the product jobs and issues the MMAs
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
     const int N = a.N, l = a.l, s = a.s;
     const int kstages = s / KS;
     const int half_stages = l * kstages;
@@ -427,32 +542,44 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     uint32_t *e_counter = a.sync;
     uint32_t *d_counter = a.sync + 1;
     uint32_t *done_D = a.sync + 2;
-    uint32_t *done_E = a.sync + 2 + a.tiles;
+    uint32_t *done_E = a.sync + 2 + a.tiles_pad;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; q++) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
+            mbar_init(&pfull[q], 1);  // pair form: the odd CTA's stage q is full
         }
         mbar_init(&acc_full, 1);
-        for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], EPI_THREADS);
+        // one arrival per read-out warp (of both CTAs in the pair form)
+        for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], (PAIR ? 2 : 1) * EPI_WARPS);
         mbar_init(&drain, 1);
         for (int q = 0; q < JQ; q++) {
             mbar_init(&job_full[q], 1);
-            mbar_init(&job_empty[q], 2);  // MMA lane, read-out leader
+            // MMA lane, read-out leader; pair form also the odd CTA's loader, stage
+            // forwarder and read-out leader
+            mbar_init(&job_empty[q], PAIR ? 5 : 2);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
     if (warp == MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_slot)),
-                     "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(512));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(512));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();  // both CTAs' barriers exist before any remote use
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *abort = &abort_flag;
@@ -464,16 +591,32 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             int t_global = 0, issued = 0;
             for (int q = 0;; q++) {
                 const int slot = q % JQ;
-                if (q >= JQ && !mbar_wait(&job_empty[slot], ((q / JQ) - 1) & 1, abort, err)) break;
-                const unsigned jn = atomicAdd(e_counter, 1u);
-                const int job = (long long)jn < a.total_e ? (int)jn : -1;
-                jobs[slot] = job;
-                mbar_arrive(&job_full[slot]);
+                int job;
+                if (rank == 0) {
+                    if (q >= JQ && !mbar_wait<PAIR>(&job_empty[slot], ((q / JQ) - 1) & 1, abort, err))
+                        break;
+                    const unsigned jn = atomicAdd(e_counter, 1u);
+                    job = (long long)jn < a.total_e ? (int)jn : -1;
+                    jobs[slot] = job;
+                    if constexpr (PAIR) {  // the odd CTA takes the same job
+                        st_remote_u32(cluster_addr(&jobs[slot], 1), (uint32_t)job);
+                        mbar_arrive_remote(cluster_addr(&job_full[slot], 1));
+                    }
+                    mbar_arrive(&job_full[slot]);
+                } else {
+                    if (!mbar_wait<true>(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+                    job = jobs[slot];
+                    mbar_arrive_remote(cluster_addr(&job_empty[slot], 0));
+                }
                 if (job < 0) break;
                 const Job J = decode_e(a, job);
+                const int gt = PAIR ? 2 * J.gt + (int)rank : J.gt;  // this CTA's gate tile
                 const int bcol = J.sub % bpp;
-                const int P0 = s - NB - bcol * NB;
-                if (!wait_count(&done_D[J.gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err)) break;
+                // first window unit of this CTA's B columns (the odd CTA of a pair holds
+                // columns PB_COLS .. NB-1 of the block)
+                const int P0 = s - NB - bcol * NB + (PAIR ? PB_COLS * (int)rank : 0);
+                if (gt < a.tiles && !wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err))
+                    break;
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 bool ok = true;
                 for (int ts = 0; ts < total_stages; ts++, t_global++) {
@@ -484,8 +627,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         break;
                     }
                     const int r = ts / kstages, ks = ts % kstages;
-                    const size_t blk = (((size_t)J.gt * a.nterms + J.j) * 2 * l + r) * kstages + ks;
-                    mbar_arrive_tx(&full[st], A_STAGE_BYTES + B_STAGE_BYTES);
+                    const size_t blk = (((size_t)gt * a.nterms + J.j) * 2 * l + r) * kstages + ks;
+                    mbar_arrive_tx(&full[st], A_STAGE_BYTES + BST);
                     bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
                              A_STAGE_BYTES, &full[st]);
                     const size_t poly = ((size_t)J.i * 2 * l + r) * 2 + J.c;
@@ -493,8 +636,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                         (P0 + ks * KS);
 #pragma unroll
                     for (int p = 0; p < PLANES; p++)
-                        bulk_g2s(b_st + st * B_STAGE_BYTES + p * B_PLANE_BYTES,
-                                 wsrc + (size_t)p * 2 * s, B_PLANE_BYTES, &full[st]);
+                        bulk_g2s(b_st + st * BST + p * BPL, wsrc + (size_t)p * 2 * s, BPL, &full[st]);
                     issued = t_global + 1;
                 }
                 if (!ok) break;
@@ -503,9 +645,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 if (t >= 0) mbar_wait_settle(&full[t % STAGES], (t / STAGES) & 1);
         }
     } else if (warp == MMA_WARP) {
-        // ---- MMA issue ----
-        if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc(TILE_M, NB);
+        if (lane == 0 && rank == 0) {
+            // ---- MMA issue (pair form: M = 256 over both CTAs' stages) ----
+            constexpr uint32_t idesc = make_idesc(PAIR ? 2 * TILE_M : TILE_M, NB);
             int t_global = 0, khalf = 0;
             bool ok = true;
             for (int q = 0; ok; q++) {
@@ -516,50 +658,83 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 if (job < 0) break;
                 for (int ts = 0; ts < total_stages && ok; ts++, t_global++) {
                     const int st = t_global % STAGES;
-                    if (!mbar_wait(&full[st], (t_global / STAGES) & 1, abort, err)) {
+                    if (!mbar_wait(&full[st], (t_global / STAGES) & 1, abort, err) ||
+                        (PAIR && !mbar_wait<true>(&pfull[st], (t_global / STAGES) & 1, abort, err))) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(a_st + st * A_STAGE_BYTES);
-                    const uint32_t b_addr = smem_u32(b_st + st * B_STAGE_BYTES);
+                    // descriptors of the stage; K-steps and planes add their byte offset / 16
+                    // to the start-address field (shared addresses < 256 KB: no carry)
+                    const uint64_t a_desc = make_desc(smem_u32(a_st + st * A_STAGE_BYTES), 128, 2048);
+                    const uint64_t b_desc = make_desc(smem_u32(b_st + st * BST), 128, 128);
                     if (ts % half_stages == 0) {
                         // first stage of a half: plane p starts once its previous contents
                         // have been read out
 #pragma unroll
                         for (int p = 0; p < PLANES; p++) {
-                            if (khalf > 0 && !mbar_wait(&acc_empty[p], (khalf - 1) & 1, abort, err)) {
+                            if (khalf > 0 &&
+                                !mbar_wait<PAIR>(&acc_empty[p], (khalf - 1) & 1, abort, err)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
 #pragma unroll
-                            for (int kk = 0; kk < KS / 16; kk++)
-                                mma_bf16(tmem + p * NB, make_desc(a_addr + kk * 256, 128, 2048),
-                                         make_desc(b_addr + p * B_PLANE_BYTES + kk * 256, 128, 128),
-                                         idesc, kk == 0 ? 0u : 1u);
+                            for (int kk = 0; kk < KS / 16; kk++) {
+                                const uint64_t ad = a_desc + (uint64_t)(kk * 256 / 16);
+                                const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
+                                if constexpr (PAIR)
+                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, kk == 0 ? 0u : 1u);
+                                else
+                                    mma_bf16(tmem + p * NB, ad, bd, idesc, kk == 0 ? 0u : 1u);
+                            }
                         }
                         if (!ok) break;
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < KS / 16; kk++) {
-                            const uint64_t ad = make_desc(a_addr + kk * 256, 128, 2048);
+                            const uint64_t ad = a_desc + (uint64_t)(kk * 256 / 16);
 #pragma unroll
-                            for (int p = 0; p < PLANES; p++)
-                                mma_bf16(tmem + p * NB, ad,
-                                         make_desc(b_addr + p * B_PLANE_BYTES + kk * 256, 128, 128),
-                                         idesc, 1u);
+                            for (int p = 0; p < PLANES; p++) {
+                                const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
+                                if constexpr (PAIR)
+                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, 1u);
+                                else
+                                    mma_bf16(tmem + p * NB, ad, bd, idesc, 1u);
+                            }
                         }
                     }
-                    mma_commit(&empty[st]);
+                    if constexpr (PAIR) mma_commit_pair_both(&empty[st]);
+                    else mma_commit(&empty[st]);
                     if ((ts + 1) % half_stages == 0) {
-                        mma_commit(&acc_full);
+                        if constexpr (PAIR) mma_commit_pair_both(&acc_full);
+                        else mma_commit(&acc_full);
                         khalf++;
                     }
                 }
             }
-            mma_commit(&drain);
+            if constexpr (PAIR) mma_commit_pair_own(&drain);
+            else mma_commit(&drain);
             mbar_wait_settle(&drain, 0);
+        } else if (PAIR && lane == 0) {
+            // ---- odd CTA of a pair: tell the MMA issuer when each of its stages is full ----
+            int t_global = 0;
+            bool ok = true;
+            for (int q = 0; ok; q++) {
+                const int slot = q % JQ;
+                if (!mbar_wait<true>(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+                const int job = jobs[slot];
+                mbar_arrive_remote(cluster_addr(&job_empty[slot], 0));
+                if (job < 0) break;
+                for (int ts = 0; ts < total_stages; ts++, t_global++) {
+                    const int st = t_global % STAGES;
+                    if (!mbar_wait(&full[st], (t_global / STAGES) & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_remote(cluster_addr(&pfull[st], 0));
+                }
+            }
         }
     } else if (warp < EPI_WARPS) {
         // ---- TMEM read-out: thread = TMEM lane = gate of the tile; this warp's 64 columns
@@ -570,19 +745,23 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
         int khalf = 0;
         for (int q = 0;; q++) {
             const int slot = q % JQ;
-            if (!mbar_wait_warp(&job_full[slot], (q / JQ) & 1, abort, err)) break;
+            if (!mbar_wait_warp<PAIR>(&job_full[slot], (q / JQ) & 1, abort, err)) break;
             const int job = jobs[slot];
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            if (tid == 0) mbar_arrive(&job_empty[slot]);
+            if (tid == 0) {
+                if (rank == 0) mbar_arrive(&job_empty[slot]);
+                else mbar_arrive_remote(cluster_addr(&job_empty[slot], 0));
+            }
             if (job < 0) break;
             const Job J = decode_e(a, job);
+            const int gt = PAIR ? 2 * J.gt + (int)rank : J.gt;  // this CTA's gate tile
             const int bcol = J.sub % bpp;
             uint32_t sum[EPI_COLS];
 #pragma unroll
             for (int e = 0; e < EPI_COLS; e++) sum[e] = RO_SUM_INIT;
             bool ok = true;
             for (int h = 0; h < 2 && ok; h++, khalf++) {
-                if (!mbar_wait_warp(&acc_full, khalf & 1, abort, err)) {
+                if (!mbar_wait_warp<PAIR>(&acc_full, khalf & 1, abort, err)) {
                     ok = false;
                     break;
                 }
@@ -616,47 +795,52 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         }
                     }
                     tc_fence_before();
-                    mbar_arrive(&acc_empty[p]);
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0) mbar_arrive(&acc_empty[p]);
+                        else mbar_arrive_remote(cluster_addr(&acc_empty[p], 0));
+                    }
                 }
             }
             if (!ok) break;
             // accumulator update: column idx of the term output is word n' = c0 - idx of
             // each of the term's output blocks.  The leader's acquires order these accesses
             // after the digit job of this step and after this tile's earlier phases.
-            if (tid == 0) {
-                wait_count(&done_D[J.gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
-                if (J.dep) wait_count(&done_E[J.gt], (uint32_t)(a.e_per_tile * J.i + J.dep), abort, err);
+            if (tid == 0 && gt < a.tiles) {
+                wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
+                if (J.dep) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * J.i + J.dep), abort, err);
             }
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             if (*abort) break;
             const KTerm &T = terms[J.j];
-            const int g = J.gt * TILE_M + gl;
+            const int g = gt * TILE_M + gl;
             if (g < a.G) {
                 // this warp's columns idx = 64 colh + e map to words c0 - idx, i.e. the
-                // 64 words starting at bcol*NB + 64 (1 - colh), in reverse order
+                // 64 words starting at bcol*NB + 64 (1 - colh), in reverse order; in the
+                // tiled accumulator each word of the warp's 32 gates is one 128-byte line
                 const int w0 = bcol * NB + EPI_COLS * (1 - colh);
                 for (int o = 0; o < T.n_out; o++) {
                     const uint32_t sg = (uint32_t)T.out_sgn[o];
-                    uint4 *row = (uint4 *)(a.acc + (size_t)g * 2 * N + (size_t)J.c * N +
-                                           (size_t)T.out_blk[o] * s + w0);
+                    uint32_t *col = a.acc + ((size_t)(gt * 2 + J.c) * N + (size_t)T.out_blk[o] * s + w0) * TILE_M + gl;
 #pragma unroll
-                    for (int q4 = 0; q4 < EPI_COLS / 4; q4++) {
-                        uint4 v = __ldcg(row + q4);  // L2 only: rows move between blocks
-                        v.x += sg * sum[EPI_COLS - 1 - (4 * q4 + 0)];
-                        v.y += sg * sum[EPI_COLS - 1 - (4 * q4 + 1)];
-                        v.z += sg * sum[EPI_COLS - 1 - (4 * q4 + 2)];
-                        v.w += sg * sum[EPI_COLS - 1 - (4 * q4 + 3)];
-                        __stcg(row + q4, v);
+                    for (int j0 = 0; j0 < EPI_COLS; j0 += RMW_BATCH) {
+                        uint32_t v[RMW_BATCH];
+#pragma unroll
+                        for (int k = 0; k < RMW_BATCH; k++) v[k] = __ldcg(col + (size_t)(j0 + k) * TILE_M);
+#pragma unroll
+                        for (int k = 0; k < RMW_BATCH; k++)
+                            __stcg(col + (size_t)(j0 + k) * TILE_M, v[k] + sg * sum[EPI_COLS - 1 - (j0 + k)]);
                     }
                 }
             }
-            __threadfence();
+            // publish: the barrier orders every read-out thread's stores before the
+            // leader's release (cumulative), so one fenced increment suffices
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            if (tid == 0) atomicAdd(&done_E[J.gt], 1u);
+            if (tid == 0 && gt < a.tiles) red_release_add(&done_E[gt], 1u);
         }
     } else {
         // ---- warps 10-13: digit jobs ----
-        const int tid = threadIdx.x - DIG_WARP0 * 32;
+        const int tid = digit_warp_index(warp) * 32 + lane;
         const uint32_t off = gadget_offset(l, a.Bgbit);
         __shared__ int d_job;
         for (;;) {
@@ -692,13 +876,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             const uint32_t *row = d_rows + m8 * pitch;
             for (int c = 0; c < 2; c++) {
                 asm volatile("bar.sync 2, 128;" ::: "memory");  // previous polynomial consumed
-                for (int v = tid; v < 8 * (N / 4); v += 128) {
-                    const int mm = v / (N / 4), q4 = v % (N / 4);
-                    const int g = gt * TILE_M + mg * 8 + mm;
-                    const uint32_t *src = a.acc + (size_t)(g < a.G ? g : 0) * 2 * N + (size_t)c * N + q4 * 4;
-                    cp_async16(d_rows + mm * pitch + q4 * 4, src, g < a.G ? 16u : 0u);
+                {
+                    // word k of the part's 8 gates: 32 contiguous bytes of the tiled
+                    // accumulator; thread tid takes words tid, tid + 128, ... (two per batch)
+                    const uint4 *src = (const uint4 *)(a.acc + (size_t)(gt * 2 + c) * N * TILE_M) + mg * 2;
+                    for (int k0 = tid; k0 < N; k0 += 256) {
+                        uint4 v[4];
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            v[2 * h] = __ldcg(src + (size_t)(k0 + 128 * h) * (TILE_M / 4));
+                            v[2 * h + 1] = __ldcg(src + (size_t)(k0 + 128 * h) * (TILE_M / 4) + 1);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const int k = k0 + 128 * h;
+                            d_rows[0 * pitch + k] = v[2 * h].x;
+                            d_rows[1 * pitch + k] = v[2 * h].y;
+                            d_rows[2 * pitch + k] = v[2 * h].z;
+                            d_rows[3 * pitch + k] = v[2 * h].w;
+                            d_rows[4 * pitch + k] = v[2 * h + 1].x;
+                            d_rows[5 * pitch + k] = v[2 * h + 1].y;
+                            d_rows[6 * pitch + k] = v[2 * h + 1].z;
+                            d_rows[7 * pitch + k] = v[2 * h + 1].w;
+                        }
+                    }
                 }
-                cp_async_wait_all();
                 asm volatile("bar.sync 2, 128;" ::: "memory");
                 for (int kc = 0; kc < kstages; kc++) {
                     const int kp = kc * KS + kb * 8;
@@ -746,16 +948,21 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     }
                 }
             }
-            __threadfence();
             asm volatile("bar.sync 2, 128;" ::: "memory");
-            if (tid == 0) atomicAdd(&done_D[gt], 1u);
+            if (tid == 0) red_release_add(&done_D[gt], 1u);
         }
     }
     tc_fence_before();
     __syncthreads();
+    // pair form: neither CTA leaves while the other may still touch its shared memory
+    // or TMEM (the even CTA has drained its MMAs before reaching this point)
+    if constexpr (PAIR) cluster_sync_all();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
 
@@ -864,13 +1071,18 @@ struct TcWorkspace {
     size_t digits_cap = 0;     // bytes
     uint32_t *sync = nullptr;  // job counter and per-tile progress counters
     size_t sync_cap = 0;       // words
+    uint32_t *acc_t = nullptr; // accumulators, gate-fastest within 128-gate tiles
+    size_t acc_t_cap = 0;      // bytes
     struct JobTable {
         uint32_t *d = nullptr;  // per-step product-job table
         int len = 0;            // entries
     };
-    std::map<int, JobTable> tables;  // by gate-tile count (kept: captured graphs use them)
+    std::map<int, JobTable> tables;  // by 2 * gate-tile count + pair form (kept: captured
+                                     // graphs use them)
     int sms = 0;
+    int max_pairs[3] = {-1, -1, -1};  // co-resident SM pairs of the pair kernel, per level
     int want_level = -1;       // requested Karatsuba levels (-1: default)
+    int want_variant = -1;     // TFHE_TC_SINGLE_SM, TFHE_TC_SM_PAIR, -1: default
 };
 
 int tfhe_tc_supported(const tfhe_ctx *ctx) {
@@ -879,7 +1091,15 @@ int tfhe_tc_supported(const tfhe_ctx *ctx) {
            (int64_t)p.l * p.N * 32 * 128 <= (1 << 24);
 }
 
-static int default_level(const tfhe_params &p) { return p.N >= 512 ? 1 : 0; }
+// Measured on B300 at N = 1024 (4096-gate level): level 2 fastest; smaller N keeps
+// blocks of at least 256 columns.
+static int default_level(const tfhe_params &p) { return p.N >= 1024 ? 2 : (p.N >= 512 ? 1 : 0); }
+
+// One SM per tile unless the pair form was asked for (measured slower on B300: the
+// coupled SMs wait for each other more than the halved key staging saves).
+static bool use_pair(tfhe_ctx *ctx) {
+    return ctx->tc && ctx->tc->want_variant == TFHE_TC_SM_PAIR;
+}
 
 static bool level_ok(const tfhe_params &p, int L) {
     if (L < 0 || L > 2) return false;
@@ -894,6 +1114,7 @@ void tfhe_tc_free(tfhe_ctx *ctx) {
     if (w->win) cudaFree(w->win);
     if (w->digits) cudaFree(w->digits);
     if (w->sync) cudaFree(w->sync);
+    if (w->acc_t) cudaFree(w->acc_t);
     for (auto &t : w->tables) cudaFree(t.second.d);
     delete w;
     ctx->tc = nullptr;
@@ -957,9 +1178,10 @@ int tfhe_tc_level(tfhe_ctx *ctx) {
 }
 
 // Per-step job table for `tiles` gate tiles (see the kernel comment for the order).
-static int prepare_table(tfhe_ctx *ctx, int tiles, const TcWorkspace::JobTable **out) {
+static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace::JobTable **out) {
     TcWorkspace *w = ctx->tc;
-    auto it = w->tables.find(tiles);
+    const int key = 2 * tiles + (pair ? 1 : 0);
+    auto it = w->tables.find(key);
     if (it != w->tables.end()) {
         *out = &it->second;
         return TFHE_OK;
@@ -970,9 +1192,23 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, const TcWorkspace::JobTable *
     const int bpp = s / NB;
     int nphase = 0;
     for (const KTerm &t : w->terms) nphase = t.phase + 1 > nphase ? t.phase + 1 : nphase;
+    // entries name the gate tile, or in the pair form the tile pair (tiles 2u, 2u+1)
+    const int units = pair ? (tiles + 1) / 2 : tiles;
+    // Phase ph of unit u is emitted at slot u + ph * lag: a unit's later phases come about
+    // one wave of the SMs (or pairs) after its earlier ones, so the read-modify-writes they
+    // wait for are done, and the unit's last product of a step sits well before its first
+    // product of the next step, leaving time for that step's digit jobs.  Every job still
+    // follows all jobs it waits for.
+    const int per_unit = (int)w->terms.size() * 2 * bpp;
+    int sms = w->sms;
+    if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int lanes = pair ? sms / 2 : sms;  // product jobs running at once
+    const int lag = nphase > 1 ? std::max(1, std::min(units, (6 * lanes / 5 + per_unit - 1) / per_unit)) : 0;
     std::vector<uint32_t> tab;
-    for (int ph = 0; ph < nphase; ph++) {
-        for (int gt = 0; gt < tiles; gt++) {
+    for (int slot = 0; slot < units + (nphase - 1) * lag; slot++) {
+        for (int ph = 0; ph < nphase; ph++) {
+            const int gt = slot - ph * lag;
+            if (gt < 0 || gt >= units) continue;
             int dep = 0;  // product jobs of this tile in earlier phases
             for (const KTerm &t : w->terms)
                 if (t.phase < ph) dep += 2 * bpp;
@@ -991,7 +1227,7 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, const TcWorkspace::JobTable *
         return tfhe_set_error(ctx, TFHE_ECUDA, "tensor-core job table upload");
     }
     t.len = (int)tab.size();
-    *out = &(w->tables[tiles] = t);
+    *out = &(w->tables[key] = t);
     return TFHE_OK;
 }
 
@@ -1000,17 +1236,25 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, const TcWorkspace::JobTable *
 static int reserve_tc(tfhe_ctx *ctx, int G, const TcWorkspace::JobTable **table) {
     const tfhe_params &p = ctx->p;
     TcWorkspace *w = ctx->tc;
+    const bool pair = use_pair(ctx);
     const int tiles = (G + TILE_M - 1) / TILE_M;
+    const int tiles_pad = pair ? (tiles + 1) / 2 * 2 : tiles;
     const int T = (int)w->terms.size();
     const int s = p.N >> w->level;
+    const uint4 *old_digits = w->digits;
     int rc = grow_dev(ctx, (void **)&w->digits, &w->digits_cap,
-                      (size_t)tiles * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
+                      (size_t)tiles_pad * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
     if (rc != TFHE_OK) return rc;
-    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles) * 4,
+    // the odd tile that pads a pair is never written: keep its digits zero
+    if (w->digits != old_digits) TFHE_CUDA_TRY(ctx, cudaMemset(w->digits, 0, w->digits_cap));
+    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles_pad) * 4,
                   "tensor-core progress counters");
     if (rc != TFHE_OK) return rc;
+    rc = grow_dev(ctx, (void **)&w->acc_t, &w->acc_t_cap, (size_t)tiles_pad * 2 * p.N * TILE_M * 4,
+                  "tensor-core accumulators");
+    if (rc != TFHE_OK) return rc;
     const TcWorkspace::JobTable *t = nullptr;
-    rc = prepare_table(ctx, tiles, &t);
+    rc = prepare_table(ctx, tiles, pair, &t);
     if (rc == TFHE_OK && table) *table = t;
     return rc;
 }
@@ -1041,12 +1285,19 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
         w->sms = sms;
     }
+    const bool pair = use_pair(ctx);
+    const int tiles_pad = pair ? (tiles + 1) / 2 * 2 : tiles;
     const int n1 = p.n + 1;
-    auto kern = w->level == 0 ? k_tc_blind_rotate<0>
-              : (w->level == 1 ? k_tc_blind_rotate<1> : k_tc_blind_rotate<2>);
-    const int smem = smem_bytes(p.N);
+    void (*kern)(BrArgs);
+    if (pair)
+        kern = w->level == 0 ? k_tc_blind_rotate<0, true>
+             : (w->level == 1 ? k_tc_blind_rotate<1, true> : k_tc_blind_rotate<2, true>);
+    else
+        kern = w->level == 0 ? k_tc_blind_rotate<0, false>
+             : (w->level == 1 ? k_tc_blind_rotate<1, false> : k_tc_blind_rotate<2, false>);
+    const int smem = smem_bytes(p.N, pair);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 2 * (size_t)tiles) * 4, st));
+    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 2 * (size_t)tiles_pad) * 4, st));
     BrArgs args;
     args.N = p.N;
     args.l = p.l;
@@ -1057,6 +1308,7 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.s = s;
     args.nterms = T;
     args.tiles = tiles;
+    args.tiles_pad = tiles_pad;
     args.cbs = 2 * (s / NB);
     args.e_per_tile = T * 2 * (s / NB);
     args.step_len = table->len;
@@ -1065,22 +1317,72 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.table = table->d;
     args.terms = w->d_terms;
     args.bar = bar;
-    args.acc = acc;
+    args.acc = w->acc_t;
     args.digits = w->digits;
     args.win = w->win;
     args.sync = w->sync;
     args.err = ctx->d_err;
-    const int grid = (int)(args.total_e < w->sms ? args.total_e : w->sms);
+
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    if (pair) {
+        // as many SM pairs as can be resident at once (one block per SM)
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int &mp = w->max_pairs[w->level];
+        if (mp < 0) {
+            cfg.gridDim = dim3(2 * (w->sms / 2));
+            int n = 0;
+            TFHE_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&n, kern, &cfg));
+            if (n < 1) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core SM pairs not schedulable");
+            mp = n;
+        }
+        const long long pairs = args.total_e < mp ? args.total_e : mp;
+        cfg.gridDim = dim3((unsigned)(2 * pairs));
+    } else {
+        cfg.gridDim = dim3((unsigned)(args.total_e < w->sms ? args.total_e : w->sms));
+    }
     StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
     {
-        const size_t total = (size_t)G * 2 * p.N;
-        k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, bar, acc);
+        const size_t total = (size_t)tiles_pad * 2 * p.N * TILE_M;
+        k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, tiles_pad, bar,
+                                                                      w->acc_t);
         rc = tfhe_check_launch(ctx, "tc_init_acc");
         if (rc != TFHE_OK) return rc;
     }
-    kern<<<grid, P_THREADS, smem, st>>>(args);
-    tm.stop(2);
-    return tfhe_check_launch(ctx, "tc blind rotate");
+    TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
+    rc = tfhe_check_launch(ctx, "tc blind rotate");
+    if (rc != TFHE_OK) return rc;
+    k_tc_untile_acc<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * tiles), 2), dim3(32, 8), 0, st>>>(
+        p.N, G, w->acc_t, acc);
+    tm.stop(3);
+    return tfhe_check_launch(ctx, "tc untile accumulators");
+}
+
+int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    if (variant < -1 || variant > TFHE_TC_SM_PAIR)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core variant");
+    if (variant == TFHE_TC_SM_PAIR) {
+        int cl = 0;
+        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, ctx->device));
+        if (!cl) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "device cannot launch SM pairs");
+    }
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    ctx->tc->want_variant = variant;
+    return TFHE_OK;
+}
+
+int tfhe_tc_variant(tfhe_ctx *ctx) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    return use_pair(ctx) ? TFHE_TC_SM_PAIR : TFHE_TC_SINGLE_SM;
 }
 
 int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *, const CmuxGeom &, cudaStream_t) {

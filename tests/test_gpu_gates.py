@@ -130,16 +130,20 @@ def test_host_buffer_entry_point_matches_device(torch_cuda):
     assert np.array_equal(out, want)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("params,seed,levels,G", [
     (ti.TOY, ti.SEED_TOY, (0, 1), 40),
     (ti.STD, ti.SEED_FLAT, (0, 1, 2), 37),
 ])
-def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G):
-    """Every Karatsuba level of the tensor-core form gives the oracle's words."""
+def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G, variant):
+    """Every Karatsuba level of the tensor-core form, on one SM per tile and on SM pairs,
+    gives the oracle's words."""
     ctx, k = gpu_context(params, seed)
     b = ti.toy_gates() if params is ti.TOY else ti.flat_level(G)
     want = orc.gate_batch(params, k.bsk, k.ksk, b.inp, b.types, b.idx)
     try:
+        ctx.set_tc_variant(variant)
+        assert ctx.tc_variant() == variant
         for L in levels:
             ctx.set_tc_level(L)
             out = empty(torch_cuda, b.types.size, params.n + 1)
@@ -148,3 +152,29 @@ def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G):
             assert np.array_equal(from_dev(out), want), L
     finally:
         ctx.set_tc_level(-1)
+        ctx.set_tc_variant(-1)
+
+
+@pytest.mark.parametrize("G", [300, 129, 1000])
+def test_tc_variants_agree_on_every_word(torch_cuda, G):
+    """One-SM and SM-pair BlindRotate give the same words for all gates, including tile
+    counts that leave the last pair half empty (3 and 2 tiles of 128 gates, 8 tiles with
+    a ragged last one); sampled gates, first and last of every tile, match the oracle."""
+    p = ti.STD
+    ctx, k = gpu_context(p, ti.SEED_FLAT)
+    b = ti.flat_level(G)
+    outs = {}
+    try:
+        for v in (0, 1):
+            ctx.set_tc_variant(v)
+            out = empty(torch_cuda, G, p.n + 1)
+            ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=1)
+            ctx.sync()
+            outs[v] = from_dev(out)
+    finally:
+        ctx.set_tc_variant(-1)
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, outs[1]), b.expected)
+    samples = sorted({g for t in range(0, G, 128) for g in (t, min(t + 127, G - 1))})
+    want = orc.gate_batch(p, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=samples)
+    assert np.array_equal(outs[1][samples], want)
