@@ -123,6 +123,80 @@ __global__ void __launch_bounds__(160) k_extract_keyswitch(
 
 static constexpr int KS_GT = 8;
 
+// Key switching with basebit = 2: the per-gate kernel above with the block's 8 gates'
+// 2-bit digits packed into one 16-bit word per key-switch row (gate g in bits 2g, 2g+1),
+// so the block's digits take N*t*2 bytes of shared memory instead of N*t*8 and several
+// blocks share an SM.  Digits, order and sums are those of the per-gate kernel.
+constexpr int KS2_GT = 8;
+__global__ void __launch_bounds__(160, 6) k_extract_keyswitch_b2(
+    int n, int N, int t, int n_pad, const uint32_t *__restrict__ acc, const uint4 *__restrict__ ksk,
+    uint32_t *__restrict__ out, int G, const uint8_t *__restrict__ types,
+    const int32_t *__restrict__ idx, int64_t num_in) {
+    extern __shared__ uint16_t dig16[];  // [N * t] packed digits
+    __shared__ int live_s[KS2_GT];
+    const int g0 = blockIdx.x * KS2_GT;
+    if (threadIdx.x < KS2_GT) {
+        const int g = g0 + threadIdx.x;
+        bool live = g < G;
+        if (live && types) live = gate_ok(types, idx, num_in, g);
+        live_s[threadIdx.x] = live;
+    }
+    __syncthreads();
+    const uint32_t prec = 1u << (32 - (1 + 2 * t));
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // t <= 8 (checked by the host)
+#pragma unroll
+        for (int g = 0; g < KS2_GT; g++) {
+            if (!live_s[g]) continue;
+            const uint32_t *A = acc + (size_t)(g0 + g) * 2 * N;
+            const uint32_t ab = ((i == 0) ? A[0] : 0u - A[N - i]) + prec;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (j < t) w[j] |= ((ab >> (32 - (j + 1) * 2)) & 3u) << (2 * g);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (j < t) dig16[i * t + j] = (uint16_t)w[j];
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    const int ncol = n_pad >> 2;
+    if (c >= ncol) return;
+    uint4 res[KS2_GT];
+#pragma unroll
+    for (int g = 0; g < KS2_GT; g++) res[g] = make_uint4(0, 0, 0, 0);
+    const int rows = N * t;
+    for (int ij = 0; ij < rows; ij++) {
+        const uint32_t w = dig16[ij];
+        const uint4 *rowbase = ksk + (size_t)ij * 3 * ncol + c;
+#pragma unroll
+        for (int g = 0; g < KS2_GT; g++) {
+            const uint32_t d = (w >> (2 * g)) & 3u;
+            if (d) {
+                const uint4 k = __ldg(rowbase + (size_t)(d - 1) * ncol);
+                res[g].x += k.x;
+                res[g].y += k.y;
+                res[g].z += k.z;
+                res[g].w += k.w;
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < KS2_GT; g++) {
+        const int gg = g0 + g;
+        if (gg >= G) break;
+        const bool live = live_s[g];
+        const uint32_t bprime = live ? acc[(size_t)gg * 2 * N + N] : 0u;
+        uint32_t *o = out + (size_t)gg * (n + 1);
+        const uint32_t v[4] = {res[g].x, res[g].y, res[g].z, res[g].w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int k = 4 * c + q;
+            if (k <= n) o[k] = live ? ((k == n ? bprime : 0u) - v[q]) : 0u;
+        }
+    }
+}
+
 static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
                                     const uint8_t *types, const int32_t *idx, int64_t num_in,
                                     cudaStream_t st) {
@@ -134,6 +208,17 @@ static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t
                                             (int)smem));
     if (ctx->n_pad / 4 > 160)
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "key switch: n + 1 > 640");
+    if (p.ks_basebit == 2 && p.ks_t <= 8) {
+        const size_t smem2 = (size_t)p.N * p.ks_t * 2;
+        TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_extract_keyswitch_b2,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem2));
+        StageTimer tm(ctx, TFHE_STAGE_KEYSWITCH, st);
+        k_extract_keyswitch_b2<<<(G + KS2_GT - 1) / KS2_GT, 160, smem2, st>>>(
+            p.n, p.N, p.ks_t, ctx->n_pad, acc, (const uint4 *)ctx->ksk, out, G, types, idx, num_in);
+        tm.stop();
+        return tfhe_check_launch(ctx, "extract_keyswitch");
+    }
     const int blocks = (G + KS_GT - 1) / KS_GT;
     StageTimer tm(ctx, TFHE_STAGE_KEYSWITCH, st);
     k_extract_keyswitch<KS_GT><<<blocks, 160, smem, st>>>(
