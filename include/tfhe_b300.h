@@ -143,6 +143,16 @@ enum { TFHE_TC_SINGLE_SM = 0, TFHE_TC_SM_PAIR = 1 };
 int tfhe_ctx_set_tc_variant(tfhe_ctx *ctx, int variant);
 int tfhe_ctx_tc_variant(tfhe_ctx *ctx);
 
+/* The tensor-core BlindRotate accumulates a product job's whole K (2l rows of the key
+ * polynomial) in one pass of fp32 TMEM accumulators when, for every gate of the tile,
+ * the sum of |digit| over that K is at most `limit`: with key byte planes |q| <= 128 every
+ * partial sum then stays within 2^24, where fp32 holds integers exactly.  Steps of a tile
+ * where some gate exceeds it take two passes of l rows (always exact for the supported
+ * parameters).  limit: 0 .. 2^17 (the default, and the largest exact value); 0 forces two
+ * passes everywhere; -1 restores the default.  Results are identical for every limit.
+ * TFHE_EINVAL above 2^17, TFHE_EUNSUPPORTED without the tensor-core form. */
+int tfhe_ctx_set_tc_pass_limit(tfhe_ctx *ctx, int limit);
+
 /* Per-kernel timing (tracing).  When enabled, the context brackets the kernel launches of
  * each stage with CUDA events on the launching stream (not while the stream is being
  * captured into a graph).  tfhe_ctx_stage_times waits for the recorded events, writes

@@ -39,6 +39,7 @@ EXPORTS = [
     "tfhe_ctx_tc_level",
     "tfhe_ctx_set_tc_variant",
     "tfhe_ctx_tc_variant",
+    "tfhe_ctx_set_tc_pass_limit",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -95,6 +96,7 @@ def lib():
         "tfhe_ctx_tc_level": (i32, [vp]),
         "tfhe_ctx_set_tc_variant": (i32, [vp, i32]),
         "tfhe_ctx_tc_variant": (i32, [vp]),
+        "tfhe_ctx_set_tc_pass_limit": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -172,6 +174,10 @@ class Context:
         rc = lib().tfhe_ctx_tc_variant(self.h)
         self._check(min(rc, 0), "tc_variant")
         return rc
+
+    def set_tc_pass_limit(self, limit: int):
+        """Largest per-gate sum of |digit| accumulated in one TMEM pass (0 .. 2^17, -1 default)."""
+        self._check(lib().tfhe_ctx_set_tc_pass_limit(self.h, limit), "set_tc_pass_limit")
 
     def enable_timing(self, on: bool = True):
         self._check(lib().tfhe_ctx_enable_timing(self.h, 1 if on else 0), "enable_timing")

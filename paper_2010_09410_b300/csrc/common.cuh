@@ -120,7 +120,8 @@ int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st);
 int tfhe_tc_set_level(tfhe_ctx *ctx, int level);
 int tfhe_tc_reserve(tfhe_ctx *ctx, int gates);
 int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant);
-int tfhe_tc_variant(tfhe_ctx *ctx);  // tensor-core buffers + job table for `gates`
+int tfhe_tc_variant(tfhe_ctx *ctx);
+int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);  // tensor-core buffers + job table for `gates`
 // Reallocate a context-owned device buffer to at least `need` bytes (no copy); refused
 // while a plan graph is being recorded; bumps mem_gen.
 int tfhe_grow(tfhe_ctx *ctx, void **ptr, size_t *cap_bytes, size_t need, const char *what);

@@ -283,6 +283,11 @@ extern "C" int tfhe_ctx_set_tc_variant(tfhe_ctx *ctx, int variant) {
     return tfhe_tc_set_variant(ctx, variant);
 }
 
+extern "C" int tfhe_ctx_set_tc_pass_limit(tfhe_ctx *ctx, int limit) {
+    if (!ctx) return TFHE_EINVAL;
+    return tfhe_tc_set_pass_limit(ctx, limit);
+}
+
 extern "C" int tfhe_ctx_tc_variant(tfhe_ctx *ctx) {
     if (!ctx) return TFHE_EINVAL;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

@@ -436,9 +436,16 @@ constexpr float RO_MAGIC = 12582912.0f;
 constexpr uint32_t RO_MAGIC_BITS = 0x4B400000u;
 constexpr float RO_FAST_LIMIT = 4194304.0f;  // 2^22
 constexpr int RO_COLS = 32;                   // columns per TMEM load slice
-constexpr int RMW_BATCH = 16;                 // accumulator loads in flight per thread
-constexpr uint32_t RO_SUM_INIT =
-    0u - 2u * (RO_MAGIC_BITS + (RO_MAGIC_BITS << 8) + (RO_MAGIC_BITS << 16) + (RO_MAGIC_BITS << 24));
+constexpr int RMW_BATCH = 32;                 // accumulator loads in flight per thread
+// bit-pattern offset that one K-pass adds over the four planes (mod 2^32)
+constexpr uint32_t RO_MAGIC_PER_PASS =
+    RO_MAGIC_BITS + (RO_MAGIC_BITS << 8) + (RO_MAGIC_BITS << 16) + (RO_MAGIC_BITS << 24);
+// A product job accumulates its whole K (2l rows of s digits) in one TMEM pass when every
+// gate g of the tile has sum_k |x_gk| <= 2^17 for the job's term: each partial sum is then
+// at most 128 * 2^17 = 2^24 in magnitude (|key byte| <= 128), so fp32 stays exact.  The
+// digit jobs check this; a (tile, step) that fails it is marked and its products take
+// two passes of l rows each, for which the worst case l * s * (32 * 2^L) * 128 <= 2^24.
+constexpr int ONE_PASS_LIMIT = 1 << 17;  // default and largest allowed limit
 constexpr int JQ = 8;       // job ring depth
 constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
 
@@ -485,6 +492,7 @@ struct BrArgs {
     int s, nterms;              // term size N / 2^L and count 3^L
     int tiles, cbs;             // gate tiles, column blocks per term output (2 * s / NB)
     int tiles_pad;              // tiles rounded up to the pair size (pair form) or tiles
+    int one_pass_limit;         // largest per-gate sum of |digit| accumulated in one pass
     int e_per_tile;             // product jobs per tile and step
     int step_len;               // entries of the per-step product-job table
     long long total_e, total_d;
@@ -495,7 +503,8 @@ struct BrArgs {
     uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
     const uint4 *win;           // [n][2l][2][nterms][4][2s] units
     uint32_t *sync;             // [0] product-job counter, [1] digit-job counter,
-                                // [2 .. 2+tiles) done_D, [2+tiles ..) done_E
+                                // then per padded tile: done_D, done_E, two_pass (the last
+                                // step + 1 whose products need two passes)
     int *err;
 };
 
@@ -513,6 +522,23 @@ __device__ __forceinline__ Job decode_e(const BrArgs &a, int job) {
     return J;
 }
 
+// TMEM passes of product job J (1 or 2): 2 when the digit jobs of its tile (both tiles of
+// a pair) marked its step.  Waits (acquire) for those digit jobs first.
+template <bool PAIR>
+__device__ __forceinline__ int passes_for(const BrArgs &a, const Job &J, const uint32_t *done_D,
+                                          const uint32_t *two_pass) {
+    int passes = 1;
+    for (int u = 0; u < (PAIR ? 2 : 1); u++) {
+        const int gt = PAIR ? 2 * J.gt + u : J.gt;
+        if (gt >= a.tiles) continue;
+        const long long t0 = clock64();
+        while (ld_acquire(&done_D[gt]) < (uint32_t)(DPARTS * (J.i + 1)) && clock64() - t0 < WAIT_CYCLES) {
+        }
+        if (*(volatile const uint32_t *)&two_pass[gt] == (uint32_t)(J.i + 1)) passes = 2;
+    }
+    return passes;
+}
+
 template <int L, bool PAIR>
 __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     constexpr int NBLK = 1 << L;                      // size-s blocks per polynomial
@@ -526,6 +552,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     __shared__ __align__(8) uint64_t acc_full, acc_empty[PLANES], drain;
     __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
     __shared__ int jobs[JQ];
+    __shared__ int job_passes[JQ];  // set by the loader before the job's first stage is full
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ KTerm terms[NT];
@@ -543,6 +570,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     uint32_t *d_counter = a.sync + 1;
     uint32_t *done_D = a.sync + 2;
     uint32_t *done_E = a.sync + 2 + a.tiles_pad;
+    uint32_t *two_pass = a.sync + 2 + 2 * a.tiles_pad;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; q++) {
@@ -617,6 +645,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 const int P0 = s - NB - bcol * NB + (PAIR ? PB_COLS * (int)rank : 0);
                 if (gt < a.tiles && !wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err))
                     break;
+                if (rank == 0) job_passes[slot] = passes_for<PAIR>(a, J, done_D, two_pass);
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 bool ok = true;
                 for (int ts = 0; ts < total_stages; ts++, t_global++) {
@@ -654,8 +683,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 const int slot = q % JQ;
                 if (!mbar_wait(&job_full[slot], (q / JQ) & 1, abort, err)) break;
                 const int job = jobs[slot];
-                mbar_arrive(&job_empty[slot]);
-                if (job < 0) break;
+                if (job < 0) {
+                    mbar_arrive(&job_empty[slot]);
+                    break;
+                }
+                int pass_stages = total_stages;  // stages per TMEM pass, decided per job
                 for (int ts = 0; ts < total_stages && ok; ts++, t_global++) {
                     const int st = t_global % STAGES;
                     if (!mbar_wait(&full[st], (t_global / STAGES) & 1, abort, err) ||
@@ -664,12 +696,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         break;
                     }
                     tc_fence_after();
+                    if (ts == 0) {
+                        if (job_passes[slot] == 2) pass_stages = half_stages;
+                        mbar_arrive(&job_empty[slot]);  // the slot is read
+                    }
                     // descriptors of the stage; K-steps and planes add their byte offset / 16
                     // to the start-address field (shared addresses < 256 KB: no carry)
                     const uint64_t a_desc = make_desc(smem_u32(a_st + st * A_STAGE_BYTES), 128, 2048);
                     const uint64_t b_desc = make_desc(smem_u32(b_st + st * BST), 128, 128);
-                    if (ts % half_stages == 0) {
-                        // first stage of a half: plane p starts once its previous contents
+                    if (ts % pass_stages == 0) {
+                        // first stage of a pass: plane p starts once its previous contents
                         // have been read out
 #pragma unroll
                         for (int p = 0; p < PLANES; p++) {
@@ -706,7 +742,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     }
                     if constexpr (PAIR) mma_commit_pair_both(&empty[st]);
                     else mma_commit(&empty[st]);
-                    if ((ts + 1) % half_stages == 0) {
+                    if ((ts + 1) % pass_stages == 0) {
                         if constexpr (PAIR) mma_commit_pair_both(&acc_full);
                         else mma_commit(&acc_full);
                         khalf++;
@@ -739,6 +775,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     } else if (warp < EPI_WARPS) {
         // ---- TMEM read-out: thread = TMEM lane = gate of the tile; this warp's 64 columns
         const int tid = threadIdx.x;
+        __shared__ int epi_passes;
         const int lane_q = warp & 3, colh = warp >> 2;
         const uint32_t lane_base = tmem + (((uint32_t)(lane_q * 32)) << 16) + colh * EPI_COLS;
         const int gl = lane_q * 32 + lane;  // gate within the tile
@@ -756,11 +793,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             const Job J = decode_e(a, job);
             const int gt = PAIR ? 2 * J.gt + (int)rank : J.gt;  // this CTA's gate tile
             const int bcol = J.sub % bpp;
+            if (tid == 0) epi_passes = passes_for<PAIR>(a, J, done_D, two_pass);
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            const int passes = epi_passes;
             uint32_t sum[EPI_COLS];
+            const uint32_t sum_init = 0u - (uint32_t)passes * RO_MAGIC_PER_PASS;
 #pragma unroll
-            for (int e = 0; e < EPI_COLS; e++) sum[e] = RO_SUM_INIT;
+            for (int e = 0; e < EPI_COLS; e++) sum[e] = sum_init;
             bool ok = true;
-            for (int h = 0; h < 2 && ok; h++, khalf++) {
+            for (int h = 0; h < passes && ok; h++, khalf++) {
                 if (!mbar_wait_warp<PAIR>(&acc_full, khalf & 1, abort, err)) {
                     ok = false;
                     break;
@@ -843,6 +884,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
         const int tid = digit_warp_index(warp) * 32 + lane;
         const uint32_t off = gadget_offset(l, a.Bgbit);
         __shared__ int d_job;
+        __shared__ int d_abs[8 * NT];  // sum of |x| per (gate of the part, term)
         for (;;) {
             if (tid == 0) {
                 const unsigned jn = atomicAdd(d_counter, 1u);
@@ -853,7 +895,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (job < 0 || *abort) break;
             const int i = job / (a.tiles * DPARTS);
-            const int gt = (job / DPARTS) % a.tiles, mg = job % DPARTS;
+            int gt, mg;
+            {
+                const int r = job % (a.tiles * DPARTS);
+                const int paired = PAIR ? (a.tiles / 2) * 2 * DPARTS : 0;
+                if (r < paired) {  // pair form: the two tiles of a pair alternate parts
+                    gt = 2 * (r / (2 * DPARTS)) + (r & 1);
+                    mg = (r % (2 * DPARTS)) >> 1;
+                } else {
+                    gt = (paired / DPARTS) + (r - paired) / DPARTS;
+                    mg = (r - paired) % DPARTS;
+                }
+            }
             if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * i), abort, err);
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (*abort) break;
@@ -870,6 +923,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 rot8[m8] = g < a.G ? (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
             }
             const int m8 = tid & 7, kb = tid >> 3;
+            for (int v = tid; v < 8 * NT; v += 128) d_abs[v] = 0;
+            int asum[NT];
+#pragma unroll
+            for (int j = 0; j < NT; j++) asum[j] = 0;
             const int rot = rot8[m8];
             const int rk = rot >= N ? rot - N : rot;      // X^rot = (-1)^{rot >= N} X^rk
             const uint32_t rneg = rot >= N ? 0xFFFFFFFFu : 0u;
@@ -938,6 +995,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 #pragma unroll
                                 for (int e = 0; e < 8; e++) x[e] += cf * dg[b][e];
                             }
+#pragma unroll
+                            for (int e = 0; e < 8; e++) asum[j] += abs(x[e]);
                             uint32_t w[4];
 #pragma unroll
                             for (int e = 0; e < 8; e += 2) w[e / 2] = bf16_bits(x[e]) | (bf16_bits(x[e + 1]) << 16);
@@ -948,6 +1007,17 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     }
                 }
             }
+            // one-pass check: sum |x| over the 16 threads of each gate, mark the step if
+            // some gate exceeds the bound for some term (read by the product jobs)
+#pragma unroll
+            for (int j = 0; j < NT; j++) {
+                int v = asum[j];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (lane < 8) atomicAdd(&d_abs[lane * NT + j], v);
+            }
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (tid < 8 * NT && d_abs[tid] > a.one_pass_limit) atomicMax(&two_pass[gt], (uint32_t)(i + 1));
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (tid == 0) red_release_add(&done_D[gt], 1u);
         }
@@ -1083,6 +1153,7 @@ struct TcWorkspace {
     int max_pairs[3] = {-1, -1, -1};  // co-resident SM pairs of the pair kernel, per level
     int want_level = -1;       // requested Karatsuba levels (-1: default)
     int want_variant = -1;     // TFHE_TC_SINGLE_SM, TFHE_TC_SM_PAIR, -1: default
+    int one_pass_limit = ONE_PASS_LIMIT;
 };
 
 int tfhe_tc_supported(const tfhe_ctx *ctx) {
@@ -1247,7 +1318,7 @@ static int reserve_tc(tfhe_ctx *ctx, int G, const TcWorkspace::JobTable **table)
     if (rc != TFHE_OK) return rc;
     // the odd tile that pads a pair is never written: keep its digits zero
     if (w->digits != old_digits) TFHE_CUDA_TRY(ctx, cudaMemset(w->digits, 0, w->digits_cap));
-    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 2 * (size_t)tiles_pad) * 4,
+    rc = grow_dev(ctx, (void **)&w->sync, &w->sync_cap, (2 + 3 * (size_t)tiles_pad) * 4,
                   "tensor-core progress counters");
     if (rc != TFHE_OK) return rc;
     rc = grow_dev(ctx, (void **)&w->acc_t, &w->acc_t_cap, (size_t)tiles_pad * 2 * p.N * TILE_M * 4,
@@ -1297,7 +1368,7 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
              : (w->level == 1 ? k_tc_blind_rotate<1, false> : k_tc_blind_rotate<2, false>);
     const int smem = smem_bytes(p.N, pair);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 2 * (size_t)tiles_pad) * 4, st));
+    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 3 * (size_t)tiles_pad) * 4, st));
     BrArgs args;
     args.N = p.N;
     args.l = p.l;
@@ -1309,6 +1380,7 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.nterms = T;
     args.tiles = tiles;
     args.tiles_pad = tiles_pad;
+    args.one_pass_limit = w->one_pass_limit;
     args.cbs = 2 * (s / NB);
     args.e_per_tile = T * 2 * (s / NB);
     args.step_len = table->len;
@@ -1377,6 +1449,15 @@ int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant) {
     }
     if (!ctx->tc) ctx->tc = new TcWorkspace();
     ctx->tc->want_variant = variant;
+    return TFHE_OK;
+}
+
+int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    if (limit < -1 || limit > ONE_PASS_LIMIT)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "one-pass limit above 2^17 is not exact");
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    ctx->tc->one_pass_limit = limit < 0 ? ONE_PASS_LIMIT : limit;
     return TFHE_OK;
 }
 

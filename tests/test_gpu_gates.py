@@ -155,6 +155,37 @@ def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G, vari
         ctx.set_tc_variant(-1)
 
 
+@pytest.mark.parametrize("limit", [0, 60000])
+@pytest.mark.parametrize("params,seed,G", [(ti.TOY, ti.SEED_TOY, 40), (ti.STD, ti.SEED_FLAT, 300)])
+def test_tc_one_and_two_pass_accumulation(torch_cuda, params, seed, G, limit):
+    """Steps accumulated in two TMEM passes (forced everywhere with limit 0, mixed with
+    one-pass steps at 60000) give the same words as the default; sampled gates match the
+    oracle."""
+    ctx, k = gpu_context(params, seed)
+    b = ti.toy_gates() if params is ti.TOY else ti.flat_level(G)
+    outs = []
+    try:
+        for lim in (-1, limit):
+            ctx.set_tc_pass_limit(lim)
+            out = empty(torch_cuda, b.types.size, params.n + 1)
+            ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=1)
+            ctx.sync()
+            outs.append(from_dev(out))
+    finally:
+        ctx.set_tc_pass_limit(-1)
+    assert np.array_equal(outs[0], outs[1])
+    samples = [0, b.types.size // 2, b.types.size - 1]
+    want = orc.gate_batch(params, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=samples)
+    assert np.array_equal(outs[1][samples], want)
+
+
+def test_tc_pass_limit_rejects_inexact_values(torch_cuda):
+    import paper_2010_09410_b300 as tb
+    ctx, _ = gpu_context(ti.STD, ti.SEED_FLAT)
+    with pytest.raises(tb.TfheError):
+        ctx.set_tc_pass_limit((1 << 17) + 1)
+
+
 @pytest.mark.parametrize("G", [300, 129, 1000])
 def test_tc_variants_agree_on_every_word(torch_cuda, G):
     """One-SM and SM-pair BlindRotate give the same words for all gates, including tile
