@@ -616,21 +616,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     if (warp == LOAD_WARP) {
         // ---- job fetch + stage loads ----
         if (lane == 0) {
+            // CTA 0 hands out job q+1 while it streams job q's stages (one job ahead),
+            // so the fetch latency hides behind the stage ring.
+            auto publish = [&](int qq) -> int {  // -2: aborted
+                const int sl = qq % JQ;
+                if (qq >= JQ && !mbar_wait<PAIR>(&job_empty[sl], ((qq / JQ) - 1) & 1, abort, err))
+                    return -2;
+                const unsigned jn = atomicAdd(e_counter, 1u);
+                const int jb = (long long)jn < a.total_e ? (int)jn : -1;
+                jobs[sl] = jb;
+                if constexpr (PAIR) {  // the odd CTA takes the same job
+                    st_remote_u32(cluster_addr(&jobs[sl], 1), (uint32_t)jb);
+                    mbar_arrive_remote(cluster_addr(&job_full[sl], 1));
+                }
+                mbar_arrive(&job_full[sl]);
+                return jb;
+            };
             int t_global = 0, issued = 0;
+            int next = rank == 0 ? publish(0) : 0;
+            const int fetch_at = total_stages > 1 ? 1 : 0;
             for (int q = 0;; q++) {
                 const int slot = q % JQ;
                 int job;
                 if (rank == 0) {
-                    if (q >= JQ && !mbar_wait<PAIR>(&job_empty[slot], ((q / JQ) - 1) & 1, abort, err))
-                        break;
-                    const unsigned jn = atomicAdd(e_counter, 1u);
-                    job = (long long)jn < a.total_e ? (int)jn : -1;
-                    jobs[slot] = job;
-                    if constexpr (PAIR) {  // the odd CTA takes the same job
-                        st_remote_u32(cluster_addr(&jobs[slot], 1), (uint32_t)job);
-                        mbar_arrive_remote(cluster_addr(&job_full[slot], 1));
-                    }
-                    mbar_arrive(&job_full[slot]);
+                    job = next;
+                    if (job == -2) break;
                 } else {
                     if (!mbar_wait<true>(&job_full[slot], (q / JQ) & 1, abort, err)) break;
                     job = jobs[slot];
@@ -650,6 +660,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 bool ok = true;
                 for (int ts = 0; ts < total_stages; ts++, t_global++) {
                     const int st = t_global % STAGES;
+                    if (rank == 0 && ts == fetch_at) next = publish(q + 1);
                     if (t_global >= STAGES &&
                         !mbar_wait(&empty[st], ((t_global / STAGES) - 1) & 1, abort, err)) {
                         ok = false;
