@@ -324,7 +324,7 @@ def peaks():
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_tc_blind_rotate
     #   -s 2 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline --form tc
-    "k_tc_blind_rotate<1>": {"bytes": 55.99e9 + 76.61e9, "source_sha256": "13147e6eb8ce6cc77c515422710a19063439b909d3ef4131d1d16efd68e874f1"},
+    "k_tc_blind_rotate<2>": {"bytes": 100.73e9 + 103.71e9, "source_sha256": "06e8fa3d45f79ddfa8569c1cc784f182b9c0e875768d3d320ed34d5e101def4d"},
 }
 
 
