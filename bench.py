@@ -42,6 +42,11 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
+    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom"],
+                    help="level: the headline flat level (default); dag: 20,000-gate 60-level "
+                         "DAG through the level scheduler; mixed: 16 uneven circuits "
+                         "interleaved; rom: 64 CMUX-tree reads of a 512-row table + one "
+                         "256-cell RAM write")
     return ap.parse_args()
 
 
@@ -391,10 +396,159 @@ def roofline(form, r, G, p, tc_level):
                          "frac": executed / per_launch_s / 1e12 / peak}}
 
 
+# ---------------------------------------------------------------------------
+# other workloads (one JSON line each; not the headline)
+# ---------------------------------------------------------------------------
+
+def run_other(args):
+    import numpy as np
+    import torch
+    import tfhe_inputs as ti
+    import paper_2010_09410_b300 as tb
+    from paper_2010_09410_b300 import build as tbuild
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return  # replicas only: these workloads run on one GPU
+    torch.cuda.set_device(local)
+    tbuild.build()
+    p = ti.STD
+    seed = ti.SEED_CMUX if args.workload == "rom" else ti.SEED_DAG
+    k = ti.keys(p, seed)
+    ctx = tb.Context(p, local)
+    ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
+                 torch.from_numpy(k.ksk.view(np.int32)).cuda())
+    if args.tc_level >= 0:
+        ctx.set_tc_level(args.tc_level)
+    if args.tc_variant >= 0:
+        ctx.set_tc_variant(args.tc_variant)
+    ctx.sync()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(
+        np.int32 if a.dtype == np.uint32 else a.dtype)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    extra = {}
+
+    if args.workload in ("dag", "mixed"):
+        circs = [ti.layered_dag(ti.SEED_DAG)] if args.workload == "dag" else ti.mixed_circuits()
+        bits = [ti.random_bits(seed, 900 + i, c.num_inputs) for i, c in enumerate(circs)]
+        cts = [ti.encrypt_tlwe0_bits(p, seed, 950 + i, k.s0, b) for i, b in enumerate(bits)]
+        widest = max(np.bincount(np.concatenate(
+            [np.zeros(0, np.int64)] + [np.asarray(c.level, np.int64) for c in circs])))
+        extra["autotune"] = [list(e) for e in ctx.autotune(int(widest))]
+        plan = ctx.plan(circs)
+        total = sum(c.num_gates for c in circs)
+        dev_in = dev(np.concatenate(cts))
+        out = torch.zeros((total, p.n + 1), dtype=torch.int32, device="cuda")
+
+        def step():
+            plan.run(dev_in, out, use_graph=True)
+        units, unit = total, "gates/s"
+        metric = ("bootstrapped gates/s through the level scheduler, " +
+                  ("20,000-gate 60-level DAG" if args.workload == "dag" else
+                   f"16 uneven circuits ({total} gates) interleaved") + ", graph replay")
+        workload = metric.split(", ", 1)[1]
+        step()
+        ctx.sync()
+        # correctness guard: every output decrypts to the plaintext circuit
+        truth = np.array([[[ti.plain_gate(t, a, b) for b in (0, 1)] for a in (0, 1)]
+                          for t in range(10)], np.uint8)
+        got = out.cpu().numpy().view(np.uint32)
+        ok, off = True, 0
+        for c, b in zip(circs, bits):
+            w = np.concatenate([b.astype(np.uint8), np.zeros(c.num_gates, np.uint8)])
+            for L in range(int(c.level.max()) + 1):
+                gs = np.nonzero(c.level == L)[0]
+                w[c.num_inputs + gs] = truth[c.types[gs], w[c.idx[gs, 0]], w[c.idx[gs, 1]]]
+            g = got[off: off + c.num_gates]
+            off += c.num_gates
+            ph = (g[:, p.n].astype(np.int64) -
+                  (g[:, :p.n].astype(np.int64) * k.s0.astype(np.int64)).sum(1)) & 0xFFFFFFFF
+            ok &= bool(np.array_equal((ph < (1 << 31)).astype(np.uint8), w[c.num_inputs:]))
+        extra["decrypt_ok"] = ok
+        extra["levels"] = plan.num_levels
+        if args.workload == "mixed":
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(plan.num_levels)]
+            start = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1)
+            start.record()
+            plan.run(dev_in, out, level_events=ev)
+            torch.cuda.synchronize()
+            extra["circuit_done_ms"] = [round(start.elapsed_time(ev[L]), 2)
+                                        for L in plan.circuit_last_level]
+            extra["circuit_gates"] = [c.num_gates for c in circs]
+    else:
+        rom = ti.cmux_rom(p, seed)
+        ram = ti.ram_write(p, seed)
+        addr = dev(rom.addr_trgsw)
+        table = dev(rom.table)
+        rout = torch.zeros((64, 2, p.N), dtype=torch.int32, device="cuda")
+        raddr = dev(ram.addr_trgsw)
+        rnew = dev(ram.new_cell)
+        cells0 = dev(ram.cells)
+        cells = cells0.clone()
+        ctx.reserve(256)
+
+        def step():
+            ctx.cmux_tree_read(addr, table, 9, rout)
+            cells.copy_(cells0)
+            ctx.ram_write(raddr, 8, rnew, cells)
+        units, unit = 64 * 511 + 256 * 8, "CMUX external products/s"
+        metric = "CMUX external products/s (64 reads of a 512-row TRLWE table + 256-cell RAM write)"
+        workload = "ROM 512 rows x 64 reads (9 address bits) + RAM write 256 cells (8 bits), N=1024 l=3 Bgbit=6"
+        step()
+        ctx.sync()
+        got = rout.cpu().numpy().view(np.uint32)
+        # correctness guard: phase b - a*s of the first 32 coefficients (negacyclic)
+        s1 = k.s1.astype(np.int64)
+        N = p.N
+        dec = np.zeros((64, 32), np.uint8)
+        for r in range(64):
+            a_, b_ = got[r, 0].astype(np.int64), got[r, 1].astype(np.int64)
+            for j in range(32):
+                # (a * s)[j] = sum_{i <= j} a[i] s[j-i] - sum_{i > j} a[i] s[N+j-i]
+                acc = int((a_[:j + 1] * s1[j::-1]).sum() - (a_[j + 1:] * s1[N - 1:j:-1]).sum())
+                ph = (int(b_[j]) - acc) & 0xFFFFFFFF
+                dec[r, j] = 1 if ph < (1 << 31) else 0
+        extra["decrypt_ok"] = bool(np.array_equal(dec, rom.table_bits[rom.addrs, :32]))
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    line = {
+        "metric": metric, "value": units * args.steps / (ms / 1e3), "unit": unit, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": workload, "units_per_step": units,
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "clocks": clk, **extra,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "level":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -266,8 +266,9 @@ typedef struct tfhe_circuit {
 
 /* Build a schedule for `num_circuits` independent circuits evaluated together:
  * gates are grouped by level (longest path from the primary inputs) and level k of
- * every circuit runs in one batch.  `form` as for tfhe_gate_batch, or -1 to let
- * the plan's autotuner pick a form per level width.  The plan owns its device
+ * every circuit runs in one batch.  `form` as for tfhe_gate_batch, or -1 to let the
+ * plan pick a form and Karatsuba level per level width (tfhe_ctx_autotune's table, or
+ * a fixed rule before autotuning).  The plan owns its device
  * copies of the wiring; the context must outlive the plan. */
 int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, int num_circuits, int form,
                       tfhe_plan **out);
@@ -289,6 +290,22 @@ int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_ou
                   void **level_events, void *stream);
 
 void tfhe_plan_destroy(tfhe_plan *plan);
+
+/* Plan autotuner (the level scheduler's choice of form and Karatsuba level per batch
+ * width).  Times every form and tensor-core Karatsuba level on batches of 64, 128, ...
+ * and max_gates gates of pseudo-random ciphertexts (one warm-up and two timed runs on
+ * `stream`; a candidate more than twice as slow as the best stops being timed at larger
+ * widths) and keeps the fastest per width; plans built afterwards with form = -1 use the
+ * entry at the nearest width (log scale).  Without it plans use a fixed rule measured on
+ * B300 at N = 1024.  Allocates scratch for 3 * max_gates ciphertexts; keeps the key
+ * windows of the levels the table uses.  Blocks until done (seconds).  Results of every
+ * form and level are identical; only speed differs. */
+int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream);
+/* The autotuner's table: fills up to `cap` entries (any pointer may be NULL) with
+ * width, form, Karatsuba level (-1 for the NTT form) and milliseconds per batch; returns
+ * the number of entries (0 before tfhe_ctx_autotune). */
+int tfhe_ctx_tune_table(const tfhe_ctx *ctx, int *widths, int *forms, int *levels, float *ms,
+                        int cap);
 
 #ifdef __cplusplus
 }

@@ -40,6 +40,8 @@ EXPORTS = [
     "tfhe_ctx_set_tc_variant",
     "tfhe_ctx_tc_variant",
     "tfhe_ctx_set_tc_pass_limit",
+    "tfhe_ctx_autotune",
+    "tfhe_ctx_tune_table",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -97,6 +99,8 @@ def lib():
         "tfhe_ctx_set_tc_variant": (i32, [vp, i32]),
         "tfhe_ctx_tc_variant": (i32, [vp]),
         "tfhe_ctx_set_tc_pass_limit": (i32, [vp, i32]),
+        "tfhe_ctx_autotune": (i32, [vp, i32, vp]),
+        "tfhe_ctx_tune_table": (i32, [vp, vp, vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -178,6 +182,19 @@ class Context:
     def set_tc_pass_limit(self, limit: int):
         """Largest per-gate sum of |digit| accumulated in one TMEM pass (0 .. 2^17, -1 default)."""
         self._check(lib().tfhe_ctx_set_tc_pass_limit(self.h, limit), "set_tc_pass_limit")
+
+    def autotune(self, max_gates: int, stream=None):
+        """Time every form / Karatsuba level per batch width; plans with form -1 use it."""
+        self._check(lib().tfhe_ctx_autotune(self.h, max_gates, _stream(stream)), "autotune")
+        return self.tune_table()
+
+    def tune_table(self):
+        """[(width, form, tc_level, ms)] measured by autotune (empty before)."""
+        n = lib().tfhe_ctx_tune_table(self.h, None, None, None, None, 0)
+        w, f, lv = (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))()
+        ms = (ctypes.c_float * max(n, 1))()
+        lib().tfhe_ctx_tune_table(self.h, w, f, lv, ms, n)
+        return [(w[i], f[i], lv[i], ms[i]) for i in range(n)]
 
     def enable_timing(self, on: bool = True):
         self._check(lib().tfhe_ctx_enable_timing(self.h, 1 if on else 0), "enable_timing")

@@ -54,7 +54,12 @@ struct tfhe_ctx {
     int32_t *st_idx = nullptr;
 
     TcWorkspace *tc = nullptr;
-    int tc_min_width = 128;  // plan autotuner: narrowest level run in the tensor-core form
+    // plan autotuner: the fastest (form, Karatsuba level) measured per batch width
+    struct TuneEntry {
+        int width, form, level;
+        float ms;
+    };
+    std::vector<TuneEntry> tune;
 
     // Workspace generation: bumped by every reallocation of a context-owned buffer, so a
     // captured plan graph (which holds raw addresses) knows to re-record itself.  While
@@ -118,17 +123,26 @@ int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc
 int tfhe_tc_supported(const tfhe_ctx *ctx);
 int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *bsk, cudaStream_t st);
 int tfhe_tc_set_level(tfhe_ctx *ctx, int level);
-int tfhe_tc_reserve(tfhe_ctx *ctx, int gates);
+int tfhe_tc_level(tfhe_ctx *ctx);
+// key windows of Karatsuba `level` (-1: the context's level) expanded for the loaded keys
+int tfhe_tc_ensure_level(tfhe_ctx *ctx, int level, cudaStream_t st);
+void tfhe_tc_keep_levels(tfhe_ctx *ctx, unsigned mask);
+// tensor-core buffers and the job table of a `gates`-gate BlindRotate at `level`
+int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level);
 int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant);
 int tfhe_tc_variant(tfhe_ctx *ctx);
-int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);  // tensor-core buffers + job table for `gates`
+int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);
+int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                         cudaStream_t st, int level);
+int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);
 // Reallocate a context-owned device buffer to at least `need` bytes (no copy); refused
 // while a plan graph is being recorded; bumps mem_gen.
 int tfhe_grow(tfhe_ctx *ctx, void **ptr, size_t *cap_bytes, size_t need, const char *what);
-int tfhe_tc_level(tfhe_ctx *ctx);
-int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                         cudaStream_t st);
-int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);
+// gate.cu: tfhe_gate_batch with the tensor-core Karatsuba level chosen per call (-1: the
+// context's level)
+int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
+                        const int32_t *in_idx, uint32_t *out, int G, int form, int tc_level,
+                        cudaStream_t st);
 void tfhe_tc_free(tfhe_ctx *ctx);
 
 #define TFHE_CUDA_TRY(ctx, call)                                                        \

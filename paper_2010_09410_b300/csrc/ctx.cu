@@ -185,7 +185,7 @@ extern "C" int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates) {
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     const int rc = tfhe_ensure_workspace(ctx, max_gates);
     if (rc != TFHE_OK) return rc;
-    return tfhe_tc_reserve(ctx, max_gates);
+    return tfhe_tc_reserve(ctx, max_gates, -1);
 }
 
 extern "C" int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream) {

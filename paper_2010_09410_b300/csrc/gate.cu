@@ -233,15 +233,16 @@ static int check_form(tfhe_ctx *ctx, int form) {
     if (form == TFHE_FORM_TC) {
         if (!tfhe_tc_supported(ctx))
             return tfhe_set_error(ctx, TFHE_EUNSUPPORTED,
-                                  "tensor-core form needs N = 1024, l * 2 <= 6, Bgbit <= 6");
+                                  "tensor-core form needs 256 <= N <= 1024, Bgbit <= 6 and "
+                                  "l * N * 32 * 128 <= 2^24");
         return TFHE_OK;
     }
     return tfhe_set_error(ctx, TFHE_EINVAL, "unknown form");
 }
 
 static int blind_rotate_dispatch(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                                 int form, cudaStream_t st) {
-    if (form == TFHE_FORM_TC) return tfhe_blind_rotate_tc(ctx, bar, acc, G, st);
+                                 int form, cudaStream_t st, int tc_level = -1) {
+    if (form == TFHE_FORM_TC) return tfhe_blind_rotate_tc(ctx, bar, acc, G, st, tc_level);
     return tfhe_blind_rotate_ntt(ctx, bar, acc, G, st);
 }
 
@@ -249,6 +250,13 @@ extern "C" int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in
                                const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
                                int form, void *stream) {
     if (!ctx) return TFHE_EINVAL;
+    return tfhe_gate_batch_cfg(ctx, in, num_in, types, in_idx, out, G, form, -1,
+                               (cudaStream_t)stream);
+}
+
+int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
+                        const int32_t *in_idx, uint32_t *out, int G, int form, int tc_level,
+                        cudaStream_t stream) {
     if (G < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch: G < 0");
     if (G == 0) return TFHE_OK;
     if (!in || !types || !in_idx || !out || num_in < 1)
@@ -268,7 +276,7 @@ extern "C" int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in
     tm.stop();
     rc = tfhe_check_launch(ctx, "combine_modswitch");
     if (rc != TFHE_OK) return rc;
-    rc = blind_rotate_dispatch(ctx, ctx->ws_bar, ctx->ws_acc, G, form, st);
+    rc = blind_rotate_dispatch(ctx, ctx->ws_bar, ctx->ws_acc, G, form, st, tc_level);
     if (rc != TFHE_OK) return rc;
     return launch_extract_keyswitch(ctx, ctx->ws_acc, out, G, types, in_idx, num_in, st);
 }

@@ -2,6 +2,7 @@
 // gates; level k of every circuit runs as one tfhe_gate_batch; the whole level
 // schedule is optionally captured into a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -12,6 +13,7 @@ struct tfhe_plan {
     int64_t total_inputs = 0, total_gates = 0, total_wires = 0;
     std::vector<int64_t> level_off;   // [num_levels + 1] offsets into the level-major gate list
     std::vector<int> level_form;      // form per level
+    std::vector<int> level_tc;        // Karatsuba level per level (tensor-core form)
     std::vector<int> circuit_last;    // last level of each circuit
     uint8_t *d_types = nullptr;       // level-major gate types
     int32_t *d_idx = nullptr;         // level-major input wire indices (internal numbering)
@@ -49,11 +51,38 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
     delete plan;
 }
 
-// Form for a level of `width` gates when the caller lets the plan choose (form = -1):
-// the tensor-core form once the batch is wide enough to fill its 128-gate tiles.
-static int tfhe_plan_pick_form(tfhe_ctx *ctx, int64_t width) {
-    if (!tfhe_tc_supported(ctx)) return TFHE_FORM_NTT;
-    return width >= ctx->tc_min_width ? TFHE_FORM_TC : TFHE_FORM_NTT;
+// Form and Karatsuba level for a level of `width` gates when the caller lets the plan
+// choose (form = -1).  After tfhe_ctx_autotune: the measured winner at the nearest tuned
+// width (log scale).  Before: a rule from a B300 sweep at N = 1024 (per-level ms, 630
+// steps): the NTT form is faster up to about 300 gates (30-39 ms, one block per gate),
+// Karatsuba level 1 from there to about 2,500 gates (49-75 ms), level 2 beyond.
+static void plan_pick(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
+    *level = -1;
+    if (!tfhe_tc_supported(ctx)) {
+        *form = TFHE_FORM_NTT;
+        return;
+    }
+    if (!ctx->tune.empty()) {
+        const tfhe_ctx::TuneEntry *best = &ctx->tune[0];
+        double bd = 1e30;
+        for (const auto &e : ctx->tune) {
+            const double d = std::fabs(std::log2((double)e.width) - std::log2((double)std::max<int64_t>(width, 1)));
+            if (d < bd || (d == bd && e.width > best->width)) {
+                bd = d;
+                best = &e;
+            }
+        }
+        *form = best->form;
+        *level = best->level;
+        return;
+    }
+    if (width < 384) {
+        *form = TFHE_FORM_NTT;
+        return;
+    }
+    *form = TFHE_FORM_TC;
+    const int L = tfhe_tc_level(ctx);
+    *level = (width < 2560 && L > 1) ? 1 : L;
 }
 
 // Size the context's workspaces for every level of the plan (a later call of another
@@ -66,7 +95,8 @@ static int plan_reserve(tfhe_plan *plan) {
     int rc = tfhe_ensure_workspace(ctx, (int)max_w);
     for (int L = 0; L < plan->num_levels && rc == TFHE_OK; L++)
         if (plan->level_form[L] == TFHE_FORM_TC)
-            rc = tfhe_tc_reserve(ctx, (int)(plan->level_off[L + 1] - plan->level_off[L]));
+            rc = tfhe_tc_reserve(ctx, (int)(plan->level_off[L + 1] - plan->level_off[L]),
+                                 plan->level_tc[L]);
     return rc;
 }
 
@@ -153,11 +183,12 @@ extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, in
         }
     }
     plan->level_form.assign(num_levels, form);
+    plan->level_tc.assign(num_levels, -1);
     int64_t max_w = 0;
     for (int L = 0; L < num_levels; L++) {
         const int64_t w = plan->level_off[L + 1] - plan->level_off[L];
         max_w = std::max(max_w, w);
-        if (form == -1) plan->level_form[L] = tfhe_plan_pick_form(ctx, w);
+        if (form == -1) plan_pick(ctx, w, &plan->level_form[L], &plan->level_tc[L]);
     }
     const size_t wb = (size_t)ctx->p.n + 1;
     if (cudaSetDevice(ctx->device) != cudaSuccess ||
@@ -204,10 +235,10 @@ static int plan_enqueue(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *g
     for (int L = 0; L < plan->num_levels; L++) {
         const int64_t off = plan->level_off[L];
         const int G = (int)(plan->level_off[L + 1] - off);
-        int rc = tfhe_gate_batch(ctx, plan->d_wires, plan->total_wires, plan->d_types + off,
-                                 plan->d_idx + 2 * off,
-                                 plan->d_wires + (plan->total_inputs + off) * wb, G,
-                                 plan->level_form[L], st);
+        int rc = tfhe_gate_batch_cfg(ctx, plan->d_wires, plan->total_wires, plan->d_types + off,
+                                     plan->d_idx + 2 * off,
+                                     plan->d_wires + (plan->total_inputs + off) * wb, G,
+                                     plan->level_form[L], plan->level_tc[L], st);
         if (rc != TFHE_OK) return rc;
         if (events && events[L]) TFHE_CUDA_TRY(ctx, cudaEventRecord((cudaEvent_t)events[L], st));
     }
@@ -262,4 +293,118 @@ extern "C" int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32
     }
     TFHE_CUDA_TRY(ctx, cudaGraphLaunch(plan->exec, st));
     return TFHE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time every form and Karatsuba level at a ladder of batch widths on
+// pseudo-random ciphertexts and keep the fastest per width (used by plans, form = -1).
+// ---------------------------------------------------------------------------
+
+// in[i] = hashed words (uniform TLWEs: uniform rotations, so no BlindRotate step is
+// trivial); gate g reads inputs 2g, 2g+1 and has type g mod 10.
+__global__ void k_tune_inputs(uint32_t *in, size_t words, uint8_t *types, int32_t *idx, int G) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += stride) {
+        uint64_t h = e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        h ^= h >> 31;
+        h *= 0xD6E8FEB86659FD93ull;
+        h ^= h >> 32;
+        in[e] = (uint32_t)h;
+    }
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)G; g += stride) {
+        types[g] = (uint8_t)(g % 10);
+        idx[2 * g] = (int32_t)(2 * g);
+        idx[2 * g + 1] = (int32_t)(2 * g + 1);
+    }
+}
+
+extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (max_gates < 1) return tfhe_set_error(ctx, TFHE_EINVAL, "autotune: max_gates < 1");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "autotune: keys not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t w1 = (size_t)ctx->p.n + 1;
+    uint32_t *in = nullptr, *out = nullptr;
+    uint8_t *types = nullptr;
+    int32_t *idx = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = TFHE_OK;
+    if (cudaMalloc(&in, 2 * (size_t)max_gates * w1 * 4) != cudaSuccess ||
+        cudaMalloc(&out, (size_t)max_gates * w1 * 4) != cudaSuccess ||
+        cudaMalloc(&types, max_gates) != cudaSuccess ||
+        cudaMalloc(&idx, 2 * (size_t)max_gates * 4) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = tfhe_set_error(ctx, TFHE_ENOMEM, "autotune: scratch allocation");
+    }
+    std::vector<tfhe_ctx::TuneEntry> table;
+    if (rc == TFHE_OK) {
+        k_tune_inputs<<<256, 256, 0, st>>>(in, 2 * (size_t)max_gates * w1, types, idx, max_gates);
+        rc = tfhe_check_launch(ctx, "tune_inputs");
+    }
+    // candidates: the NTT form, and the tensor-core form at every supported level
+    std::vector<std::pair<int, int>> cand = {{TFHE_FORM_NTT, -1}};
+    if (tfhe_tc_supported(ctx))
+        for (int L = 0; L <= 2; L++)
+            if (tfhe_tc_ensure_level(ctx, L, st) == TFHE_OK) cand.push_back({TFHE_FORM_TC, L});
+    ctx->err.clear();
+    std::vector<int> widths;
+    for (int w = 64; w < max_gates; w *= 2) widths.push_back(w);
+    widths.push_back(max_gates);
+    std::vector<bool> alive(cand.size(), true);
+    for (int w : widths) {
+        if (rc != TFHE_OK) break;
+        tfhe_ctx::TuneEntry best{w, TFHE_FORM_NTT, -1, 1e30f};
+        std::vector<float> ms(cand.size(), 1e30f);
+        for (size_t ci = 0; ci < cand.size() && rc == TFHE_OK; ci++) {
+            if (!alive[ci]) continue;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3 && rc == TFHE_OK; rep++) {  // one warm-up, two timed
+                cudaEventRecord(e0, st);
+                rc = tfhe_gate_batch_cfg(ctx, in, 2 * (int64_t)w, types, idx, out, w,
+                                         cand[ci].first, cand[ci].second, st);
+                cudaEventRecord(e1, st);
+                if (rc == TFHE_OK && cudaEventSynchronize(e1) != cudaSuccess)
+                    rc = tfhe_set_error(ctx, TFHE_ECUDA, "autotune: timing");
+                float x = 0;
+                if (rc == TFHE_OK && rep > 0 && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess)
+                    t = std::min(t, x);
+            }
+            ms[ci] = t;
+            if (t < best.ms) best = {w, cand[ci].first, cand[ci].second, t};
+        }
+        // a candidate more than twice as slow as the best stops being timed at larger
+        // widths (each form's time grows with the width at least as fast beyond this)
+        for (size_t ci = 0; ci < cand.size(); ci++)
+            if (ms[ci] > 2 * best.ms) alive[ci] = false;
+        table.push_back(best);
+    }
+    if (rc == TFHE_OK) rc = tfhe_ctx_sync(ctx, stream);
+    if (rc == TFHE_OK) {
+        ctx->tune = table;
+        unsigned used = 0;
+        for (const auto &e : table)
+            if (e.form == TFHE_FORM_TC && e.level >= 0) used |= 1u << e.level;
+        tfhe_tc_keep_levels(ctx, used);  // keep only the windows the table uses
+    }
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (types) cudaFree(types);
+    if (idx) cudaFree(idx);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+extern "C" int tfhe_ctx_tune_table(const tfhe_ctx *ctx, int *widths, int *forms, int *levels,
+                                   float *ms, int cap) {
+    if (!ctx) return TFHE_EINVAL;
+    const int n = (int)ctx->tune.size();
+    for (int i = 0; i < n && i < cap; i++) {
+        if (widths) widths[i] = ctx->tune[i].width;
+        if (forms) forms[i] = ctx->tune[i].form;
+        if (levels) levels[i] = ctx->tune[i].level;
+        if (ms) ms[i] = ctx->tune[i].ms;
+    }
+    return n;
 }

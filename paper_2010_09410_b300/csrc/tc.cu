@@ -1143,11 +1143,16 @@ static void build_plan(int N, int L, std::vector<KTerm> &terms) {
 }
 
 struct TcWorkspace {
-    int level = -1;            // Karatsuba levels of the prepared windows
-    std::vector<KTerm> terms;
-    KTerm *d_terms = nullptr;
-    uint4 *win = nullptr;      // window units for every step
-    size_t win_cap = 0;        // bytes
+    // per Karatsuba level: term plan and key windows (several levels can be resident, so
+    // a plan can run each batch width at the level that suits it)
+    struct Level {
+        std::vector<KTerm> terms;
+        KTerm *d_terms = nullptr;
+        uint4 *win = nullptr;      // window units for every step
+        size_t win_cap = 0;        // bytes
+        bool ready = false;        // windows expanded for the current keys
+    };
+    Level lv[3];
     uint4 *digits = nullptr;
     size_t digits_cap = 0;     // bytes
     uint32_t *sync = nullptr;  // job counter and per-tile progress counters
@@ -1158,8 +1163,8 @@ struct TcWorkspace {
         uint32_t *d = nullptr;  // per-step product-job table
         int len = 0;            // entries
     };
-    std::map<int, JobTable> tables;  // by 2 * gate-tile count + pair form (kept: captured
-                                     // graphs use them)
+    std::map<int, JobTable> tables;  // by (level, pair form, gate tiles); kept: captured
+                                     // graphs use them
     int sms = 0;
     int max_pairs[3] = {-1, -1, -1};  // co-resident SM pairs of the pair kernel, per level
     int want_level = -1;       // requested Karatsuba levels (-1: default)
@@ -1192,8 +1197,10 @@ static bool level_ok(const tfhe_params &p, int L) {
 void tfhe_tc_free(tfhe_ctx *ctx) {
     if (!ctx->tc) return;
     TcWorkspace *w = ctx->tc;
-    if (w->d_terms) cudaFree(w->d_terms);
-    if (w->win) cudaFree(w->win);
+    for (auto &L : w->lv) {
+        if (L.d_terms) cudaFree(L.d_terms);
+        if (L.win) cudaFree(L.win);
+    }
     if (w->digits) cudaFree(w->digits);
     if (w->sync) cudaFree(w->sync);
     if (w->acc_t) cudaFree(w->acc_t);
@@ -1206,41 +1213,77 @@ static int grow_dev(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need, const c
     return tfhe_grow(ctx, ptr, cap, need, what);
 }
 
-// (Re)build the term plan and expand the windows of the whole BSK for `level`.
+// (Re)build the term plan of `level` and expand the windows of the whole BSK for it.
 static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
-    TcWorkspace *w = ctx->tc;
+    TcWorkspace::Level &V = ctx->tc->lv[level];
     if (ctx->capturing)
         return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core windows: cannot rebuild while recording");
-    // job tables depend on the term plan
-    for (auto &t : w->tables) cudaFree(t.second.d);
-    w->tables.clear();
-    ctx->mem_gen++;
-    build_plan(p.N, level, w->terms);
-    const int T = (int)w->terms.size();
+    build_plan(p.N, level, V.terms);
+    const int T = (int)V.terms.size();
     const int s = p.N >> level;
-    if (!w->d_terms && cudaMalloc(&w->d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
+    if (!V.d_terms && cudaMalloc(&V.d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
         return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core term plan");
-    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(w->d_terms, w->terms.data(), sizeof(KTerm) * T,
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(V.d_terms, V.terms.data(), sizeof(KTerm) * T,
                                        cudaMemcpyHostToDevice, st));
     const size_t npoly = (size_t)p.n * 2 * p.l * 2;
     const size_t bytes = npoly * T * PLANES * 2 * (size_t)s * sizeof(uint4);
-    int rc = grow_dev(ctx, (void **)&w->win, &w->win_cap, bytes, "tensor-core key windows");
+    int rc = grow_dev(ctx, (void **)&V.win, &V.win_cap, bytes, "tensor-core key windows");
     if (rc != TFHE_OK) return rc;
-    k_tc_windows<<<dim3((unsigned)npoly, T), 256, 0, st>>>(ctx->bsk_raw, p.N, s, T, w->d_terms,
-                                                          w->win);
+    k_tc_windows<<<dim3((unsigned)npoly, T), 256, 0, st>>>(ctx->bsk_raw, p.N, s, T, V.d_terms,
+                                                          V.win);
     rc = tfhe_check_launch(ctx, "tc_windows");
     if (rc != TFHE_OK) return rc;
-    w->level = level;
+    V.ready = true;
     return TFHE_OK;
 }
 
-// Expand the windows of the whole BSK (called when the keys are loaded).
+static int resolve_level(tfhe_ctx *ctx, int level) {
+    return level >= 0 ? level
+                      : (ctx->tc && ctx->tc->want_level >= 0 ? ctx->tc->want_level : default_level(ctx->p));
+}
+
+// Windows of `level` (-1: the context's level) expanded for the loaded keys.
+int tfhe_tc_ensure_level(tfhe_ctx *ctx, int level, cudaStream_t st) {
+    if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
+    level = resolve_level(ctx, level);
+    if (!level_ok(ctx->p, level))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba level not supported for this N");
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    if (!ctx->has_keys || ctx->tc->lv[level].ready) return TFHE_OK;
+    return prepare_windows(ctx, level, st);
+}
+
+// New keys: re-expand every level in use (and the context's level).
 int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *, cudaStream_t st) {
     if (!tfhe_tc_supported(ctx)) return TFHE_OK;
     if (!ctx->tc) ctx->tc = new TcWorkspace();
-    const int L = ctx->tc->want_level >= 0 ? ctx->tc->want_level : default_level(ctx->p);
-    return prepare_windows(ctx, L, st);
+    const int L0 = resolve_level(ctx, -1);
+    for (int L = 0; L < 3; L++) {
+        TcWorkspace::Level &V = ctx->tc->lv[L];
+        if (V.ready || L == L0) {
+            V.ready = false;
+            const int rc = prepare_windows(ctx, L, st);
+            if (rc != TFHE_OK) return rc;
+        }
+    }
+    return TFHE_OK;
+}
+
+// Free the key windows of levels outside `mask` (bit L = level L) except the context's
+// level; they are expanded again if a later call needs them.
+void tfhe_tc_keep_levels(tfhe_ctx *ctx, unsigned mask) {
+    if (!ctx->tc) return;
+    const int L0 = resolve_level(ctx, -1);
+    for (int L = 0; L < 3; L++) {
+        TcWorkspace::Level &V = ctx->tc->lv[L];
+        if (L == L0 || (mask >> L) & 1 || !V.win) continue;
+        cudaFree(V.win);
+        V.win = nullptr;
+        V.win_cap = 0;
+        V.ready = false;
+        ctx->mem_gen++;
+    }
 }
 
 int tfhe_tc_set_level(tfhe_ctx *ctx, int level) {
@@ -1250,19 +1293,20 @@ int tfhe_tc_set_level(tfhe_ctx *ctx, int level) {
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba level not supported for this N");
     if (!ctx->tc) ctx->tc = new TcWorkspace();
     ctx->tc->want_level = level;
-    if (ctx->has_keys && ctx->tc->level != level) return prepare_windows(ctx, level, 0);
-    return TFHE_OK;
+    return tfhe_tc_ensure_level(ctx, level, 0);
 }
 
 int tfhe_tc_level(tfhe_ctx *ctx) {
     if (!tfhe_tc_supported(ctx)) return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no tensor-core form");
-    return ctx->tc && ctx->tc->want_level >= 0 ? ctx->tc->want_level : default_level(ctx->p);
+    return resolve_level(ctx, -1);
 }
 
 // Per-step job table for `tiles` gate tiles (see the kernel comment for the order).
-static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace::JobTable **out) {
+static int prepare_table(tfhe_ctx *ctx, int level, int tiles, bool pair,
+                         const TcWorkspace::JobTable **out) {
     TcWorkspace *w = ctx->tc;
-    const int key = 2 * tiles + (pair ? 1 : 0);
+    const std::vector<KTerm> &terms = w->lv[level].terms;
+    const int key = ((level * 2 + (pair ? 1 : 0)) << 16) | tiles;
     auto it = w->tables.find(key);
     if (it != w->tables.end()) {
         *out = &it->second;
@@ -1270,10 +1314,10 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace:
     }
     if (ctx->capturing)
         return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core job table missing while recording a graph");
-    const int s = ctx->p.N >> w->level;
+    const int s = ctx->p.N >> level;
     const int bpp = s / NB;
     int nphase = 0;
-    for (const KTerm &t : w->terms) nphase = t.phase + 1 > nphase ? t.phase + 1 : nphase;
+    for (const KTerm &t : terms) nphase = t.phase + 1 > nphase ? t.phase + 1 : nphase;
     // entries name the gate tile, or in the pair form the tile pair (tiles 2u, 2u+1)
     const int units = pair ? (tiles + 1) / 2 : tiles;
     // Phase ph of unit u is emitted at slot u + ph * lag: a unit's later phases come about
@@ -1281,7 +1325,7 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace:
     // wait for are done, and the unit's last product of a step sits well before its first
     // product of the next step, leaving time for that step's digit jobs.  Every job still
     // follows all jobs it waits for.
-    const int per_unit = (int)w->terms.size() * 2 * bpp;
+    const int per_unit = (int)terms.size() * 2 * bpp;
     int sms = w->sms;
     if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const int lanes = pair ? sms / 2 : sms;  // product jobs running at once
@@ -1292,10 +1336,10 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace:
             const int gt = slot - ph * lag;
             if (gt < 0 || gt >= units) continue;
             int dep = 0;  // product jobs of this tile in earlier phases
-            for (const KTerm &t : w->terms)
+            for (const KTerm &t : terms)
                 if (t.phase < ph) dep += 2 * bpp;
-            for (int j = 0; j < (int)w->terms.size(); j++) {
-                if (w->terms[j].phase != ph) continue;
+            for (int j = 0; j < (int)terms.size(); j++) {
+                if (terms[j].phase != ph) continue;
                 for (int c = 0; c < 2; c++)
                     for (int b = 0; b < bpp; b++) tab.push_back(pack_job(JOB_E, gt, j, c, b, dep));
             }
@@ -1315,14 +1359,14 @@ static int prepare_table(tfhe_ctx *ctx, int tiles, bool pair, const TcWorkspace:
 
 // Buffers and job table of a G-gate BlindRotate, sized before the first launch (and
 // before a graph that contains it is recorded).
-static int reserve_tc(tfhe_ctx *ctx, int G, const TcWorkspace::JobTable **table) {
+static int reserve_tc(tfhe_ctx *ctx, int G, int level, const TcWorkspace::JobTable **table) {
     const tfhe_params &p = ctx->p;
     TcWorkspace *w = ctx->tc;
     const bool pair = use_pair(ctx);
     const int tiles = (G + TILE_M - 1) / TILE_M;
     const int tiles_pad = pair ? (tiles + 1) / 2 * 2 : tiles;
-    const int T = (int)w->terms.size();
-    const int s = p.N >> w->level;
+    const int T = (int)w->lv[level].terms.size();
+    const int s = p.N >> level;
     const uint4 *old_digits = w->digits;
     int rc = grow_dev(ctx, (void **)&w->digits, &w->digits_cap,
                       (size_t)tiles_pad * T * 2 * p.l * s * TILE_M * 2, "tensor-core digit buffer");
@@ -1336,31 +1380,35 @@ static int reserve_tc(tfhe_ctx *ctx, int G, const TcWorkspace::JobTable **table)
                   "tensor-core accumulators");
     if (rc != TFHE_OK) return rc;
     const TcWorkspace::JobTable *t = nullptr;
-    rc = prepare_table(ctx, tiles, pair, &t);
+    rc = prepare_table(ctx, level, tiles, pair, &t);
     if (rc == TFHE_OK && table) *table = t;
     return rc;
 }
 
-int tfhe_tc_reserve(tfhe_ctx *ctx, int gates) {
-    if (gates <= 0 || !tfhe_tc_supported(ctx) || !ctx->tc || !ctx->tc->win || ctx->tc->level < 0)
-        return TFHE_OK;  // nothing to size before the keys are loaded
-    return reserve_tc(ctx, gates, nullptr);
+int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level) {
+    if (gates <= 0 || !tfhe_tc_supported(ctx) || !ctx->has_keys) return TFHE_OK;
+    int rc = tfhe_tc_ensure_level(ctx, level, 0);  // nothing to size before the keys are loaded
+    if (rc != TFHE_OK) return rc;
+    return reserve_tc(ctx, gates, resolve_level(ctx, level), nullptr);
 }
 
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                         cudaStream_t st) {
+                         cudaStream_t st, int level) {
     const tfhe_params &p = ctx->p;
     if (G == 0) return TFHE_OK;
     if (!tfhe_tc_supported(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
+    int rc = tfhe_tc_ensure_level(ctx, level, st);
+    if (rc != TFHE_OK) return rc;
+    level = resolve_level(ctx, level);
     TcWorkspace *w = ctx->tc;
-    if (!w || !w->win || w->level < 0)
-        return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
+    const TcWorkspace::Level &V = w->lv[level];
+    if (!V.ready) return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
     const int tiles = (G + TILE_M - 1) / TILE_M;
-    const int T = (int)w->terms.size();
-    const int s = p.N >> w->level;
+    const int T = (int)V.terms.size();
+    const int s = p.N >> level;
     const TcWorkspace::JobTable *table = nullptr;
-    int rc = reserve_tc(ctx, G, &table);
+    rc = reserve_tc(ctx, G, level, &table);
     if (rc != TFHE_OK) return rc;
     if (!w->sms) {
         int sms = 0;
@@ -1372,11 +1420,11 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     const int n1 = p.n + 1;
     void (*kern)(BrArgs);
     if (pair)
-        kern = w->level == 0 ? k_tc_blind_rotate<0, true>
-             : (w->level == 1 ? k_tc_blind_rotate<1, true> : k_tc_blind_rotate<2, true>);
+        kern = level == 0 ? k_tc_blind_rotate<0, true>
+             : (level == 1 ? k_tc_blind_rotate<1, true> : k_tc_blind_rotate<2, true>);
     else
-        kern = w->level == 0 ? k_tc_blind_rotate<0, false>
-             : (w->level == 1 ? k_tc_blind_rotate<1, false> : k_tc_blind_rotate<2, false>);
+        kern = level == 0 ? k_tc_blind_rotate<0, false>
+             : (level == 1 ? k_tc_blind_rotate<1, false> : k_tc_blind_rotate<2, false>);
     const int smem = smem_bytes(p.N, pair);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 3 * (size_t)tiles_pad) * 4, st));
@@ -1398,11 +1446,11 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.total_e = (long long)p.n * table->len;
     args.total_d = (long long)p.n * tiles * DPARTS;
     args.table = table->d;
-    args.terms = w->d_terms;
+    args.terms = V.d_terms;
     args.bar = bar;
     args.acc = w->acc_t;
     args.digits = w->digits;
-    args.win = w->win;
+    args.win = V.win;
     args.sync = w->sync;
     args.err = ctx->d_err;
 
@@ -1419,7 +1467,7 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        int &mp = w->max_pairs[w->level];
+        int &mp = w->max_pairs[level];
         if (mp < 0) {
             cfg.gridDim = dim3(2 * (w->sms / 2));
             int n = 0;
