@@ -65,6 +65,10 @@ def _lib():
         "orc_homgate": (i32, [P, vp, vp, i32, vp, vp, vp]),
         "orc_gate_batch": (i32, [P, vp, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_int64,
                                  ctypes.c_int64]),
+        "orc_hommux_noks": (None, [P, vp, vp, vp, vp, vp]),
+        "orc_hommux": (None, [P, vp, vp, vp, vp, vp, vp]),
+        "orc_mux_batch": (i32, [P, vp, vp, vp, ctypes.c_int64, vp, i32, vp, ctypes.c_int64,
+                                ctypes.c_int64]),
         "orc_cmux_tree_read": (None, [P, vp, vp, i32, vp]),
         "orc_ram_write": (None, [P, vp, i32, vp, vp]),
         "orc_extprod_count": (ctypes.c_uint64, []),
@@ -245,6 +249,56 @@ def gate_batch(params, bsk, ksk, inp, types, idx, gates=None, threads: int | Non
         rc = lib.orc_gate_batch(pp, pb, pk, pi, inp.shape[0], pt, px, po, int(g), int(g) + 1)
         if rc != 0:
             raise ValueError(f"bad gate {g}")
+
+    threads = threads or os.cpu_count() or 1
+    if threads == 1 or len(gates) == 1:
+        for g in gates:
+            one(g)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(one, gates))
+    return out[gates]
+
+
+def hommux_noks(params, bsk, c, a, b):
+    """HomMUX without SE and IKS (reading R13): TLWE c, a, b -> TRLWE u32[2][N]."""
+    bsk, pb = _c(bsk, np.uint32)
+    (c, pc), (a, pa), (b, pbb) = _c(c, np.uint32), _c(a, np.uint32), _c(b, np.uint32)
+    out = np.zeros((2, params.N), np.uint32)
+    _lib().orc_hommux_noks(_p(params), pb, pc, pa, pbb, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def hommux(params, bsk, ksk, c, a, b):
+    """HomMUX (reading R13): TLWE c, a, b -> TLWE u32[n+1] decrypting to c ? a : b."""
+    bsk, pb = _c(bsk, np.uint32)
+    ksk, pk = _c(ksk, np.uint32)
+    (c, pc), (a, pa), (b, pbb) = _c(c, np.uint32), _c(a, np.uint32), _c(b, np.uint32)
+    out = np.zeros(params.n + 1, np.uint32)
+    _lib().orc_hommux(_p(params), pb, pk, pc, pa, pbb, ctypes.c_void_p(out.ctypes.data))
+    return out
+
+
+def mux_batch(params, bsk, ksk, inp, idx, noks=False, gates=None, threads: int | None = None):
+    """MUXes of a batch (idx [G][3]: selector, input taken when it is 1, the other), all
+    or the listed subset, one per thread.  TLWE outputs u32[*][n+1], or TRLWE outputs
+    u32[*][2][N] with noks."""
+    bsk, pb = _c(bsk, np.uint32)
+    ksk, pk = _c(ksk, np.uint32)
+    inp, pi = _c(inp, np.uint32)
+    idx, px = _c(idx, np.int32)
+    G = idx.shape[0]
+    gates = np.arange(G) if gates is None else np.asarray(gates, np.int64)
+    out = (np.zeros((G, 2, params.N), np.uint32) if noks
+           else np.zeros((G, params.n + 1), np.uint32))
+    po = ctypes.c_void_p(out.ctypes.data)
+    pp = _p(params)
+    lib = _lib()
+
+    def one(g):
+        if lib.orc_mux_batch(pp, pb, pk, pi, inp.shape[0], px, 1 if noks else 0, po,
+                             int(g), int(g) + 1) != 0:
+            raise ValueError(f"bad mux {g}")
 
     threads = threads or os.cpu_count() or 1
     if threads == 1 or len(gates) == 1:

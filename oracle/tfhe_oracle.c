@@ -33,6 +33,11 @@
  *   R8 RAM write bar (Section 8.2 "Write Unit" and its Remark): for cell c the
  *      controlled data passes through v CMUXes, bit j ascending; the selector is
  *      C_j when bit j of c is 1 and G - C_j otherwise (G the gadget TRGSW of 1).
+ *   R13 HomMUX (Section 2.1.2 "Homomorphic Gates", "HomMUX without SE and IKS"; the
+ *      paper names the gate but not its steps): MUX(c, a, b) = c ? a : b as
+ *      u = BlindRotate(AND(c, a)) + BlindRotate(ANDNY(c, b)) + (0, mu X^0), the two
+ *      gate combinations as in R6 and mu = 1/8; "without SE and IKS" is u itself
+ *      (three TLWE in, one TRLWE out); HomMUX is IKS(SE(u)).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -287,6 +292,64 @@ int orc_gate_batch(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk
         if (orc_homgate(p, bsk, ksk, types[g], in + (size_t)a * w, in + (size_t)b * w,
                         out + (size_t)g * w) != 0)
             return -1;
+    }
+    return 0;
+}
+
+/* ---- HomMUX (reading R13) ---------------------------------------------------- */
+
+/* HomMUX without SE and IKS: TLWE c, a, b -> TRLWE out u32[2][N]. */
+void orc_hommux_noks(const orc_params *p, const uint32_t *bsk, const uint32_t *c,
+                     const uint32_t *a, const uint32_t *b, uint32_t *out) {
+    const int n = p->n, N = p->N;
+    uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint32_t *bar = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)2 * N);
+    /* c AND a (type 1) */
+    orc_gate_combine(n, 1, c, a, lin);
+    for (int k = 0; k <= n; k++) bar[k] = orc_modswitch(N, lin[k]);
+    orc_blind_rotate(p, bsk, bar, out);
+    /* (not c) AND b (type 6, ANDNY) */
+    orc_gate_combine(n, 6, c, b, lin);
+    for (int k = 0; k <= n; k++) bar[k] = orc_modswitch(N, lin[k]);
+    orc_blind_rotate(p, bsk, bar, acc);
+    for (int k = 0; k < 2 * N; k++) out[k] += acc[k];
+    out[N] += 1u << 29; /* + (0, mu X^0) */
+    free(lin);
+    free(bar);
+    free(acc);
+}
+
+/* HomMUX: TLWE c, a, b -> TLWE out u32[n+1] = IKS(SE(u)). */
+void orc_hommux(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk, const uint32_t *c,
+                const uint32_t *a, const uint32_t *b, uint32_t *out) {
+    const int N = p->N;
+    uint32_t *u = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)2 * N);
+    uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(N + 1));
+    orc_hommux_noks(p, bsk, c, a, b, u);
+    orc_sample_extract(N, u, ext);
+    orc_keyswitch(p, ksk, ext, out);
+    free(u);
+    free(ext);
+}
+
+/* MUXes g in [g_begin, g_end): out[g] = MUX(in[idx[g][0]], in[idx[g][1]], in[idx[g][2]])
+ * (selector, then the input chosen when it is 1, then the other), TLWE (noks = 0) or
+ * TRLWE (noks = 1) outputs.  Returns 0, or -1 on a bad index. */
+int orc_mux_batch(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk,
+                  const uint32_t *in, int64_t num_in, const int32_t *idx, int noks, uint32_t *out,
+                  int64_t g_begin, int64_t g_end) {
+    const size_t w = (size_t)p->n + 1;
+    const size_t wo = noks ? (size_t)2 * p->N : w;
+    for (int64_t g = g_begin; g < g_end; g++) {
+        const int32_t s = idx[3 * g], a = idx[3 * g + 1], b = idx[3 * g + 2];
+        if (s < 0 || a < 0 || b < 0 || s >= num_in || a >= num_in || b >= num_in) return -1;
+        if (noks)
+            orc_hommux_noks(p, bsk, in + (size_t)s * w, in + (size_t)a * w, in + (size_t)b * w,
+                            out + (size_t)g * wo);
+        else
+            orc_hommux(p, bsk, ksk, in + (size_t)s * w, in + (size_t)a * w, in + (size_t)b * w,
+                       out + (size_t)g * wo);
     }
     return 0;
 }

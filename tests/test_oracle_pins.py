@@ -322,6 +322,57 @@ def test_gate_rejects_unknown_type():
         orc.gate_combine(4, 10, np.zeros(5), np.zeros(5))
 
 
+# ---- HomMUX (reading R13) --------------------------------------------------------------
+
+MUX_CASES = [(c, a, b) for c in (0, 1) for a in (0, 1) for b in (0, 1)]
+
+
+def test_hommux_truth_table_toy_params():
+    """MUX(c, a, b) decrypts to c ? a : b for all eight inputs, twice each, real keys."""
+    p = ti.TOY
+    k = ti.keys(p, ti.SEED_TOY)
+    bits = np.array([x for case in MUX_CASES * 2 for x in case], np.uint8)
+    inp = ti.encrypt_tlwe0_bits(p, ti.SEED_TOY, 31, k.s0, bits)
+    idx = np.arange(3 * 16, dtype=np.int32).reshape(16, 3)
+    out = orc.mux_batch(p, k.bsk, k.ksk, inp, idx)
+    want = [a if c else b for c, a, b in MUX_CASES * 2]
+    assert orc.tlwe_decrypt(k.s0, out).tolist() == want
+
+
+def test_hommux_without_ks_coefficient_zero_is_the_mux():
+    """HomMUX without SE and IKS: coefficient 0 of the TRLWE has phase +1/8 for a 1 and
+    -1/8 for a 0, within the bootstrapping noise (far below 1/16)."""
+    p = ti.TOY
+    k = ti.keys(p, ti.SEED_TOY)
+    bits = np.array([x for case in MUX_CASES for x in case], np.uint8)
+    inp = ti.encrypt_tlwe0_bits(p, ti.SEED_TOY, 32, k.s0, bits)
+    idx = np.arange(24, dtype=np.int32).reshape(8, 3)
+    u = orc.mux_batch(p, k.bsk, k.ksk, inp, idx, noks=True)
+    for g, (c, a, b) in enumerate(MUX_CASES):
+        ph = int(s32(orc.trlwe_phase(k.s1, u[g])[0]))
+        want = MU if (a if c else b) else -MU
+        assert abs(ph - want) < MU // 2, (c, a, b, ph)
+
+
+def test_hommux_tfhe_like_params():
+    p = ti.STD
+    k = ti.keys(p, ti.SEED_FLAT)
+    cases = MUX_CASES[1::2]  # four of the eight cases at the full parameters
+    bits = np.array([x for case in cases for x in case], np.uint8)
+    inp = ti.encrypt_tlwe0_bits(p, ti.SEED_FLAT, 33, k.s0, bits)
+    idx = np.arange(3 * len(cases), dtype=np.int32).reshape(len(cases), 3)
+    out = orc.mux_batch(p, k.bsk, k.ksk, inp, idx)
+    assert orc.tlwe_decrypt(k.s0, out).tolist() == [a if c else b for c, a, b in cases]
+
+
+def test_mux_batch_rejects_bad_index():
+    p = ti.TOY
+    k = ti.keys(p, ti.SEED_TOY)
+    inp = np.zeros((3, p.n + 1), np.uint32)
+    with pytest.raises(ValueError):
+        orc.mux_batch(p, k.bsk, k.ksk, inp, np.array([[0, 1, 3]], np.int32))
+
+
 # ---- CMUX memory ---------------------------------------------------------------------
 
 def test_cmux_tree_reads_every_address_toy():
