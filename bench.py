@@ -42,11 +42,11 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
-    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom"],
+    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux"],
                     help="level: the headline flat level (default); dag: 20,000-gate 60-level "
                          "DAG through the level scheduler; mixed: 16 uneven circuits "
                          "interleaved; rom: 64 CMUX-tree reads of a 512-row table + one "
-                         "256-cell RAM write")
+                         "256-cell RAM write; mux: 2048 HomMUXes (4096 bootstraps)")
     return ap.parse_args()
 
 
@@ -413,7 +413,7 @@ def run_other(args):
     torch.cuda.set_device(local)
     tbuild.build()
     p = ti.STD
-    seed = ti.SEED_CMUX if args.workload == "rom" else ti.SEED_DAG
+    seed = {"rom": ti.SEED_CMUX, "mux": ti.SEED_FLAT}.get(args.workload, ti.SEED_DAG)
     k = ti.keys(p, seed)
     ctx = tb.Context(p, local)
     ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
@@ -477,6 +477,28 @@ def run_other(args):
             extra["circuit_done_ms"] = [round(start.elapsed_time(ev[L]), 2)
                                         for L in plan.circuit_last_level]
             extra["circuit_gates"] = [c.num_gates for c in circs]
+    elif args.workload == "mux":
+        G = 2048
+        bits = ti.random_bits(seed, 60, 3 * G)
+        inp = dev(ti.encrypt_tlwe0_bits(p, seed, 61, k.s0, bits))
+        idx3 = dev(np.arange(3 * G, dtype=np.int32).reshape(G, 3))
+        out = torch.zeros((G, p.n + 1), dtype=torch.int32, device="cuda")
+        form = tb.FORM_TC if args.form != "ntt" else tb.FORM_NTT
+
+        def step():
+            ctx.mux_batch(inp, idx3, out, form=form)
+        units, unit = G, "HomMUX/s"
+        metric = "HomMUX/s (2048 three-input MUX gates, two bootstraps each), bit-exact"
+        workload = "2048 HomMUX, n=630 N=1024 l=3 Bgbit=6 t=8 basebit=2"
+        step()
+        ctx.sync()
+        got = out.cpu().numpy().view(np.uint32)
+        ph = (got[:, p.n].astype(np.int64) -
+              (got[:, :p.n].astype(np.int64) * k.s0.astype(np.int64)).sum(1)) & 0xFFFFFFFF
+        b3 = bits.reshape(G, 3)
+        extra["decrypt_ok"] = bool(np.array_equal((ph < (1 << 31)).astype(np.uint8),
+                                                  np.where(b3[:, 0] == 1, b3[:, 1], b3[:, 2])))
+        extra["form"] = "tc" if form == tb.FORM_TC else "ntt"
     else:
         rom = ti.cmux_rom(p, seed)
         ram = ti.ram_write(p, seed)

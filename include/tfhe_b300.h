@@ -187,6 +187,22 @@ int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches);
 int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
                     const int32_t *in_idx, uint32_t *out, int G, int form, void *stream);
 
+/* HomMUX (Section 2.1.2 "Homomorphic Gates": the three-operand MUX; "HomMUX without SE
+ * and IKS"): out[g] = MUX(in[idx3[g][0]], in[idx3[g][1]], in[idx3[g][2]]), i.e. the
+ * selector's plaintext chooses the second input when it is 1 and the third when it is 0.
+ * Two bootstraps per MUX: BlindRotate of (selector AND second) and of ((not selector)
+ * AND third), whose TRLWEs are summed with (0, 1/8 X^0); tfhe_mux_batch then applies
+ * SampleExtract and the identity key switch (out: device u32[G][n+1] TLWE lvl0), while
+ * tfhe_mux_batch_noks returns the summed TRLWE (out_trlwe: device u32[G][2][N]).
+ * in: device u32[num_in][n+1]; idx3: device int32[G][3]; form as for tfhe_gate_batch.
+ * Host-detectable errors return before launch; a MUX with an index outside
+ * [0, num_in) gets an all-zero output and TFHE_EINVAL at the next tfhe_ctx_sync.
+ * Asynchronous on `stream`; workspaces for 2G bootstraps are grown as needed. */
+int tfhe_mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,
+                   uint32_t *out, int G, int form, void *stream);
+int tfhe_mux_batch_noks(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,
+                        uint32_t *out_trlwe, int G, int form, void *stream);
+
 /* tfhe_gate_batch with HOST buffers (pinned or pageable): copies the inputs in,
  * evaluates, copies the outputs back, and returns once `out` holds the result.
  * Uses context-owned device staging buffers. */

@@ -42,6 +42,8 @@ EXPORTS = [
     "tfhe_ctx_set_tc_pass_limit",
     "tfhe_ctx_autotune",
     "tfhe_ctx_tune_table",
+    "tfhe_mux_batch",
+    "tfhe_mux_batch_noks",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -101,6 +103,8 @@ def lib():
         "tfhe_ctx_set_tc_pass_limit": (i32, [vp, i32]),
         "tfhe_ctx_autotune": (i32, [vp, i32, vp]),
         "tfhe_ctx_tune_table": (i32, [vp, vp, vp, vp, vp, i32]),
+        "tfhe_mux_batch": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
+        "tfhe_mux_batch_noks": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -217,6 +221,14 @@ class Context:
         self._check(lib().tfhe_gate_batch(self.h, _ptr(inp), inp.shape[0], _ptr(types),
                                           _ptr(idx), _ptr(out), G, form, _stream(stream)),
                     "gate_batch")
+        return out
+
+    def mux_batch(self, inp, idx3, out, form=FORM_NTT, stream=None, noks=False):
+        """HomMUX of rows idx3[g] = (selector, taken if 1, taken if 0); TLWE out [G][n+1],
+        or with noks the TRLWE before SampleExtract and key switching [G][2][N]."""
+        fn = lib().tfhe_mux_batch_noks if noks else lib().tfhe_mux_batch
+        self._check(fn(self.h, _ptr(inp), inp.shape[0], _ptr(idx3), _ptr(out), idx3.shape[0],
+                       form, _stream(stream)), "mux_batch")
         return out
 
     def gate_batch_noalloc(self, inp, types, idx, out, stream=None):

@@ -44,6 +44,56 @@ __global__ void k_combine_modswitch(int n, int shift, const uint32_t *__restrict
     }
 }
 
+// ---- HomMUX: c ? a : b as two bootstraps, c AND a and (not c) AND b, whose TRLWEs are
+// summed with (0, 1/8 X^0) (Section 2.1.2 "HomMUX without SE and IKS"); SampleExtract
+// and the identity key switch of the sum give the TLWE gate output.
+__device__ __forceinline__ bool mux_ok(const int32_t *idx3, int64_t num_in, int64_t g) {
+    const int32_t s = idx3[3 * g], a = idx3[3 * g + 1], b = idx3[3 * g + 2];
+    return s >= 0 && a >= 0 && b >= 0 && s < num_in && a < num_in && b < num_in;
+}
+
+// Block h: half h & 1 of MUX h >> 1 (0: c AND a, 1: (not c) AND b), combined and
+// ModSwitched like k_combine_modswitch.
+__global__ void k_mux_combine_modswitch(int n, int shift, const uint32_t *__restrict__ in,
+                                        int64_t num_in, const int32_t *__restrict__ idx3,
+                                        uint32_t *__restrict__ bar, int *err) {
+    const int64_t h = blockIdx.x, g = h >> 1;
+    const int half = (int)(h & 1);
+    uint32_t *o = bar + h * (n + 1);
+    if (!mux_ok(idx3, num_in, g)) {
+        if (threadIdx.x == 0) atomicCAS(err, 0, TFHE_EINVAL);
+        for (int k = threadIdx.x; k <= n; k += blockDim.x) o[k] = 0;
+        return;
+    }
+    const uint32_t *cs = in + (int64_t)idx3[3 * g] * (n + 1);
+    const uint32_t *x = in + (int64_t)idx3[3 * g + 1 + half] * (n + 1);
+    const uint32_t sc = half ? 0xFFFFFFFFu : 1u;  // -c for the (not c) half
+    const uint32_t kappa = 0u - (1u << 29);       // -1/8 (AND, ANDNY)
+    const uint32_t rnd = 1u << (shift - 1);
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+        uint32_t v = sc * cs[k] + x[k];
+        if (k == n) v += kappa;
+        o[k] = (v + rnd) >> shift;
+    }
+}
+
+// out[g] = acc[2g] + acc[2g+1] + (0, mu X^0); all zero for a MUX with a bad index.
+__global__ void k_mux_sum(int N, int G, const uint32_t *__restrict__ acc, int64_t num_in,
+                          const int32_t *__restrict__ idx3, uint32_t *__restrict__ out) {
+    const size_t total = (size_t)G * 2 * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t g = e / (2 * N);
+        const int w = (int)(e % (2 * N));
+        uint32_t v = 0;
+        if (mux_ok(idx3, num_in, (int64_t)g)) {
+            v = acc[(2 * g) * 2 * N + w] + acc[(2 * g + 1) * 2 * N + w];
+            if (w == N) v += 1u << 29;
+        }
+        out[e] = v;
+    }
+}
+
 // SampleExtract + identity key switch for GT gates per block.  Thread c owns the
 // 16-byte column c of the lvl0 ciphertext (words 4c..4c+3 of the padded row).
 //   phase 1: unsigned key-switching digits of every extracted mask coefficient
@@ -389,4 +439,56 @@ int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *
                                   const uint8_t *types, const int32_t *idx, int64_t num_in,
                                   cudaStream_t st) {
     return launch_extract_keyswitch(ctx, acc, out, G, types, idx, num_in, st);
+}
+
+// ---- HomMUX batches ----------------------------------------------------------------
+
+static int mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,
+                     uint32_t *out, int G, int form, bool noks, cudaStream_t st) {
+    if (G < 0) return tfhe_set_error(ctx, TFHE_EINVAL, "mux_batch: G < 0");
+    if (G == 0) return TFHE_OK;
+    if (!in || !idx3 || !out || num_in < 1)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "mux_batch: null pointer or num_in < 1");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "mux_batch: keys not set");
+    if ((int64_t)G * 2 > 0x7FFFFFFF) return tfhe_set_error(ctx, TFHE_EINVAL, "mux_batch: G too large");
+    int rc = check_form(ctx, form);
+    if (rc != TFHE_OK) return rc;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    rc = tfhe_ensure_workspace(ctx, 2 * G);  // two bootstraps per MUX
+    if (rc != TFHE_OK) return rc;
+    const tfhe_params &p = ctx->p;
+    const int shift = 32 - (ctx->logN + 1);
+    {
+        StageTimer tm(ctx, TFHE_STAGE_COMBINE, st);
+        k_mux_combine_modswitch<<<2 * G, 256, 0, st>>>(p.n, shift, in, num_in, idx3, ctx->ws_bar,
+                                                       ctx->d_err);
+        tm.stop();
+        rc = tfhe_check_launch(ctx, "mux_combine_modswitch");
+        if (rc != TFHE_OK) return rc;
+    }
+    rc = blind_rotate_dispatch(ctx, ctx->ws_bar, ctx->ws_acc, 2 * G, form, st);
+    if (rc != TFHE_OK) return rc;
+    uint32_t *sum = noks ? out : ctx->ws_tmp;
+    {
+        StageTimer tm(ctx, TFHE_STAGE_COMBINE, st);
+        k_mux_sum<<<1184, 256, 0, st>>>(p.N, G, ctx->ws_acc, num_in, idx3, sum);
+        tm.stop();
+        rc = tfhe_check_launch(ctx, "mux_sum");
+        if (rc != TFHE_OK) return rc;
+    }
+    if (noks) return TFHE_OK;
+    return launch_extract_keyswitch(ctx, ctx->ws_tmp, out, G, nullptr, nullptr, 0, st);
+}
+
+extern "C" int tfhe_mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                              const int32_t *idx3, uint32_t *out, int G, int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    return mux_batch(ctx, in, num_in, idx3, out, G, form, false, (cudaStream_t)stream);
+}
+
+extern "C" int tfhe_mux_batch_noks(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
+                                   const int32_t *idx3, uint32_t *out_trlwe, int G, int form,
+                                   void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    return mux_batch(ctx, in, num_in, idx3, out_trlwe, G, form, true, (cudaStream_t)stream);
 }
