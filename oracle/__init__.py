@@ -70,6 +70,7 @@ def _lib():
         "orc_mux_batch": (i32, [P, vp, vp, vp, ctypes.c_int64, vp, i32, vp, ctypes.c_int64,
                                 ctypes.c_int64]),
         "orc_cmux_tree_read": (None, [P, vp, vp, i32, vp]),
+        "orc_ram_cycle": (None, [P, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
         "orc_ram_write": (None, [P, vp, i32, vp, vp]),
         "orc_extprod_count": (ctypes.c_uint64, []),
         "orc_extprod_count_reset": (None, []),
@@ -332,3 +333,19 @@ def extprod_count() -> int:
 
 def extprod_count_reset() -> None:
     _lib().orc_extprod_count_reset()
+
+
+def ram_cycle(params, bsk, ksk, addr_trgsw, v, flag, wdata, cells):
+    """One RAM cycle (reading R14): returns (read data u32[w][n+1], new cells
+    u32[w][2^v][2][N]); cells is not modified."""
+    bsk, pb = _c(bsk, np.uint32)
+    ksk, pk = _c(ksk, np.uint32)
+    a, pa = _c(addr_trgsw, np.uint32)
+    f, pf = _c(flag, np.uint32)
+    wd, pw = _c(wdata, np.uint32)
+    new = np.array(cells, dtype=np.uint32, copy=True, order="C")
+    w = wd.shape[0]
+    rd = np.zeros((w, params.n + 1), np.uint32)
+    _lib().orc_ram_cycle(_p(params), pb, pk, pa, v, w, pf, pw, ctypes.c_void_p(new.ctypes.data),
+                         ctypes.c_void_p(rd.ctypes.data))
+    return rd, new

@@ -33,6 +33,13 @@
  *   R8 RAM write bar (Section 8.2 "Write Unit" and its Remark): for cell c the
  *      controlled data passes through v CMUXes, bit j ascending; the selector is
  *      C_j when bit j of c is 1 and G - C_j otherwise (G the gadget TRGSW of 1).
+ *   R14 RAM cycle (Section 8.2 "Control Unit" and "Write Unit"): one address per cycle
+ *      for read and write; the w bit blocks are read by CMUX trees sharing the address
+ *      (R7), the read words go through SE and IKS (returned as the read data), the
+ *      controlled data is HomMUX without SE and IKS of (write flag, write data, read
+ *      data) (R13), each block's write bar takes it (R8), and every cell is refreshed by
+ *      SE, IKS, ModSwitch and BlindRotate (R4) back to a TRLWE whose coefficient 0
+ *      carries the bit.
  *   R13 HomMUX (Section 2.1.2 "Homomorphic Gates", "HomMUX without SE and IKS"; the
  *      paper names the gate but not its steps): MUX(c, a, b) = c ? a : b as
  *      u = BlindRotate(AND(c, a)) + BlindRotate(ANDNY(c, b)) + (0, mu X^0), the two
@@ -407,4 +414,41 @@ void orc_ram_write(const orc_params *p, const uint32_t *addr, int v, const uint3
     }
     free(gmc);
     free(r);
+}
+
+/* RAM cycle, reading R14.  cells u32[w][2^v][2][N] (bit block b, cell x) updated in
+ * place; addr u32[v][2l][2][N]; flag u32[n+1]; wdata u32[w][n+1]; rdata u32[w][n+1]
+ * receives the read word (TLWE lvl0, before the write). */
+void orc_ram_cycle(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk,
+                   const uint32_t *addr, int v, int w, const uint32_t *flag, const uint32_t *wdata,
+                   uint32_t *cells, uint32_t *rdata) {
+    const int n = p->n, N = p->N;
+    const size_t tr = (size_t)2 * N, w1 = (size_t)n + 1, rows = (size_t)1 << v;
+    uint32_t *rd = (uint32_t *)malloc(sizeof(uint32_t) * tr);
+    uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(N + 1));
+    uint32_t *ctl = (uint32_t *)malloc(sizeof(uint32_t) * tr);
+    uint32_t *lvl0 = (uint32_t *)malloc(sizeof(uint32_t) * w1);
+    uint32_t *bar = (uint32_t *)malloc(sizeof(uint32_t) * w1);
+    for (int b = 0; b < w; b++) {
+        uint32_t *block = cells + (size_t)b * rows * tr;
+        /* read unit + control unit */
+        orc_cmux_tree_read(p, addr, block, v, rd);
+        orc_sample_extract(N, rd, ext);
+        orc_keyswitch(p, ksk, ext, rdata + (size_t)b * w1);
+        orc_hommux_noks(p, bsk, flag, wdata + (size_t)b * w1, rdata + (size_t)b * w1, ctl);
+        /* write unit: write bars, then the refresh of every cell */
+        orc_ram_write(p, addr, v, ctl, block);
+        for (size_t x = 0; x < rows; x++) {
+            uint32_t *cell = block + x * tr;
+            orc_sample_extract(N, cell, ext);
+            orc_keyswitch(p, ksk, ext, lvl0);
+            for (int k = 0; k <= n; k++) bar[k] = orc_modswitch(N, lvl0[k]);
+            orc_blind_rotate(p, bsk, bar, cell);
+        }
+    }
+    free(rd);
+    free(ext);
+    free(ctl);
+    free(lvl0);
+    free(bar);
 }

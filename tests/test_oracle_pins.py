@@ -405,6 +405,28 @@ def test_ram_write_changes_exactly_the_addressed_cell_toy():
             assert np.array_equal(orc.trlwe_decrypt(k.s1, res[c]), want), (addr, c)
 
 
+@pytest.mark.parametrize("flag_bit,stream", [(0, 1), (1, 2), (1, 3)])
+def test_ram_cycle_reads_then_writes_the_addressed_word_toy(flag_bit, stream):
+    """RAM cycle (reading R14): the read data is the addressed word before the write;
+    afterwards coefficient 0 of every refreshed cell decrypts to the old bit, except the
+    addressed word, which holds the write data when the flag is 1."""
+    p, v, w = ti.TOY, 3, 3
+    rc = ti.ram_cycle(p, ti.SEED_TOY, v=v, w=w, flag_bit=flag_bit, stream=stream)
+    rd, new = orc.ram_cycle(p, rc.keys.bsk, rc.keys.ksk, rc.addr_trgsw, v, rc.flag, rc.wdata,
+                            rc.cells)
+    assert orc.tlwe_decrypt(rc.keys.s0, rd).tolist() == rc.cell_bits[:, rc.addr].tolist()
+    want = rc.cell_bits.copy()
+    if flag_bit:
+        want[:, rc.addr] = rc.wdata_bits
+    got = np.array([[orc.trlwe_decrypt(rc.keys.s1, new[b, x])[0] for x in range(1 << v)]
+                    for b in range(w)])
+    assert np.array_equal(got, want)
+    # refreshed cells carry +-1/8 at coefficient 0 within bootstrapping noise
+    ph = np.array([[int(s32(orc.trlwe_phase(rc.keys.s1, new[b, x])[0])) for x in range(1 << v)]
+                   for b in range(w)])
+    assert np.all(np.abs(np.abs(ph) - MU) < MU // 4)
+
+
 def test_cmux_counts_match_paper_table():
     """Per-bit CMUX counts times w reproduce the paper's Read/Write Unit totals."""
     p = ti.TOY

@@ -384,3 +384,37 @@ def ram_write(p: Params = STD, seed: int = SEED_CMUX, v: int = 8, packed: int = 
     abits = ((addr >> np.arange(v)) & 1).astype(np.uint8)
     addr_trgsw = encrypt_trgsw_bits(p, seed, 23, k.s1, abits)
     return RamWrite(k, v, cb, cells, nb[0], new_cell, addr, addr_trgsw)
+
+
+@dataclasses.dataclass
+class RamCycle:
+    keys: Keys
+    v: int
+    w: int
+    cell_bits: np.ndarray   # u8[w][2^v]: bit of word x in block b at [b][x]
+    cells: np.ndarray       # u32[w][2^v][2][N], the bit at coefficient 0
+    addr: int
+    addr_trgsw: np.ndarray  # u32[v][2l][2][N]
+    flag_bit: int
+    flag: np.ndarray        # u32[n+1]
+    wdata_bits: np.ndarray  # u8[w]
+    wdata: np.ndarray       # u32[w][n+1]
+
+
+def ram_cycle(p: Params = STD, seed: int = SEED_CMUX, v: int = 8, w: int = 16,
+              flag_bit: int = 1, stream: int = 0) -> RamCycle:
+    """A RAM of 2^v words of w bits (one TRLWE per bit, the bit at coefficient 0, the
+    other coefficients encoding 0), a random encrypted address, write flag and word."""
+    k = keys(p, seed)
+    rows = 1 << v
+    cb = random_bits(seed, 70 + stream, w * rows).reshape(w, rows)
+    msg = np.zeros((w * rows, p.N), np.uint8)
+    msg[:, 0] = cb.reshape(-1)
+    cells = encrypt_trlwe_bits(p, seed, 70 + stream, k.s1, msg).reshape(w, rows, 2, p.N)
+    addr = int(random_below(seed, 71 + stream, 1, rows)[0])
+    abits = ((addr >> np.arange(v)) & 1).astype(np.uint8)
+    addr_trgsw = encrypt_trgsw_bits(p, seed, 72 + stream, k.s1, abits)
+    flag = encrypt_tlwe0_bits(p, seed, 73 + stream, k.s0, np.array([flag_bit], np.uint8))[0]
+    wb = random_bits(seed, 74 + stream, w)
+    wdata = encrypt_tlwe0_bits(p, seed, 75 + stream, k.s0, wb)
+    return RamCycle(k, v, w, cb, cells, addr, addr_trgsw, flag_bit, flag, wb, wdata)
