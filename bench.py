@@ -42,11 +42,12 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
-    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux"],
+    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle"],
                     help="level: the headline flat level (default); dag: 20,000-gate 60-level "
                          "DAG through the level scheduler; mixed: 16 uneven circuits "
                          "interleaved; rom: 64 CMUX-tree reads of a 512-row table + one "
-                         "256-cell RAM write; mux: 2048 HomMUXes (4096 bootstraps)")
+                         "256-cell RAM write; mux: 2048 HomMUXes (4096 bootstraps); ramcycle: "
+                         "one RAM cycle of 256 words x 16 bits (4096 refresh bootstraps)")
     return ap.parse_args()
 
 
@@ -413,7 +414,8 @@ def run_other(args):
     torch.cuda.set_device(local)
     tbuild.build()
     p = ti.STD
-    seed = {"rom": ti.SEED_CMUX, "mux": ti.SEED_FLAT}.get(args.workload, ti.SEED_DAG)
+    seed = {"rom": ti.SEED_CMUX, "ramcycle": ti.SEED_CMUX,
+            "mux": ti.SEED_FLAT}.get(args.workload, ti.SEED_DAG)
     k = ti.keys(p, seed)
     ctx = tb.Context(p, local)
     ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
@@ -477,6 +479,30 @@ def run_other(args):
             extra["circuit_done_ms"] = [round(start.elapsed_time(ev[L]), 2)
                                         for L in plan.circuit_last_level]
             extra["circuit_gates"] = [c.num_gates for c in circs]
+    elif args.workload == "ramcycle":
+        v, w = 8, 16
+        rc = ti.ram_cycle(p, seed, v=v, w=w, flag_bit=1)
+        addr, flag, wdata = dev(rc.addr_trgsw), dev(rc.flag), dev(rc.wdata)
+        cells0 = dev(rc.cells)
+        cells = cells0.clone()
+        rdata = torch.zeros((w, p.n + 1), dtype=torch.int32, device="cuda")
+        form = tb.FORM_TC if args.form != "ntt" else tb.FORM_NTT
+
+        def step():
+            cells.copy_(cells0)
+            ctx.ram_cycle(addr, v, flag, wdata, cells, rdata, form=form)
+        units, unit = 1, "RAM cycles/s"
+        metric = "RAM cycles/s (CMUX Memory, 256 words x 16 bits: read, control, write, refresh)"
+        workload = ("RAM cycle, v=8 w=16: 16 CMUX trees of 255 CMUXes, 32 MUX bootstraps, "
+                    "4096 write bars of 8 CMUXes, 4096 refresh bootstraps; N=1024 n=630")
+        step()
+        ctx.sync()
+        got = rdata.cpu().numpy().view(np.uint32)
+        ph = (got[:, p.n].astype(np.int64) -
+              (got[:, :p.n].astype(np.int64) * k.s0.astype(np.int64)).sum(1)) & 0xFFFFFFFF
+        extra["decrypt_ok"] = bool(np.array_equal((ph < (1 << 31)).astype(np.uint8),
+                                                  rc.cell_bits[:, rc.addr]))
+        extra["form"] = "tc" if form == tb.FORM_TC else "ntt"
     elif args.workload == "mux":
         G = 2048
         bits = ti.random_bits(seed, 60, 3 * G)

@@ -280,6 +280,21 @@ typedef struct tfhe_circuit {
     const int32_t *in_idx;  /* host i32[num_gates][2] */
 } tfhe_circuit;
 
+/* One cycle of the CMUX-Memory RAM (Section 8.2: read unit, control unit, write unit)
+ * at one encrypted address.  cells: device u32[w][2^v][2][N], in/out: bit block b of
+ * word x at [b][x], the bit at coefficient 0 (the other coefficients are not used).
+ * addr_trgsw: device u32[v][2l][2][N] (address bit j at [j]); flag: device u32[n+1] TLWE
+ * lvl0 write flag; wdata: device u32[w][n+1] TLWE lvl0 write word; rdata: device
+ * u32[w][n+1] out, the word read at the address before the write.  Steps: the w bit
+ * blocks' CMUX trees (sharing the address) read the word; SampleExtract and the
+ * identity key switch give rdata; HomMUX without SE and IKS of (flag, write bit, read
+ * bit) gives the controlled data; each block's write bar takes it at the address; every
+ * cell is refreshed by SampleExtract, key switching, ModSwitch and BlindRotate.  The
+ * CMUX steps run in the NTT form; `form` selects the BlindRotate form of the MUX and
+ * refresh bootstraps (w * 2^v + 2w bootstraps per cycle).  w * 2^v <= 2^24. */
+int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, int w, const uint32_t *flag,
+                   const uint32_t *wdata, uint32_t *cells, uint32_t *rdata, int form, void *stream);
+
 /* Build a schedule for `num_circuits` independent circuits evaluated together:
  * gates are grouped by level (longest path from the primary inputs) and level k of
  * every circuit runs in one batch.  `form` as for tfhe_gate_batch, or -1 to let the

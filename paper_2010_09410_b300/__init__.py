@@ -44,6 +44,7 @@ EXPORTS = [
     "tfhe_ctx_tune_table",
     "tfhe_mux_batch",
     "tfhe_mux_batch_noks",
+    "tfhe_ram_cycle",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -105,6 +106,7 @@ def lib():
         "tfhe_ctx_tune_table": (i32, [vp, vp, vp, vp, vp, i32]),
         "tfhe_mux_batch": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
         "tfhe_mux_batch_noks": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
+        "tfhe_ram_cycle": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +274,13 @@ class Context:
         self._check(lib().tfhe_ram_write(self.h, _ptr(addr_trgsw), v, _ptr(new_cell), _ptr(cells),
                                          form, _stream(stream)), "ram_write")
         return cells
+
+    def ram_cycle(self, addr_trgsw, v, flag, wdata, cells, rdata, form=FORM_TC, stream=None):
+        """One RAM cycle: reads rdata [w][n+1] at the address, writes if flag, refreshes."""
+        self._check(lib().tfhe_ram_cycle(self.h, _ptr(addr_trgsw), v, wdata.shape[0], _ptr(flag),
+                                         _ptr(wdata), _ptr(cells), _ptr(rdata), form,
+                                         _stream(stream)), "ram_cycle")
+        return rdata
 
     def plan(self, circuits, form=FORM_AUTO):
         return Plan(self, circuits, form)

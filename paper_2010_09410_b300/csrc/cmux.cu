@@ -119,3 +119,106 @@ extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
     return tfhe_ram_write_ntt(ctx, ctx->ws_trgsw_ntt, ctx->ws_trgsw_ntt + (size_t)v * per, v,
                               new_cell, cells, st);
 }
+
+// ---------------------------------------------------------------------------
+// One RAM cycle (Section 8.2: read unit, control unit, write unit)
+// ---------------------------------------------------------------------------
+
+// idx3[b] = (flag, write bit b, read bit b) rows of the MUX input block.
+__global__ void k_ram_mux_idx(int w, int32_t *idx3) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= w) return;
+    idx3[3 * b] = 0;
+    idx3[3 * b + 1] = 1 + b;
+    idx3[3 * b + 2] = 1 + w + b;
+}
+
+extern "C" int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, int w,
+                              const uint32_t *flag, const uint32_t *wdata, uint32_t *cells,
+                              uint32_t *rdata, int form, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    int rc = check_common(ctx, v, form);
+    if (rc != TFHE_OK) return rc;
+    if (w < 1 || ((int64_t)w << v) > (1 << 24))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "ram_cycle: w must be >= 1 and w * 2^v <= 2^24");
+    if (!addr_trgsw || !flag || !wdata || !cells || !rdata)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "ram_cycle: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "ram_cycle: keys not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const tfhe_params &p = ctx->p;
+    const size_t N2 = 2 * (size_t)p.N, w1 = (size_t)p.n + 1, per = (size_t)2 * p.l * N2;
+    const int64_t cells_n = (int64_t)w << v;
+    // scratch: read TRLWEs [w][2N] | controlled TRLWEs [w][2N] | MUX inputs [1+2w][n+1] |
+    //          MUX indices [w][3] | lvl0 [w 2^v][n+1] | ModSwitched [w 2^v][n+1]
+    const size_t o_rd = 0, o_ctl = o_rd + w * N2, o_min = o_ctl + w * N2,
+                 o_idx = o_min + (1 + 2 * (size_t)w) * w1, o_l0 = o_idx + 3 * (size_t)w,
+                 o_bar = o_l0 + (size_t)cells_n * w1, words = o_bar + (size_t)cells_n * w1;
+    rc = tfhe_grow(ctx, (void **)&ctx->ws_ram, &ctx->ws_ram_cap, words * 4, "ram_cycle scratch");
+    if (rc != TFHE_OK) return rc;
+    uint32_t *S = ctx->ws_ram;
+    uint32_t *min = S + o_min;
+    int32_t *idx3 = (int32_t *)(S + o_idx);
+
+    // selectors C_j and G - C_j in the NTT domain (the CMUX parts run in the NTT form)
+    if (ctx->ws_gmc_cap < v) {
+        size_t cap = (size_t)ctx->ws_gmc_cap * per * 4;
+        rc = tfhe_grow(ctx, (void **)&ctx->ws_gmc, &cap, (size_t)v * per * 4, "ram_cycle selectors");
+        if (rc != TFHE_OK) {
+            if (!ctx->ws_gmc) ctx->ws_gmc_cap = 0;
+            return rc;
+        }
+        ctx->ws_gmc_cap = v;
+    }
+    k_gadget_minus<<<256, 256, 0, st>>>(addr_trgsw, ctx->ws_gmc, v, p.l, p.N, p.Bgbit);
+    rc = tfhe_check_launch(ctx, "gadget_minus");
+    if (rc != TFHE_OK) return rc;
+    rc = tfhe_ensure_trgsw_ws(ctx, (size_t)2 * v);
+    if (rc != TFHE_OK) return rc;
+    const uint64_t *c_ntt = ctx->ws_trgsw_ntt, *gmc_ntt = ctx->ws_trgsw_ntt + (size_t)v * per;
+    rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
+    if (rc == TFHE_OK)
+        rc = tfhe_trgsw_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
+    if (rc != TFHE_OK) return rc;
+
+    // read unit: the w bit blocks' CMUX trees share the address (selector stride 0)
+    rc = tfhe_ensure_workspace(ctx, (int)(w * ((int64_t)1 << (v - 1))));
+    if (rc != TFHE_OK) return rc;
+    {
+        uint32_t *buf[2] = {ctx->ws_acc, ctx->ws_tmp};
+        const uint32_t *in = cells;
+        int64_t in_ystride = ((int64_t)1 << v) * (int64_t)N2;
+        for (int j = 0; j < v && rc == TFHE_OK; j++) {
+            const int M = 1 << (v - 1 - j);
+            uint32_t *o = (j == v - 1) ? S + o_rd : buf[j & 1];
+            CmuxGeom g{in + N2, in, o, 2 * (int64_t)N2, in_ystride, (int64_t)N2, (int64_t)M * (int64_t)N2,
+                       0, M, w, (int64_t)w * M};
+            rc = tfhe_cmux_ntt(ctx, c_ntt + (size_t)j * per, g, st);
+            in = o;
+            in_ystride = (int64_t)M * N2;
+        }
+        if (rc != TFHE_OK) return rc;
+    }
+    // control unit: read words to TLWE (returned), then MUX(flag, write bit, read bit)
+    rc = tfhe_launch_extract_keyswitch(ctx, S + o_rd, rdata, w, nullptr, nullptr, 0, st);
+    if (rc != TFHE_OK) return rc;
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(min, flag, w1 * 4, cudaMemcpyDeviceToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(min + w1, wdata, (size_t)w * w1 * 4, cudaMemcpyDeviceToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(min + (1 + (size_t)w) * w1, rdata, (size_t)w * w1 * 4,
+                                       cudaMemcpyDeviceToDevice, st));
+    k_ram_mux_idx<<<(w + 127) / 128, 128, 0, st>>>(w, idx3);
+    rc = tfhe_check_launch(ctx, "ram_mux_idx");
+    if (rc == TFHE_OK) rc = tfhe_mux_batch_impl(ctx, min, 1 + 2 * (int64_t)w, idx3, S + o_ctl, w, form,
+                                                true, st);
+    if (rc != TFHE_OK) return rc;
+    // write unit: each block's write bar selects the controlled data at the address ...
+    for (int b = 0; b < w && rc == TFHE_OK; b++)
+        rc = tfhe_ram_write_ntt(ctx, c_ntt, gmc_ntt, v, S + o_ctl + (size_t)b * N2,
+                                cells + ((size_t)b << v) * N2, st);
+    if (rc != TFHE_OK) return rc;
+    // ... and every cell is refreshed: SE, IKS, ModSwitch, BlindRotate back to a TRLWE
+    rc = tfhe_launch_extract_keyswitch(ctx, cells, S + o_l0, (int)cells_n, nullptr, nullptr, 0, st);
+    if (rc == TFHE_OK) rc = tfhe_launch_modswitch_rows(ctx, S + o_l0, S + o_bar, cells_n, st);
+    if (rc == TFHE_OK) rc = tfhe_blind_rotate_form(ctx, S + o_bar, cells, (int)cells_n, form, st);
+    return rc;
+}

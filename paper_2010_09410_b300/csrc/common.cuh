@@ -46,6 +46,8 @@ struct tfhe_ctx {
     size_t ws_trgsw_cap = 0;           // in TRGSWs
     uint32_t *ws_gmc = nullptr;        // G - C_j selectors for the RAM write
     int ws_gmc_cap = 0;                // in TRGSWs
+    uint32_t *ws_ram = nullptr;        // RAM-cycle scratch (read words, controlled data,
+    size_t ws_ram_cap = 0;             //  MUX inputs, refreshed lvl0 and ModSwitched rows)
 
     // host-API staging (device side)
     size_t st_in_cap = 0, st_gate_cap = 0;
@@ -138,6 +140,16 @@ int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStre
 // Reallocate a context-owned device buffer to at least `need` bytes (no copy); refused
 // while a plan graph is being recorded; bumps mem_gen.
 int tfhe_grow(tfhe_ctx *ctx, void **ptr, size_t *cap_bytes, size_t need, const char *what);
+// gate.cu: building blocks of the RAM cycle (cmux.cu)
+int tfhe_mux_batch_impl(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,
+                        uint32_t *out, int G, int form, bool noks, cudaStream_t st);
+int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
+                                  const uint8_t *types, const int32_t *idx, int64_t num_in,
+                                  cudaStream_t st);
+int tfhe_launch_modswitch_rows(tfhe_ctx *ctx, const uint32_t *in, uint32_t *bar, int64_t G,
+                               cudaStream_t st);
+int tfhe_blind_rotate_form(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
+                           cudaStream_t st);
 // gate.cu: tfhe_gate_batch with the tensor-core Karatsuba level chosen per call (-1: the
 // context's level)
 int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,

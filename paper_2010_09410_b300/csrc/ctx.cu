@@ -76,6 +76,7 @@ extern "C" void tfhe_ctx_destroy(tfhe_ctx *ctx) {
     free_dev(ctx->ws_tmp);
     free_dev(ctx->ws_trgsw_ntt);
     free_dev(ctx->ws_gmc);
+    free_dev(ctx->ws_ram);
     free_dev(ctx->st_in);
     free_dev(ctx->st_out);
     free_dev(ctx->st_types);

@@ -44,6 +44,26 @@ __global__ void k_combine_modswitch(int n, int shift, const uint32_t *__restrict
     }
 }
 
+// bar[g][k] = ModSwitch(in[g][k]) for G rows of n+1 words (a bootstrap of the TLWE
+// itself: the refresh of Section 8.2's write bars).
+__global__ void k_modswitch_rows(int n1, int shift, int64_t G, const uint32_t *__restrict__ in,
+                                 uint32_t *__restrict__ bar) {
+    const size_t total = (size_t)G * n1;
+    const uint32_t rnd = 1u << (shift - 1);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x)
+        bar[e] = (in[e] + rnd) >> shift;
+}
+
+int tfhe_launch_modswitch_rows(tfhe_ctx *ctx, const uint32_t *in, uint32_t *bar, int64_t G,
+                               cudaStream_t st) {
+    k_modswitch_rows<<<1184, 256, 0, st>>>(ctx->p.n + 1, 32 - (ctx->logN + 1), G, in, bar);
+    return tfhe_check_launch(ctx, "modswitch_rows");
+}
+
+int tfhe_blind_rotate_form(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
+                           cudaStream_t st);
+
 // ---- HomMUX: c ? a : b as two bootstraps, c AND a and (not c) AND b, whose TRLWEs are
 // summed with (0, 1/8 X^0) (Section 2.1.2 "HomMUX without SE and IKS"); SampleExtract
 // and the identity key switch of the sum give the TLWE gate output.
@@ -296,6 +316,11 @@ static int blind_rotate_dispatch(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *a
     return tfhe_blind_rotate_ntt(ctx, bar, acc, G, st);
 }
 
+int tfhe_blind_rotate_form(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
+                           cudaStream_t st) {
+    return blind_rotate_dispatch(ctx, bar, acc, G, form, st);
+}
+
 extern "C" int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
                                const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
                                int form, void *stream) {
@@ -478,6 +503,11 @@ static int mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const in
     }
     if (noks) return TFHE_OK;
     return launch_extract_keyswitch(ctx, ctx->ws_tmp, out, G, nullptr, nullptr, 0, st);
+}
+
+int tfhe_mux_batch_impl(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,
+                        uint32_t *out, int G, int form, bool noks, cudaStream_t st) {
+    return mux_batch(ctx, in, num_in, idx3, out, G, form, noks, st);
 }
 
 extern "C" int tfhe_mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
