@@ -71,6 +71,7 @@ def _lib():
                                 ctypes.c_int64]),
         "orc_cmux_tree_read": (None, [P, vp, vp, i32, vp]),
         "orc_ram_cycle": (None, [P, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
+        "orc_rom_read": (None, [P, vp, vp, vp, i32, i32, vp, vp]),
         "orc_ram_write": (None, [P, vp, i32, vp, vp]),
         "orc_extprod_count": (ctypes.c_uint64, []),
         "orc_extprod_count_reset": (None, []),
@@ -349,3 +350,16 @@ def ram_cycle(params, bsk, ksk, addr_trgsw, v, flag, wdata, cells):
     _lib().orc_ram_cycle(_p(params), pb, pk, pa, v, w, pf, pw, ctypes.c_void_p(new.ctypes.data),
                          ctypes.c_void_p(rd.ctypes.data))
     return rd, new
+
+
+def rom_read(params, ksk, addr_trgsw, table, v, w):
+    """ROM read with vertical and horizontal packing (reading R15): returns (TRLWE
+    u32[2][N] holding the word at coefficients 0..w-1, TLWE lvl0 bits u32[w][n+1])."""
+    ksk, pk = _c(ksk, np.uint32)
+    a, pa = _c(addr_trgsw, np.uint32)
+    t, pt = _c(table, np.uint32)
+    trlwe = np.zeros((2, params.N), np.uint32)
+    bits = np.zeros((w, params.n + 1), np.uint32)
+    _lib().orc_rom_read(_p(params), pk, pa, pt, v, w, ctypes.c_void_p(trlwe.ctypes.data),
+                        ctypes.c_void_p(bits.ctypes.data))
+    return trlwe, bits

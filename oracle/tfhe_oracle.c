@@ -33,6 +33,16 @@
  *   R8 RAM write bar (Section 8.2 "Write Unit" and its Remark): for cell c the
  *      controlled data passes through v CMUXes, bit j ascending; the selector is
  *      C_j when bit j of c is 1 and G - C_j otherwise (G the gadget TRGSW of 1).
+ *   R15 ROM with vertical and horizontal packing (Section 8.3 "ROM"; Table "The number
+ *      of CMUXs in CMUX Memory": 8 for the ROM): M words of w bits, P = N / w words per
+ *      TRLWE with word q of a TRLWE in coefficients q w .. q w + w - 1 (bit i at q w + i),
+ *      T = M / P TRLWEs.  Address bits 0 .. log2 P - 1 pick the word inside a TRLWE, the
+ *      rest the TRLWE.  A read first runs the CMUX tree (R7) over the TRLWE bits, then
+ *      the blind rotation ACC <- CMUX(C_j, X^{-w 2^j} ACC, ACC) for the low bits j
+ *      ascending, which brings the word to coefficients 0 .. w-1; bit i is SE at
+ *      coefficient i (the TRLWE times X^{-i}, then R5's extraction) followed by IKS.
+ *      512 words of bytes at N = 1024, i.e. 128 words of 32 bits in 4 TRLWEs, take
+ *      3 + 5 = 8 CMUXes.
  *   R14 RAM cycle (Section 8.2 "Control Unit" and "Write Unit"): one address per cycle
  *      for read and write; the w bit blocks are read by CMUX trees sharing the address
  *      (R7), the read words go through SE and IKS (returned as the read data), the
@@ -451,4 +461,38 @@ void orc_ram_cycle(const orc_params *p, const uint32_t *bsk, const uint32_t *ksk
     free(ctl);
     free(lvl0);
     free(bar);
+}
+
+/* ROM read, reading R15.  addr u32[v][2l][2][N]; table u32[T][2][N] with T = M / (N / w)
+ * a power of two, v = log2 M; out_trlwe u32[2][N] (word at coefficients 0..w-1, may be
+ * NULL); out_bits u32[w][n+1] (TLWE lvl0 of each bit, may be NULL). */
+void orc_rom_read(const orc_params *p, const uint32_t *ksk, const uint32_t *addr,
+                  const uint32_t *table, int v, int w, uint32_t *out_trlwe, uint32_t *out_bits) {
+    const int N = p->N, l = p->l;
+    const size_t tr = (size_t)2 * N, gsw = (size_t)2 * l * tr;
+    int lo = 0;
+    while ((w << lo) < N) lo++;             /* log2 (N / w) */
+    const int hi = v - lo;                  /* TRLWE-selecting bits */
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * tr);
+    uint32_t *rot = (uint32_t *)malloc(sizeof(uint32_t) * tr);
+    uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(N + 1));
+    orc_cmux_tree_read(p, addr + (size_t)lo * gsw, table, hi, acc);
+    for (int j = 0; j < lo; j++) {
+        const int k = (2 * N - ((w << j) % (2 * N))) % (2 * N);  /* X^{-w 2^j} */
+        orc_rotate(N, k, acc, rot);
+        orc_rotate(N, k, acc + N, rot + N);
+        orc_cmux(p, addr + (size_t)j * gsw, rot, acc, acc);
+    }
+    if (out_trlwe) memcpy(out_trlwe, acc, sizeof(uint32_t) * tr);
+    if (out_bits)
+        for (int i = 0; i < w; i++) {
+            const int k = (2 * N - i) % (2 * N);                  /* X^{-i} */
+            orc_rotate(N, k, acc, rot);
+            orc_rotate(N, k, acc + N, rot + N);
+            orc_sample_extract(N, rot, ext);
+            orc_keyswitch(p, ksk, ext, out_bits + (size_t)i * (p->n + 1));
+        }
+    free(acc);
+    free(rot);
+    free(ext);
 }

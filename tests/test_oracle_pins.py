@@ -427,6 +427,32 @@ def test_ram_cycle_reads_then_writes_the_addressed_word_toy(flag_bit, stream):
     assert np.all(np.abs(np.abs(ph) - MU) < MU // 4)
 
 
+def test_packed_rom_reads_every_address_toy():
+    """ROM with vertical and horizontal packing (reading R15): every address of a
+    32-word x 32-bit ROM (4 TRLWEs of 8 words at N = 256) reads back its word, both as
+    the TRLWE's coefficients 0..31 and as 32 TLWE bits."""
+    p = ti.TOY
+    rom = ti.packed_rom(p, ti.SEED_TOY, M=32, w=32, R=32, stream=5)
+    k = rom.keys
+    for r in range(32):
+        trlwe, bits = orc.rom_read(p, k.ksk, rom.addr_trgsw[r], rom.table, rom.v, rom.w)
+        want = rom.words[rom.addrs[r]]
+        assert np.array_equal(orc.trlwe_decrypt(k.s1, trlwe)[:32], want), r
+        assert np.array_equal(orc.tlwe_decrypt(k.s0, bits), want), r
+
+
+def test_packed_rom_cmux_count_matches_paper_table():
+    """The paper's ROM (512 B: 128 words of 32 bits in 4 TRLWEs at N = 1024) takes 8
+    CMUXes per read (Table "The number of CMUXs in CMUX Memory")."""
+    p = ti.STD
+    rom = ti.packed_rom(p, ti.SEED_CMUX, M=128, w=32, R=1, stream=6)
+    assert rom.table.shape == (4, 2, p.N) and rom.v == 7
+    orc.extprod_count_reset()
+    trlwe, bits = orc.rom_read(p, rom.keys.ksk, rom.addr_trgsw[0], rom.table, rom.v, rom.w)
+    assert orc.extprod_count() == 8
+    assert np.array_equal(orc.tlwe_decrypt(rom.keys.s0, bits), rom.words[rom.addrs[0]])
+
+
 def test_cmux_counts_match_paper_table():
     """Per-bit CMUX counts times w reproduce the paper's Read/Write Unit totals."""
     p = ti.TOY

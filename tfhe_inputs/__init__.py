@@ -418,3 +418,32 @@ def ram_cycle(p: Params = STD, seed: int = SEED_CMUX, v: int = 8, w: int = 16,
     wb = random_bits(seed, 74 + stream, w)
     wdata = encrypt_tlwe0_bits(p, seed, 75 + stream, k.s0, wb)
     return RamCycle(k, v, w, cb, cells, addr, addr_trgsw, flag_bit, flag, wb, wdata)
+
+
+@dataclasses.dataclass
+class PackedRom:
+    keys: Keys
+    v: int
+    w: int
+    words: np.ndarray       # u8[M][w] plaintext bits
+    table: np.ndarray       # u32[T][2][N]: word q of TRLWE t at coefficients q w .. q w + w - 1
+    addrs: np.ndarray       # i64[R]
+    addr_trgsw: np.ndarray  # u32[R][v][2l][2][N]
+
+
+def packed_rom(p: Params = STD, seed: int = SEED_CMUX, M: int = 128, w: int = 32,
+               R: int = 8, stream: int = 0) -> PackedRom:
+    """ROM of M words of w bits with vertical and horizontal packing (N / w words per
+    TRLWE), read at R random addresses."""
+    k = keys(p, seed)
+    P = p.N // w
+    T = M // P
+    v = int(M).bit_length() - 1
+    words = random_bits(seed, 80 + stream, M * w).reshape(M, w)
+    msg = words.reshape(T, P * w)
+    table = encrypt_trlwe_bits(p, seed, 80 + stream, k.s1, msg)
+    addrs = random_below(seed, 81 + stream, R, M).astype(np.int64)
+    abits = ((addrs[:, None] >> np.arange(v)[None, :]) & 1).astype(np.uint8)
+    addr_trgsw = encrypt_trgsw_bits(p, seed, 82 + stream, k.s1, abits.reshape(-1)).reshape(
+        R, v, 2 * p.l, 2, p.N)
+    return PackedRom(k, v, w, words, table, addrs, addr_trgsw)
