@@ -42,12 +42,13 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
-    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle"],
+    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle", "romp"],
                     help="level: the headline flat level (default); dag: 20,000-gate 60-level "
                          "DAG through the level scheduler; mixed: 16 uneven circuits "
                          "interleaved; rom: 64 CMUX-tree reads of a 512-row table + one "
                          "256-cell RAM write; mux: 2048 HomMUXes (4096 bootstraps); ramcycle: "
-                         "one RAM cycle of 256 words x 16 bits (4096 refresh bootstraps)")
+                         "one RAM cycle of 256 words x 16 bits (4096 refresh bootstraps); romp: "
+                         "64 reads of the packed 512-byte ROM (128 words x 32 bits)")
     return ap.parse_args()
 
 
@@ -414,7 +415,7 @@ def run_other(args):
     torch.cuda.set_device(local)
     tbuild.build()
     p = ti.STD
-    seed = {"rom": ti.SEED_CMUX, "ramcycle": ti.SEED_CMUX,
+    seed = {"rom": ti.SEED_CMUX, "ramcycle": ti.SEED_CMUX, "romp": ti.SEED_CMUX,
             "mux": ti.SEED_FLAT}.get(args.workload, ti.SEED_DAG)
     k = ti.keys(p, seed)
     ctx = tb.Context(p, local)
@@ -479,6 +480,25 @@ def run_other(args):
             extra["circuit_done_ms"] = [round(start.elapsed_time(ev[L]), 2)
                                         for L in plan.circuit_last_level]
             extra["circuit_gates"] = [c.num_gates for c in circs]
+    elif args.workload == "romp":
+        R = 64
+        prom = ti.packed_rom(p, seed, M=128, w=32, R=R)
+        addr, table = dev(prom.addr_trgsw), dev(prom.table)
+        trlwe = torch.zeros((R, 2, p.N), dtype=torch.int32, device="cuda")
+        bits = torch.zeros((R, 32, p.n + 1), dtype=torch.int32, device="cuda")
+
+        def step():
+            ctx.rom_read(addr, table, prom.v, 32, trlwe, bits)
+        units, unit = R, "ROM reads/s"
+        metric = "ROM reads/s (packed 512-byte ROM, 8 CMUXes + 32 key switches per read)"
+        workload = "64 reads of 128 words x 32 bits in 4 TRLWEs (N=1024): tree + blind rotation"
+        step()
+        ctx.sync()
+        got = bits.cpu().numpy().view(np.uint32).reshape(R * 32, p.n + 1)
+        ph = (got[:, p.n].astype(np.int64) -
+              (got[:, :p.n].astype(np.int64) * k.s0.astype(np.int64)).sum(1)) & 0xFFFFFFFF
+        extra["decrypt_ok"] = bool(np.array_equal((ph < (1 << 31)).astype(np.uint8).reshape(R, 32),
+                                                  prom.words[prom.addrs]))
     elif args.workload == "ramcycle":
         v, w = 8, 16
         rc = ti.ram_cycle(p, seed, v=v, w=w, flag_bit=1)

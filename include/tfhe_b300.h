@@ -280,6 +280,19 @@ typedef struct tfhe_circuit {
     const int32_t *in_idx;  /* host i32[num_gates][2] */
 } tfhe_circuit;
 
+/* ROM read with vertical and horizontal packing (Section 8.3 "ROM"): a ROM of 2^v words
+ * of w bits (w a power of two <= N) stored as T = 2^v * w / N TRLWEs, word q of a TRLWE
+ * in coefficients q w .. q w + w - 1 (bit i at q w + i).  table: device u32[T][2][N];
+ * addr_trgsw: device u32[R][v][2l][2][N] (bit j of read r's address at [r][j]).  Address
+ * bits 0 .. log2(N/w)-1 pick the word inside a TRLWE, the rest the TRLWE.  Per read: a
+ * CMUX tree over the TRLWE bits, then a blind rotation ACC <- CMUX(C_j, X^{-w 2^j} ACC,
+ * ACC) over the low bits (T - 1 + log2(N/w) CMUXes: 8 for 512 bytes at N = 1024), which
+ * leaves the word at coefficients 0 .. w-1.  out_trlwe: device u32[R][2][N] or NULL;
+ * out_bits: device u32[R][w][n+1] TLWE lvl0 (SampleExtract at coefficient i + identity
+ * key switch) or NULL; not both NULL.  CMUXes run in the NTT form.  Asynchronous. */
+int tfhe_rom_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *table, int v, int w,
+                  uint32_t *out_trlwe, uint32_t *out_bits, int R, void *stream);
+
 /* One cycle of the CMUX-Memory RAM (Section 8.2: read unit, control unit, write unit)
  * at one encrypted address.  cells: device u32[w][2^v][2][N], in/out: bit block b of
  * word x at [b][x], the bit at coefficient 0 (the other coefficients are not used).

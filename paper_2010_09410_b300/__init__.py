@@ -45,6 +45,7 @@ EXPORTS = [
     "tfhe_mux_batch",
     "tfhe_mux_batch_noks",
     "tfhe_ram_cycle",
+    "tfhe_rom_read",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
 NUM_STAGES = 8
@@ -107,6 +108,7 @@ def lib():
         "tfhe_mux_batch": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
         "tfhe_mux_batch_noks": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
         "tfhe_ram_cycle": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]),
+        "tfhe_rom_read": (i32, [vp, vp, vp, i32, i32, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -281,6 +283,15 @@ class Context:
                                          _ptr(wdata), _ptr(cells), _ptr(rdata), form,
                                          _stream(stream)), "ram_cycle")
         return rdata
+
+    def rom_read(self, addr_trgsw, table, v, w, out_trlwe=None, out_bits=None, stream=None):
+        """Packed ROM read: out_trlwe [R][2][N] and/or out_bits [R][w][n+1]."""
+        R = addr_trgsw.shape[0]
+        self._check(lib().tfhe_rom_read(self.h, _ptr(addr_trgsw), _ptr(table), v, w,
+                                        _ptr(out_trlwe) if out_trlwe is not None else None,
+                                        _ptr(out_bits) if out_bits is not None else None, R,
+                                        _stream(stream)), "rom_read")
+        return out_trlwe, out_bits
 
     def plan(self, circuits, form=FORM_AUTO):
         return Plan(self, circuits, form)

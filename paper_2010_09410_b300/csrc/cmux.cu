@@ -1,5 +1,7 @@
 // cmux.cu -- CMUX Memory (Section 8.2): the read unit's CMUX tree and the CMUX part
 // of the write unit's write bars.
+#include <algorithm>
+
 #include "common.cuh"
 
 // G - C_j for j < v (Remark, Section 8.2): the selector that encrypts 1 - a_j.
@@ -221,4 +223,101 @@ extern "C" int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, 
     if (rc == TFHE_OK) rc = tfhe_launch_modswitch_rows(ctx, S + o_l0, S + o_bar, cells_n, st);
     if (rc == TFHE_OK) rc = tfhe_blind_rotate_form(ctx, S + o_bar, cells, (int)cells_n, form, st);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// ROM with vertical and horizontal packing (Section 8.3): N / w words of w bits per TRLWE
+// ---------------------------------------------------------------------------
+
+// out[o] = X^{-(base + (o % rep) * step)} in[o / rep] for `rows` output TRLWEs (both
+// polynomials; 0 <= shift < N): coefficient c takes p[c + s], or -p[c + s - N] past N.
+__global__ void k_rotate_rows(int N, int64_t rows, int rep, int base, int step,
+                              const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
+    const size_t total = (size_t)rows * 2 * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t o = e / (2 * N);
+        const int w = (int)(e % (2 * N));
+        const int poly = w / N, cidx = w % N;
+        const int s = (base + (int)(o % rep) * step) % N;
+        const uint32_t *src = in + ((o / rep) * 2 + poly) * (size_t)N;
+        const int k = cidx + s;
+        out[e] = k < N ? src[k] : 0u - src[k - N];
+    }
+}
+
+extern "C" int tfhe_rom_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *table,
+                             int v, int w, uint32_t *out_trlwe, uint32_t *out_bits, int R,
+                             void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    const tfhe_params &p = ctx->p;
+    if (w < 1 || w > p.N || (w & (w - 1)))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "rom_read: w must be a power of two <= N");
+    int lo = 0;
+    while ((w << lo) < p.N) lo++;  // log2(N / w) address bits pick the word in a TRLWE
+    if (v < lo || v - lo > 16)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "rom_read: need log2(N/w) <= v <= log2(N/w) + 16");
+    if (R < 0 || (int64_t)R * w > (1 << 24))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "rom_read: R < 0 or R * w > 2^24");
+    if (R == 0) return TFHE_OK;
+    if (!addr_trgsw || !table || (!out_trlwe && !out_bits))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "rom_read: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "rom_read: keys not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int hi = v - lo;
+    const int64_t N2 = 2 * (int64_t)p.N;
+    const size_t per = (size_t)2 * p.l * 2 * p.N;
+    // selectors in the NTT domain, every read's v address bits
+    int rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
+    if (rc == TFHE_OK) rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
+    if (rc != TFHE_OK) return rc;
+    const uint64_t *sel = ctx->ws_trgsw_ntt;
+    // scratch: two accumulators and one rotated copy per read
+    rc = tfhe_grow(ctx, (void **)&ctx->ws_ram, &ctx->ws_ram_cap, (size_t)3 * R * N2 * 4,
+                   "rom_read scratch");
+    if (rc != TFHE_OK) return rc;
+    uint32_t *acc[2] = {ctx->ws_ram, ctx->ws_ram + (size_t)R * N2};
+    uint32_t *rot = ctx->ws_ram + (size_t)2 * R * N2;
+    rc = tfhe_ensure_workspace(ctx, std::max(R * w, hi > 0 ? R << (hi - 1) : 1));
+    if (rc != TFHE_OK) return rc;
+    // CMUX tree over the TRLWE-selecting bits lo .. v-1 (R7), into acc[0]
+    if (hi == 0) {
+        k_rotate_rows<<<1184, 256, 0, st>>>(p.N, R, R, 0, 0, table, acc[0]);  // broadcast row 0
+        rc = tfhe_check_launch(ctx, "rotate_rows");
+    } else {
+        uint32_t *buf[2] = {ctx->ws_acc, ctx->ws_tmp};
+        const uint32_t *in = table;
+        int64_t in_ystride = 0;
+        for (int j = 0; j < hi && rc == TFHE_OK; j++) {
+            const int M = 1 << (hi - 1 - j);
+            uint32_t *o = (j == hi - 1) ? acc[0] : buf[j & 1];
+            CmuxGeom g{in + N2, in, o, 2 * N2, in_ystride, N2, (int64_t)M * N2, (int64_t)v,
+                       M, R, (int64_t)R * M};
+            rc = tfhe_cmux_ntt(ctx, sel + (size_t)(lo + j) * per, g, st);
+            in = o;
+            in_ystride = (int64_t)M * N2;
+        }
+    }
+    if (rc != TFHE_OK) return rc;
+    // blind rotation by the word bits: ACC <- CMUX(C_j, X^{-w 2^j} ACC, ACC)
+    int cur = 0;
+    for (int j = 0; j < lo && rc == TFHE_OK; j++) {
+        k_rotate_rows<<<1184, 256, 0, st>>>(p.N, R, 1, (w << j) % p.N, 0, acc[cur], rot);
+        rc = tfhe_check_launch(ctx, "rotate_rows");
+        if (rc != TFHE_OK) break;
+        CmuxGeom g{rot, acc[cur], acc[cur ^ 1], 0, N2, 0, N2, (int64_t)v, 1, R, (int64_t)R};
+        rc = tfhe_cmux_ntt(ctx, sel + (size_t)j * per, g, st);
+        cur ^= 1;
+    }
+    if (rc != TFHE_OK) return rc;
+    if (out_trlwe)
+        TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(out_trlwe, acc[cur], (size_t)R * N2 * 4,
+                                           cudaMemcpyDeviceToDevice, st));
+    if (!out_bits) return TFHE_OK;
+    // bit i: SE at coefficient i (X^{-i} then coefficient 0), then the identity key switch
+    k_rotate_rows<<<1184, 256, 0, st>>>(p.N, (int64_t)R * w, w, 0, 1, acc[cur], ctx->ws_acc);
+    rc = tfhe_check_launch(ctx, "rotate_rows");
+    if (rc != TFHE_OK) return rc;
+    return tfhe_launch_extract_keyswitch(ctx, ctx->ws_acc, out_bits, R * w, nullptr, nullptr, 0, st);
 }
