@@ -300,6 +300,27 @@ __device__ __forceinline__ void byte_planes(uint32_t q, int (&pl)[PLANES]) {
 
 constexpr int MAX_TERMS = 9;  // 3^L, L <= 2
 
+// Digit combination of each term (weight of input block b), per level, in build_plan's
+// term order; the host checks its plan against this table.  Compile-time weights let the
+// digit jobs add only the blocks a term uses.
+__host__ __device__ constexpr int in_coef_tab(int L, int j, int b) {
+    constexpr int t0[1][4] = {{1, 0, 0, 0}};
+    constexpr int t1[3][4] = {{1, 0, 0, 0}, {-1, 1, 0, 0}, {1, 1, 0, 0}};
+    constexpr int t2[9][4] = {{1, 1, 0, 0},   {0, 1, 0, 0},  {1, 0, 0, 0},
+                              {-1, -1, 1, 1}, {0, -1, 0, 1}, {-1, 0, 1, 0},
+                              {1, 1, 1, 1},   {0, 1, 0, 1},  {1, 0, 1, 0}};
+    return L == 0 ? t0[j][b] : (L == 1 ? t1[j][b] : t2[j][b]);
+}
+
+// Two small integers (|x| < 2^22) as packed bf16: x + 1.5 * 2^23 is exact in fp32, so its
+// bit pattern is 0x4B400000 + x and subtracting 1.5 * 2^23 back gives float(x); the high
+// halves of the two floats are the bf16 values (exact for |x| <= 256).
+__device__ __forceinline__ uint32_t pack_bf16x2(int x0, int x1) {
+    const float f0 = __int_as_float(0x4B400000 + x0) - 12582912.0f;
+    const float f1 = __int_as_float(0x4B400000 + x1) - 12582912.0f;
+    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
 struct KTerm {
     int n_in, in_blk[4], in_sgn[4];      // digit combination: sum sgn * block (size s)
     int n_out, out_blk[4], out_sgn[4];   // output blocks (size s) receiving sgn * P
@@ -1002,15 +1023,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                             for (int e = 0; e < 8; e++) x[e] = 0;
 #pragma unroll
                             for (int b = 0; b < NBLK; b++) {
-                                const int cf = terms[j].in_coef[b];
+                                const int cf = in_coef_tab(L, j, b);
 #pragma unroll
-                                for (int e = 0; e < 8; e++) x[e] += cf * dg[b][e];
+                                for (int e = 0; e < 8; e++) {
+                                    if (cf == 1) x[e] += dg[b][e];
+                                    else if (cf == -1) x[e] -= dg[b][e];
+                                }
                             }
 #pragma unroll
                             for (int e = 0; e < 8; e++) asum[j] += abs(x[e]);
                             uint32_t w[4];
 #pragma unroll
-                            for (int e = 0; e < 8; e += 2) w[e / 2] = bf16_bits(x[e]) | (bf16_bits(x[e + 1]) << 16);
+                            for (int e = 0; e < 8; e += 2) w[e / 2] = pack_bf16x2(x[e], x[e + 1]);
                             const size_t blk = (((size_t)gt * NT + j) * 2 * l + r) * kstages + kc;
                             a.digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
                                 make_uint4(w[0], w[1], w[2], w[3]);
@@ -1126,6 +1150,9 @@ static void build_plan(int N, int L, std::vector<KTerm> &terms) {
         for (int b = 0; b < 4; b++) t.in_coef[b] = 0;
         for (int m = 0; m < t.n_in; m++) t.in_coef[t.in_blk[m]] += t.in_sgn[m];
     }
+    for (size_t j = 0; j < terms.size(); j++)  // the kernels' compile-time table must agree
+        for (int b = 0; b < 4; b++)
+            if (terms[j].in_coef[b] != (b < (1 << L) ? in_coef_tab(L, (int)j, b) : 0)) terms.clear();
     // phases: greedy, terms of one phase write disjoint output blocks
     std::vector<std::vector<int>> used;  // per phase, blocks written
     for (KTerm &t : terms) {
@@ -1220,6 +1247,8 @@ static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     if (ctx->capturing)
         return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core windows: cannot rebuild while recording");
     build_plan(p.N, level, V.terms);
+    if (V.terms.empty())
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba plan differs from the kernels' table");
     const int T = (int)V.terms.size();
     const int s = p.N >> level;
     if (!V.d_terms && cudaMalloc(&V.d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
