@@ -338,8 +338,8 @@ void tfhe_plan_destroy(tfhe_plan *plan);
 /* Plan autotuner (the level scheduler's choice of form and Karatsuba level per batch
  * width).  Times every form and tensor-core Karatsuba level on batches of 64, 128, ...
  * and max_gates gates of pseudo-random ciphertexts (one warm-up and two timed runs on
- * `stream`; a candidate more than twice as slow as the best stops being timed at larger
- * widths) and keeps the fastest per width; plans built afterwards with form = -1 use the
+ * `stream`; the NTT form stops being timed at larger widths once it is twice as slow as
+ * the best) and keeps the fastest per width; plans built afterwards with form = -1 use the
  * entry at the nearest width (log scale).  Without it plans use a fixed rule measured on
  * B300 at N = 1024.  Allocates scratch for 3 * max_gates ciphertexts; keeps the key
  * windows of the levels the table uses.  Blocks until done (seconds).  Results of every

@@ -22,6 +22,7 @@ struct TcWorkspace;  // tensor-core form buffers (tc.cu)
 struct tfhe_ctx {
     tfhe_params p{};
     int device = 0;
+    int sms = 0;    // multiprocessors of the device (queried on first use)
     int logN = 0;
     int n_pad = 0;  // KSK row length in words, (n + 1) rounded up to a multiple of 4
     std::string err;

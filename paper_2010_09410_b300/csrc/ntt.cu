@@ -143,7 +143,7 @@ __device__ __forceinline__ void extprod_ntt(const uint32_t *d, const uint64_t *_
 }
 
 // One block per gate: BlindRotate of the test vector by (a~, b~) = bar[g].
-__global__ void __launch_bounds__(256) k_blind_rotate_ntt(
+__global__ void __launch_bounds__(1024) k_blind_rotate_ntt(
     int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
     uint32_t *__restrict__ acc_out, const uint64_t *__restrict__ bsk,
     const uint64_t *__restrict__ psi_f, const uint64_t *__restrict__ psi_i) {
@@ -261,9 +261,16 @@ int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
+    // threads per gate: measured on B300 at N = 1024 (per-level ms for 64 / 148 / 296 /
+    // 512 / 2048 gates): 256 threads 30.2 / 29.4 / 38.9 / 71.5 / 230; 512 threads 24.0 /
+    // 23.2 / 36.8 / 67.0 / 218; 1024 threads 22.1 / 21.5 / 38.1 / 71.1 / 237
+    if (!ctx->sms)
+        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount,
+                                                  ctx->device));
+    const int threads = G <= ctx->sms ? 1024 : 512;
     StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_NTT, st);
-    k_blind_rotate_ntt<<<G, 256, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar, acc,
-                                             ctx->bsk_ntt, ctx->psi_fwd, ctx->psi_inv);
+    k_blind_rotate_ntt<<<G, threads, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar, acc,
+                                                 ctx->bsk_ntt, ctx->psi_fwd, ctx->psi_inv);
     tm.stop();
     return tfhe_check_launch(ctx, "blind_rotate_ntt");
 }

@@ -373,10 +373,12 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream) {
             ms[ci] = t;
             if (t < best.ms) best = {w, cand[ci].first, cand[ci].second, t};
         }
-        // a candidate more than twice as slow as the best stops being timed at larger
-        // widths (each form's time grows with the width at least as fast beyond this)
+        // the NTT form stops being timed once it is twice as slow as the best: its time
+        // grows linearly with the width (one block per gate), while the tensor-core
+        // form's per-gate cost falls as its tiles fill, so only the NTT form's standing
+        // can only get worse at larger widths
         for (size_t ci = 0; ci < cand.size(); ci++)
-            if (ms[ci] > 2 * best.ms) alive[ci] = false;
+            if (cand[ci].first == TFHE_FORM_NTT && ms[ci] > 2 * best.ms) alive[ci] = false;
         table.push_back(best);
     }
     if (rc == TFHE_OK) rc = tfhe_ctx_sync(ctx, stream);
