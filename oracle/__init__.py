@@ -6,7 +6,8 @@ Only the tests, the smoke check and the CPU-baseline leg of the benchmark import
 this package; the product library never does, and this package imports nothing
 from the product library.
 
-Every function is written against the definitions; all arithmetic is mod 2^32.
+Every function is written against the definitions; all arithmetic is mod 2^32, except
+the level-2 ring of circuit bootstrapping (reading R16), which is mod 2^64.
 Parity of absolute ciphertext words with the CUDA path rests on the readings R1-R8
 listed at the top of `tfhe_oracle.c`; those readings are pinned by the properties
 the scheme fixes (decryption, truth tables, rounding bounds, algebraic
@@ -33,6 +34,11 @@ class _P(ctypes.Structure):
                 ("ks_basebit", ctypes.c_int32)]
 
 
+class _Q(ctypes.Structure):
+    _fields_ = [("N2", ctypes.c_int32), ("l2", ctypes.c_int32), ("Bg2bit", ctypes.c_int32),
+                ("pks_t", ctypes.c_int32), ("pks_basebit", ctypes.c_int32)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, no target-specific flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -46,6 +52,7 @@ def _lib():
     lib = ctypes.CDLL(_LIB)
     vp, i32, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
     P = ctypes.POINTER(_P)
+    Q = ctypes.POINTER(_Q)
     sig = {
         "orc_poly_mul": (None, [i32, vp, vp, vp]),
         "orc_rotate": (None, [i32, i32, vp, vp]),
@@ -73,6 +80,19 @@ def _lib():
         "orc_ram_cycle": (None, [P, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
         "orc_rom_read": (None, [P, vp, vp, vp, i32, i32, vp, vp]),
         "orc_ram_write": (None, [P, vp, i32, vp, vp]),
+        "orc64_poly_mul": (None, [i32, vp, vp, vp]),
+        "orc64_rotate": (None, [i32, i32, vp, vp]),
+        "orc64_tlwe_phase": (ctypes.c_uint64, [i32, vp, vp]),
+        "orc64_trlwe_phase": (None, [i32, vp, vp, vp]),
+        "orc64_decompose": (None, [i32, i32, ctypes.c_uint64, vp]),
+        "orc64_external_product": (None, [i32, i32, i32, vp, vp, vp]),
+        "orc64_cmux": (None, [i32, i32, i32, vp, vp, vp, vp]),
+        "orc64_blind_rotate": (None, [P, Q, vp, vp, ctypes.c_uint64, vp]),
+        "orc64_sample_extract": (None, [i32, vp, vp]),
+        "orc_cb_tlwe2": (None, [P, Q, vp, vp, i32, vp]),
+        "orc_pks_digits": (None, [i32, i32, ctypes.c_uint64, vp]),
+        "orc_private_keyswitch": (None, [P, Q, vp, i32, vp, vp]),
+        "orc_circuit_bootstrap": (None, [P, Q, vp, vp, vp, vp]),
         "orc_extprod_count": (ctypes.c_uint64, []),
         "orc_extprod_count_reset": (None, []),
     }
@@ -86,6 +106,10 @@ def _lib():
 def _p(params):
     n, N, l, Bgbit, t, bb = params.abi() if hasattr(params, "abi") else params
     return ctypes.byref(_P(n, N, l, Bgbit, t, bb))
+
+
+def _q(cbp):
+    return ctypes.byref(_Q(*cbp.abi()))
 
 
 def _c(a, dtype):
@@ -363,3 +387,123 @@ def rom_read(params, ksk, addr_trgsw, table, v, w):
     _lib().orc_rom_read(_p(params), pk, pa, pt, v, w, ctypes.c_void_p(trlwe.ctypes.data),
                         ctypes.c_void_p(bits.ctypes.data))
     return trlwe, bits
+
+
+# ---- circuit bootstrapping (reading R16): Torus64 primitives and the CB steps ----------
+
+def _out(shape, dtype):
+    o = np.zeros(shape, dtype)
+    return o, ctypes.c_void_p(o.ctypes.data)
+
+
+def poly_mul64(a_int, b_torus):
+    a, pa = _c(a_int, np.int32)
+    b, pb = _c(b_torus, np.uint64)
+    o, po = _out(a.size, np.uint64)
+    _lib().orc64_poly_mul(a.size, pa, pb, po)
+    return o
+
+
+def rotate64(p, k):
+    a, pa = _c(p, np.uint64)
+    o, po = _out(a.size, np.uint64)
+    _lib().orc64_rotate(a.size, int(k), pa, po)
+    return o
+
+
+def decompose64(l, Bgbit, t):
+    o, po = _out(l, np.int32)
+    _lib().orc64_decompose(l, Bgbit, int(t) & (2**64 - 1), po)
+    return o
+
+
+def tlwe2_phase(s2, c):
+    s, ps = _c(s2, np.uint32)
+    c, pc = _c(c, np.uint64)
+    return int(_lib().orc64_tlwe_phase(s.size, ps, pc))
+
+
+def trlwe2_phase(s2, c):
+    s, ps = _c(s2, np.uint32)
+    c, pc = _c(c, np.uint64)
+    o, po = _out(s.size, np.uint64)
+    _lib().orc64_trlwe_phase(s.size, ps, pc, po)
+    return o
+
+
+def external_product64(l, Bgbit, C, d):
+    C, pC = _c(C, np.uint64)
+    d, pd = _c(d, np.uint64)
+    o, po = _out(d.shape, np.uint64)
+    _lib().orc64_external_product(d.shape[-1], l, Bgbit, pC, pd, po)
+    return o
+
+
+def cmux64(l, Bgbit, C, d1, d0):
+    C, pC = _c(C, np.uint64)
+    d1, p1 = _c(d1, np.uint64)
+    d0, p0 = _c(d0, np.uint64)
+    o, po = _out(d0.shape, np.uint64)
+    _lib().orc64_cmux(d0.shape[-1], l, Bgbit, pC, p1, p0, po)
+    return o
+
+
+def blind_rotate64(params, cbp, bsk2, bar, mu):
+    b, pb = _c(bsk2, np.uint64)
+    bar, pbar = _c(bar, np.uint32)
+    o, po = _out((2, cbp.N2), np.uint64)
+    _lib().orc64_blind_rotate(_p(params), _q(cbp), pb, pbar, int(mu) & (2**64 - 1), po)
+    return o
+
+
+def sample_extract64(trlwe):
+    c, pc = _c(trlwe, np.uint64)
+    N = c.shape[-1]
+    o, po = _out(N + 1, np.uint64)
+    _lib().orc64_sample_extract(N, pc, po)
+    return o
+
+
+def cb_tlwe2(params, cbp, bsk2, tlwe0, u):
+    """Step 1 of circuit bootstrapping for level u (1..l): lvl2 TLWE u64[N2+1] of m/Bg^u."""
+    b, pb = _c(bsk2, np.uint64)
+    c, pc = _c(tlwe0, np.uint32)
+    o, po = _out(cbp.N2 + 1, np.uint64)
+    _lib().orc_cb_tlwe2(_p(params), _q(cbp), pb, pc, int(u), po)
+    return o
+
+
+def pks_digits(t, basebit, a):
+    o, po = _out(t, np.uint32)
+    _lib().orc_pks_digits(t, basebit, int(a) & (2**64 - 1), po)
+    return o
+
+
+def private_keyswitch(params, cbp, pksk, z, tlwe2):
+    """Private functional key switch of a lvl2 TLWE to a lvl1 TRLWE u32[2][N]
+    (z = 0: f(x) = -s1[X] x, z = 1: f(x) = x)."""
+    k, pk = _c(pksk, np.uint32)
+    c, pc = _c(tlwe2, np.uint64)
+    o, po = _out((2, params.N), np.uint32)
+    _lib().orc_private_keyswitch(_p(params), _q(cbp), pk, int(z), pc, po)
+    return o
+
+
+def circuit_bootstrap(params, cbp, bsk2, pksk, tlwe0, threads: int | None = None):
+    """Circuit bootstrapping of one lvl0 TLWE (u32[n+1]) or a batch (u32[R][n+1]) to
+    TRGSW lvl1 u32[(R)][2l][2][N]; one input per thread."""
+    b, pb = _c(bsk2, np.uint64)
+    k, pk = _c(pksk, np.uint32)
+    c = np.ascontiguousarray(tlwe0, np.uint32)
+    flat = c.reshape(-1, params.n + 1)
+    out = np.zeros((flat.shape[0], 2 * params.l, 2, params.N), np.uint32)
+    lib, pp, pq = _lib(), _p(params), _q(cbp)
+
+    def one(r):
+        lib.orc_circuit_bootstrap(pp, pq, pb, pk, ctypes.c_void_p(flat[r].ctypes.data),
+                                  ctypes.c_void_p(out[r].ctypes.data))
+
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max(1, min(threads, flat.shape[0]))) as ex:
+        list(ex.map(one, range(flat.shape[0])))
+    return out if c.ndim > 1 else out[0]

@@ -50,6 +50,10 @@
  *      data) (R13), each block's write bar takes it (R8), and every cell is refreshed by
  *      SE, IKS, ModSwitch and BlindRotate (R4) back to a TRLWE whose coefficient 0
  *      carries the bit.
+ *   R16 Circuit Bootstrapping (Section 2.1.2 "Circuit Bootstrapping"; steps from the TFHE
+ *      construction the paper cites): l BlindRotates over a lvl2 ring on the 64-bit
+ *      torus with test vectors 1/(2 Bg^u), then private functional key switching to the
+ *      2l TRGSW rows with f(x) = -s1[X] x (rows 0..l-1) and f(x) = x (rows l..2l-1).
  *   R13 HomMUX (Section 2.1.2 "Homomorphic Gates", "HomMUX without SE and IKS"; the
  *      paper names the gate but not its steps): MUX(c, a, b) = c ? a : b as
  *      u = BlindRotate(AND(c, a)) + BlindRotate(ANDNY(c, b)) + (0, mu X^0), the two
@@ -495,4 +499,194 @@ void orc_rom_read(const orc_params *p, const uint32_t *ksk, const uint32_t *addr
     free(acc);
     free(rot);
     free(ext);
+}
+
+/* ==== Circuit Bootstrapping (Section 2.1.2 "Circuit Bootstrapping"; reading R16) ======
+ *
+ * TLWE lvl0 -> TRGSW lvl1.  The paper names the operation and its source (the TFHE
+ * construction) and notes (Section 6.2(a)) that it needs a modulus above 64 bits in an
+ * NTT; its steps, in the TFHE construction's order:
+ *   1. for u = 1..l: BlindRotate the ModSwitched input (to Z_{2 N2}) over the lvl2 ring
+ *      on the 64-bit torus with the test vector mu_u sum_j X^j, mu_u = 1/(2 Bg^u);
+ *      SampleExtract; add mu_u to b.  The result is a lvl2 TLWE of m / Bg^u (m the input
+ *      bit: phase >= 0 is 1, reading R1).
+ *   2. row u-1 of the TRGSW = private functional key switch of that TLWE with
+ *      f_0(x) = -s1[X] x (a TRLWE of phase -m s1 / Bg^u, i.e. m / Bg^u on the a column);
+ *      row l+u-1 = the same with f_1(x) = x (m / Bg^u on the b column).
+ * Torus64 functions mirror the Torus32 ones above with uint64 arithmetic. */
+
+typedef struct { int32_t N2, l2, Bg2bit, pks_t, pks_basebit; } orc_cb_params;
+
+/* out = a * b in Z[X]/(X^N+1) over Torus64 (schoolbook). */
+void orc64_poly_mul(int N, const int32_t *a, const uint64_t *b, uint64_t *out) {
+    uint64_t *acc = (uint64_t *)calloc((size_t)N, sizeof(uint64_t));
+    for (int i = 0; i < N; i++) {
+        const uint64_t ai = (uint64_t)(int64_t)a[i];
+        for (int j = 0; j < N - i; j++) acc[i + j] += ai * b[j];
+        for (int j = N - i; j < N; j++) acc[i + j - N] -= ai * b[j];
+    }
+    memcpy(out, acc, sizeof(uint64_t) * (size_t)N);
+    free(acc);
+}
+
+/* out = X^k * p over Torus64, k in [0, 2N). */
+void orc64_rotate(int N, int k, const uint64_t *p, uint64_t *out) {
+    int neg = 0;
+    k %= 2 * N;
+    if (k < 0) k += 2 * N;
+    if (k >= N) { k -= N; neg = 1; }
+    for (int j = 0; j < N; j++) {
+        uint64_t v = (j >= k) ? p[j - k] : (uint64_t)(0u - p[j - k + N]);
+        out[j] = neg ? (uint64_t)(0u - v) : v;
+    }
+}
+
+/* phase = b - <a, s> over Torus64 (lvl2 TLWE, s = s2). */
+uint64_t orc64_tlwe_phase(int n, const uint32_t *s, const uint64_t *c) {
+    uint64_t as = 0;
+    for (int i = 0; i < n; i++) as += c[i] * (uint64_t)s[i];
+    return c[n] - as;
+}
+
+/* phase[X] = b[X] - a[X] s[X] over Torus64. */
+void orc64_trlwe_phase(int N, const uint32_t *s, const uint64_t *c, uint64_t *phase) {
+    int32_t *si = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    uint64_t *as = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    for (int i = 0; i < N; i++) si[i] = (int32_t)s[i];
+    orc64_poly_mul(N, si, c, as);
+    for (int i = 0; i < N; i++) phase[i] = c[N + i] - as[i];
+    free(si);
+    free(as);
+}
+
+/* Reading R2 on Torus64: digits d_1..d_l in [-Bg/2, Bg/2), sum_j d_j 2^{64 - j Bgbit} =
+ * t rounded to the nearest multiple of 2^{64 - l Bgbit} (ties upward). */
+void orc64_decompose(int l, int Bgbit, uint64_t t, int32_t *digits) {
+    const uint64_t Bg = (uint64_t)1 << Bgbit, half = Bg / 2;
+    uint64_t offset = (uint64_t)1 << (64 - l * Bgbit - 1);
+    for (int j = 1; j <= l; j++) offset += half << (64 - j * Bgbit);
+    const uint64_t u = t + offset;
+    for (int j = 1; j <= l; j++)
+        digits[j - 1] = (int32_t)((u >> (64 - j * Bgbit)) & (Bg - 1)) - (int32_t)half;
+}
+
+/* out = C (.) d over Torus64: C u64[2l][2][N], d u64[2][N]. */
+void orc64_external_product(int N, int l, int Bgbit, const uint64_t *C, const uint64_t *d,
+                            uint64_t *out) {
+    int32_t *dig = (int32_t *)malloc(sizeof(int32_t) * (size_t)2 * l * N);
+    uint64_t *prod = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    uint64_t *res = (uint64_t *)calloc((size_t)2 * N, sizeof(uint64_t));
+    int32_t tmp[64];
+    for (int c = 0; c < 2; c++)
+        for (int k = 0; k < N; k++) {
+            orc64_decompose(l, Bgbit, d[c * N + k], tmp);
+            for (int j = 0; j < l; j++) dig[(size_t)(c * l + j) * N + k] = tmp[j];
+        }
+    for (int row = 0; row < 2 * l; row++)
+        for (int col = 0; col < 2; col++) {
+            orc64_poly_mul(N, dig + (size_t)row * N, C + ((size_t)row * 2 + col) * N, prod);
+            for (int k = 0; k < N; k++) res[col * N + k] += prod[k];
+        }
+    memcpy(out, res, sizeof(uint64_t) * (size_t)2 * N);
+    free(dig);
+    free(prod);
+    free(res);
+    orc_extprod_calls++;
+}
+
+/* CMUX over Torus64: out = d0 + C (.) (d1 - d0). */
+void orc64_cmux(int N, int l, int Bgbit, const uint64_t *C, const uint64_t *d1,
+                const uint64_t *d0, uint64_t *out) {
+    uint64_t *diff = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)2 * N);
+    uint64_t *ep = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)2 * N);
+    for (int k = 0; k < 2 * N; k++) diff[k] = d1[k] - d0[k];
+    orc64_external_product(N, l, Bgbit, C, diff, ep);
+    for (int k = 0; k < 2 * N; k++) out[k] = d0[k] + ep[k];
+    free(diff);
+    free(ep);
+}
+
+/* Reading R4 on the lvl2 ring: bar = (a~, b~) in Z_{2 N2} (length n + 1); bsk2
+ * u64[n][2 l2][2][N2]; acc u64[2][N2] = BlindRotate of the test vector mu sum_j X^j. */
+void orc64_blind_rotate(const orc_params *p, const orc_cb_params *q, const uint64_t *bsk2,
+                        const uint32_t *bar, uint64_t mu, uint64_t *acc) {
+    const int N = q->N2, n = p->n;
+    const size_t per = (size_t)2 * q->l2 * 2 * N;
+    uint64_t *tv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    uint64_t *rot = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)2 * N);
+    for (int k = 0; k < N; k++) tv[k] = mu;
+    memset(acc, 0, sizeof(uint64_t) * (size_t)N);
+    orc64_rotate(N, (int)((2 * N - bar[n] % (2 * N)) % (2 * N)), tv, acc + N);
+    for (int i = 0; i < n; i++) {
+        orc64_rotate(N, (int)bar[i], acc, rot);
+        orc64_rotate(N, (int)bar[i], acc + N, rot + N);
+        orc64_cmux(N, q->l2, q->Bg2bit, bsk2 + (size_t)i * per, rot, acc, acc);
+    }
+    free(tv);
+    free(rot);
+}
+
+/* TRLWE -> TLWE (coefficient 0) over Torus64. */
+void orc64_sample_extract(int N, const uint64_t *c, uint64_t *out) {
+    out[0] = c[0];
+    for (int j = 1; j < N; j++) out[j] = 0u - c[N - j];
+    out[N] = c[N];
+}
+
+/* Step 1 for one u: lvl0 TLWE in u32[n+1] -> lvl2 TLWE out u64[N2+1] of m / Bg^u. */
+void orc_cb_tlwe2(const orc_params *p, const orc_cb_params *q, const uint64_t *bsk2,
+                  const uint32_t *in, int u, uint64_t *out) {
+    const int n = p->n, N2 = q->N2;
+    uint32_t *bar = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint64_t *acc = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)2 * N2);
+    const uint64_t mu = (uint64_t)1 << (64 - u * p->Bgbit - 1); /* 1 / (2 Bg^u) */
+    for (int k = 0; k <= n; k++) bar[k] = orc_modswitch(N2, in[k]);
+    orc64_blind_rotate(p, q, bsk2, bar, mu, acc);
+    orc64_sample_extract(N2, acc, out);
+    out[N2] += mu;
+    free(bar);
+    free(acc);
+}
+
+/* Unsigned base-2^bb digits of a Torus64 value rounded to t digits (reading R5). */
+void orc_pks_digits(int t, int bb, uint64_t a, uint32_t *digits) {
+    const uint64_t prec = (uint64_t)1 << (64 - (1 + bb * t));
+    const uint64_t abar = a + prec;
+    for (int j = 0; j < t; j++)
+        digits[j] = (uint32_t)((abar >> (64 - (j + 1) * bb)) & (((uint64_t)1 << bb) - 1));
+}
+
+/* Private functional key switch (reading R16): lvl2 TLWE in u64[N2+1] -> TRLWE lvl1
+ * out u32[2][N] with phase f_z(phase(in)).  pksk u32[2][N2+1][t][base][2][N].  With
+ * a_{N2} = b and k_{N2} = -1: out = -sum_{i <= N2} sum_j PKSK[z][i][j][digit_j(a_i)]. */
+void orc_private_keyswitch(const orc_params *p, const orc_cb_params *q, const uint32_t *pksk,
+                           int z, const uint64_t *in, uint32_t *out) {
+    const int N = p->N, N2 = q->N2, t = q->pks_t, bb = q->pks_basebit, base = 1 << bb;
+    const size_t tr = (size_t)2 * N;
+    uint32_t dig[64];
+    memset(out, 0, sizeof(uint32_t) * tr);
+    for (int i = 0; i <= N2; i++) {
+        orc_pks_digits(t, bb, in[i], dig);
+        for (int j = 0; j < t; j++) {
+            const uint32_t v = dig[j];
+            if (v == 0) continue;
+            const uint32_t *row =
+                pksk + ((((size_t)z * (N2 + 1) + i) * t + j) * base + v) * tr;
+            for (size_t k = 0; k < tr; k++) out[k] -= row[k];
+        }
+    }
+}
+
+/* Circuit bootstrapping of one lvl0 TLWE: out u32[2l][2][N], a TRGSW of the input bit. */
+void orc_circuit_bootstrap(const orc_params *p, const orc_cb_params *q, const uint64_t *bsk2,
+                           const uint32_t *pksk, const uint32_t *in, uint32_t *out) {
+    const int l = p->l;
+    const size_t tr = (size_t)2 * p->N;
+    uint64_t *t2 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(q->N2 + 1));
+    for (int u = 1; u <= l; u++) {
+        orc_cb_tlwe2(p, q, bsk2, in, u, t2);
+        orc_private_keyswitch(p, q, pksk, 0, t2, out + (size_t)(u - 1) * tr);
+        orc_private_keyswitch(p, q, pksk, 1, t2, out + (size_t)(l + u - 1) * tr);
+    }
+    free(t2);
 }

@@ -58,6 +58,37 @@ SEED_FLAT = 0x20100941 + 2
 SEED_DAG = 0x20100941 + 3
 SEED_CMUX = 0x20100941 + 4
 SEED_MIXED = 0x20100941 + 5
+SEED_CB = 0x20100941 + 6
+
+
+@dataclasses.dataclass(frozen=True)
+class CBParams:
+    """Circuit-bootstrapping parameters: the level-2 ring over the 64-bit torus and the
+    private functional key switch back to lvl1 (the paper names circuit bootstrapping,
+    Section 2.1.2, but prints no parameters)."""
+    N2: int           # lvl2 ring degree
+    l2: int           # lvl2 gadget levels
+    Bg2bit: int       # log2 of the lvl2 gadget base
+    pks_t: int        # private key-switching levels
+    pks_basebit: int  # log2 of the private key-switching base
+    sigma2: float     # lvl2 key noise stdev (Torus64 units)
+    sigma_pks: float  # private key-switching key noise stdev (Torus32 units)
+
+    @property
+    def pks_base(self) -> int:
+        return 1 << self.pks_basebit
+
+    def abi(self):
+        return (self.N2, self.l2, self.Bg2bit, self.pks_t, self.pks_basebit)
+
+
+# lvl2 for the toy set (N2=512) and for the TFHE-like set (N2=2048); both l2=4, Bg2bit=9,
+# private key switching t=10, basebit=3 (the sizes that reproduce the paper's "Size of Keys
+# and Ciphertexts" table), with the lvl1 noise of the set.
+CB_TOY = CBParams(N2=512, l2=4, Bg2bit=9, pks_t=10, pks_basebit=3, sigma2=2.0**-44,
+                  sigma_pks=2.0**-30)
+CB_STD = CBParams(N2=2048, l2=4, Bg2bit=9, pks_t=10, pks_basebit=3, sigma2=2.0**-44,
+                  sigma_pks=2.0**-25)
 
 GATE_NAMES = ["NAND", "AND", "OR", "NOR", "XOR", "XNOR", "ANDNY", "ANDYN", "ORNY", "ORYN"]
 
@@ -81,11 +112,17 @@ class _CParams(ctypes.Structure):
                 ("sigma1", ctypes.c_double)]
 
 
+class _CCbParams(ctypes.Structure):
+    _fields_ = [("N2", ctypes.c_int32), ("l2", ctypes.c_int32), ("Bg2bit", ctypes.c_int32),
+                ("pks_t", ctypes.c_int32), ("pks_basebit", ctypes.c_int32),
+                ("sigma2", ctypes.c_double), ("sigma_pks", ctypes.c_double)]
+
+
 def build(force: bool = False) -> str:
     """Compile the generator into an in-tree shared library."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-std=c11", "-o", _LIB, _SRC,
-                               "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-std=c11", "-fopenmp", "-o",
+                               _LIB, _SRC, "-lm"])
     return _LIB
 
 
@@ -101,8 +138,13 @@ def _lib():
     for f in (lib.tin_tlwe0_encrypt_bits, lib.tin_trlwe_encrypt_bits, lib.tin_trgsw_encrypt_bits):
         f.argtypes = [P, ctypes.c_uint64, ctypes.c_uint64, u32p, u32p, ctypes.c_int64, u32p]
     lib.tin_random_u64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, u32p]
+    Q = ctypes.POINTER(_CCbParams)
+    lib.tin_keygen2.argtypes = [Q, ctypes.c_uint64, u32p]
+    lib.tin_bsk2.argtypes = [P, Q, ctypes.c_uint64, u32p, u32p, u32p]
+    lib.tin_pksk.argtypes = [P, Q, ctypes.c_uint64, u32p, u32p, u32p]
     for f in (lib.tin_keygen, lib.tin_bsk, lib.tin_ksk, lib.tin_tlwe0_encrypt_bits,
-              lib.tin_trlwe_encrypt_bits, lib.tin_trgsw_encrypt_bits, lib.tin_random_u64):
+              lib.tin_trlwe_encrypt_bits, lib.tin_trgsw_encrypt_bits, lib.tin_random_u64,
+              lib.tin_keygen2, lib.tin_bsk2, lib.tin_pksk):
         f.restype = None
     return lib
 
@@ -114,6 +156,41 @@ def _cp(p: Params):
 def _ptr(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def _cq(q: CBParams):
+    return ctypes.byref(_CCbParams(q.N2, q.l2, q.Bg2bit, q.pks_t, q.pks_basebit, q.sigma2,
+                                   q.sigma_pks))
+
+
+def keygen2(q: CBParams, seed: int) -> np.ndarray:
+    """lvl2 key s2 in B_{N2}[X]."""
+    s2 = np.zeros(q.N2, np.uint32)
+    _lib().tin_keygen2(_cq(q), seed, _ptr(s2))
+    return s2
+
+
+def bsk2_shape(p: Params, q: CBParams):
+    return (p.n, 2 * q.l2, 2, q.N2)
+
+
+def pksk_shape(p: Params, q: CBParams):
+    return (2, q.N2 + 1, q.pks_t, q.pks_base, 2, p.N)
+
+
+def make_bsk2(p: Params, q: CBParams, seed: int, s0, s2) -> np.ndarray:
+    """BSK2 u64[n][2 l2][2][N2]: TRGSW_{s2}(s0[i]) over Torus64."""
+    bsk2 = np.zeros(bsk2_shape(p, q), np.uint64)
+    _lib().tin_bsk2(_cp(p), _cq(q), seed, _ptr(s0), _ptr(s2), _ptr(bsk2))
+    return bsk2
+
+
+def make_pksk(p: Params, q: CBParams, seed: int, s1, s2) -> np.ndarray:
+    """PKSK u32[2][N2+1][t][base][2][N]: private functional key-switching keys for
+    f_0(x) = -s1[X] x and f_1(x) = x."""
+    pksk = np.zeros(pksk_shape(p, q), np.uint32)
+    _lib().tin_pksk(_cp(p), _cq(q), seed, _ptr(s1), _ptr(s2), _ptr(pksk))
+    return pksk
 
 
 def keygen(p: Params, seed: int):
@@ -447,3 +524,34 @@ def packed_rom(p: Params = STD, seed: int = SEED_CMUX, M: int = 128, w: int = 32
     addr_trgsw = encrypt_trgsw_bits(p, seed, 82 + stream, k.s1, abits.reshape(-1)).reshape(
         R, v, 2 * p.l, 2, p.N)
     return PackedRom(k, v, w, words, table, addrs, addr_trgsw)
+
+
+@dataclasses.dataclass
+class CBKeys:
+    s2: np.ndarray    # u32[N2] lvl2 key
+    bsk2: np.ndarray  # u64[n][2 l2][2][N2]
+    pksk: np.ndarray  # u32[2][N2+1][t][base][2][N]
+
+
+@functools.lru_cache(maxsize=2)
+def cb_keys(p: Params, q: CBParams, seed: int) -> CBKeys:
+    k = keys(p, seed)
+    s2 = keygen2(q, seed)
+    return CBKeys(s2, make_bsk2(p, q, seed, k.s0, s2), make_pksk(p, q, seed, k.s1, s2))
+
+
+@dataclasses.dataclass
+class CBBatch:
+    keys: Keys
+    cbk: CBKeys
+    bits: np.ndarray  # u8[R]
+    tlwe: np.ndarray  # u32[R][n+1] lvl0 encryptions of bits
+
+
+def cb_batch(p: Params = TOY, q: CBParams = CB_TOY, seed: int = SEED_CB, R: int = 4,
+             stream: int = 0) -> CBBatch:
+    """R lvl0 TLWE encryptions of uniform random bits to circuit-bootstrap."""
+    k = keys(p, seed)
+    bits = random_bits(seed, 90 + stream, R)
+    return CBBatch(k, cb_keys(p, q, seed), bits, encrypt_tlwe0_bits(p, seed, 90 + stream, k.s0,
+                                                                      bits))

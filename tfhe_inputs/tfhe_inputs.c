@@ -29,6 +29,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef struct {
@@ -223,4 +224,113 @@ void tin_random_u64(uint64_t seed, uint64_t stream, int64_t count, uint64_t *out
     tin_rng r;
     rng_init(&r, seed, TIN_BITS, stream);
     for (int64_t k = 0; k < count; k++) out[k] = rng_next(&r);
+}
+
+/* ==== Circuit-bootstrapping keys (Section 2.1.2 "Circuit Bootstrapping") ================
+ *
+ * Circuit bootstrapping (TLWE lvl0 -> TRGSW lvl1) goes through a level-2 ring over the
+ * 64-bit torus (Torus64: x -> round(x * 2^64) mod 2^64) and back to lvl1 by private
+ * functional key switching.  Its keys:
+ *   s2:    B_{N2}[X], uniform binary (lvl2 TRLWE key)
+ *   BSK2:  u64[n][2 l2][2][N2],  BSK2[i] = TRGSW_{s2}(s0[i]) over Torus64 (rows as for
+ *          the lvl1 TRGSW, 1/Bg2^j = 2^(64 - j Bg2bit) at coefficient 0)
+ *   PKSK:  u32[2][N2 + 1][t][base][2][N],
+ *          PKSK[z][i][j][v] = TRLWE_{s1}(f_z(v * k_i / base^(j+1))), k_i = s2[i] for i < N2
+ *          and k_{N2} = -1, with f_0(x) = -s1[X] * x and f_1(x) = x; v = 0 is the zero
+ *          ciphertext.
+ * Each TRGSW (per i) and each PKSK block (per z, i) draws from its own stream, so the
+ * objects are generated in parallel with identical bytes. */
+
+typedef struct {
+    int32_t N2, l2, Bg2bit, pks_t, pks_basebit;
+    double sigma2, sigma_pks; /* noise stdev: lvl2 keys (Torus64), PKSK (Torus32) */
+} tin_cb_params;
+
+enum { TIN_S2 = 10, TIN_BSK2 = 11, TIN_PKSK = 12 };
+
+static inline uint64_t rng_torus64(tin_rng *r) { return rng_next(r); }
+
+/* Box-Muller normal sample, scaled to Torus64 and rounded. */
+static int64_t rng_noise64(tin_rng *r, double sigma) {
+    if (sigma <= 0.0) return 0;
+    double u1 = ((double)((rng_next(r) >> 11) + 1)) * 0x1.0p-53;
+    double u2 = ((double)(rng_next(r) >> 11)) * 0x1.0p-53;
+    double g = sqrt(-2.0 * log(u1)) * cos(6.283185307179586476925 * u2);
+    return (int64_t)llround(sigma * g * 18446744073709551616.0);
+}
+
+void tin_keygen2(const tin_cb_params *q, uint64_t seed, uint32_t *s2) {
+    tin_rng r;
+    rng_init(&r, seed, TIN_S2, 0);
+    for (int i = 0; i < q->N2; i++) s2[i] = rng_bit(&r);
+}
+
+/* b[X] += a[X] * s[X] mod (X^N + 1) over Torus64, s binary. */
+static void add_mask_times_key64(int N, const uint64_t *a, const uint32_t *s, uint64_t *b) {
+    for (int j = 0; j < N; j++) {
+        if (!s[j]) continue;
+        for (int k = 0; k < j; k++) b[k] -= a[k - j + N];
+        for (int k = j; k < N; k++) b[k] += a[k - j];
+    }
+}
+
+/* BSK2[i] = TRGSW_{s2}(s0[i]) over Torus64, i < n. */
+void tin_bsk2(const tin_params *p, const tin_cb_params *q, uint64_t seed, const uint32_t *s0,
+              const uint32_t *s2, uint64_t *bsk2) {
+    const int N2 = q->N2, l2 = q->l2;
+    const size_t per = (size_t)2 * l2 * 2 * N2;
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < p->n; i++) {
+        tin_rng r;
+        rng_init(&r, seed, TIN_BSK2, (uint64_t)i);
+        uint64_t *C = bsk2 + (size_t)i * per;
+        for (int row = 0; row < 2 * l2; row++) {
+            uint64_t *a = C + (size_t)row * 2 * N2, *b = a + N2;
+            for (int k = 0; k < N2; k++) a[k] = rng_torus64(&r);
+            for (int k = 0; k < N2; k++) b[k] = (uint64_t)rng_noise64(&r, q->sigma2);
+            add_mask_times_key64(N2, a, s2, b);
+            const int j = (row < l2 ? row : row - l2) + 1;
+            const uint64_t g = (uint64_t)1u << (64 - j * q->Bg2bit);
+            if (row < l2) a[0] += (uint64_t)s0[i] * g;
+            else b[0] += (uint64_t)s0[i] * g;
+        }
+    }
+}
+
+/* PKSK[z][i][j][v], layout u32[2][N2+1][t][base][2][N]. */
+void tin_pksk(const tin_params *p, const tin_cb_params *q, uint64_t seed, const uint32_t *s1,
+              const uint32_t *s2, uint32_t *pksk) {
+    const int N = p->N, N2 = q->N2, t = q->pks_t, bb = q->pks_basebit, base = 1 << bb;
+    const size_t row_words = (size_t)2 * N;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int z = 0; z < 2; z++) {
+        for (int i = 0; i <= N2; i++) {
+            tin_rng r;
+            rng_init(&r, seed, TIN_PKSK, ((uint64_t)z << 32) ^ (uint64_t)i);
+            uint32_t *msg = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)N);
+            const uint32_t key = i < N2 ? s2[i] : 0xFFFFFFFFu; /* k_{N2} = -1 */
+            for (int j = 0; j < t; j++) {
+                for (int v = 0; v < base; v++) {
+                    uint32_t *c =
+                        pksk + ((((size_t)z * (N2 + 1) + i) * t + j) * base + v) * row_words;
+                    if (v == 0) {
+                        memset(c, 0, sizeof(uint32_t) * row_words);
+                        continue;
+                    }
+                    const uint32_t x = (uint32_t)v * key * ((uint32_t)1u << (32 - (j + 1) * bb));
+                    if (z == 0)
+                        for (int k = 0; k < N; k++) msg[k] = (uint32_t)(0u - x * s1[k]);
+                    else {
+                        memset(msg, 0, sizeof(uint32_t) * (size_t)N);
+                        msg[0] = x;
+                    }
+                    uint32_t *a = c, *b = c + N;
+                    for (int k = 0; k < N; k++) a[k] = rng_torus(&r);
+                    for (int k = 0; k < N; k++) b[k] = msg[k] + (uint32_t)rng_noise(&r, q->sigma_pks);
+                    add_mask_times_key(N, a, s1, b);
+                }
+            }
+            free(msg);
+        }
+    }
 }
