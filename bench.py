@@ -42,13 +42,15 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
-    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle", "romp"],
+    ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle", "romp", "cb"],
                     help="level: the headline flat level (default); dag: 20,000-gate 60-level "
                          "DAG through the level scheduler; mixed: 16 uneven circuits "
                          "interleaved; rom: 64 CMUX-tree reads of a 512-row table + one "
                          "256-cell RAM write; mux: 2048 HomMUXes (4096 bootstraps); ramcycle: "
                          "one RAM cycle of 256 words x 16 bits (4096 refresh bootstraps); romp: "
-                         "64 reads of the packed 512-byte ROM (128 words x 32 bits)")
+                         "64 reads of the packed 512-byte ROM (128 words x 32 bits); cb: 576 "
+                         "circuit bootstraps (64 x 9 TLWE address bits) feeding 64 CMUX-tree "
+                         "reads")
     return ap.parse_args()
 
 
@@ -416,7 +418,7 @@ def run_other(args):
     tbuild.build()
     p = ti.STD
     seed = {"rom": ti.SEED_CMUX, "ramcycle": ti.SEED_CMUX, "romp": ti.SEED_CMUX,
-            "mux": ti.SEED_FLAT}.get(args.workload, ti.SEED_DAG)
+            "mux": ti.SEED_FLAT, "cb": ti.SEED_CB}.get(args.workload, ti.SEED_DAG)
     k = ti.keys(p, seed)
     ctx = tb.Context(p, local)
     ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
@@ -480,6 +482,45 @@ def run_other(args):
             extra["circuit_done_ms"] = [round(start.elapsed_time(ev[L]), 2)
                                         for L in plan.circuit_last_level]
             extra["circuit_gates"] = [c.num_gates for c in circs]
+    elif args.workload == "cb":
+        R, v = 64, 9
+        q = ti.CB_STD
+        cbk = ti.cb_keys(p, q, seed)
+        ctx.set_cb_keys(q, torch.from_numpy(cbk.bsk2.view(np.int64)).cuda(), dev(cbk.pksk))
+        ctx.sync()
+        rom = ti.cmux_rom(p, seed, v=v, R=R)
+        abits = ((rom.addrs[:, None] >> np.arange(v)[None, :]) & 1).astype(np.uint8).reshape(-1)
+        tl = dev(ti.encrypt_tlwe0_bits(p, seed, 97, k.s0, abits))
+        table = dev(rom.table)
+        addr = torch.zeros((R * v, 2 * p.l, 2, p.N), dtype=torch.int32, device="cuda")
+        rout = torch.zeros((R, 2, p.N), dtype=torch.int32, device="cuda")
+
+        def step():
+            ctx.circuit_bootstrap(tl, addr)
+            ctx.cmux_tree_read(addr, table, v, rout)
+        units, unit = R * v, "circuit bootstraps/s"
+        metric = ("circuit bootstraps/s (lvl0 TLWE -> lvl1 TRGSW over a Torus64 lvl2 ring), "
+                  "feeding 64 CMUX-tree reads")
+        workload = ("64 reads x 9 TLWE address bits: 576 circuit bootstraps (N2=2048 l2=4 "
+                    "Bg2bit=9, private KS t=10 basebit=3) + 64 reads of a 512-row table, N=1024")
+        step()
+        ctx.sync()
+        ctx.enable_timing(True)
+        step()
+        st = ctx.stage_times()
+        ctx.enable_timing(False)
+        extra["stage_ms_per_step"] = {kname: round(st[kname][0], 3)
+                                      for kname in ("cb_blind_rotate", "cb_keyswitch", "cmux")}
+        got = rout.cpu().numpy().view(np.uint32)
+        s1 = k.s1.astype(np.int64)
+        N = p.N
+        dec = np.zeros((R, 32), np.uint8)
+        for r in range(R):
+            a_, b_ = got[r, 0].astype(np.int64), got[r, 1].astype(np.int64)
+            for j in range(32):
+                acc = int((a_[:j + 1] * s1[j::-1]).sum() - (a_[j + 1:] * s1[N - 1:j:-1]).sum())
+                dec[r, j] = 1 if ((int(b_[j]) - acc) & 0xFFFFFFFF) < (1 << 31) else 0
+        extra["decrypt_ok"] = bool(np.array_equal(dec, rom.table_bits[rom.addrs, :32]))
     elif args.workload == "romp":
         R = 64
         prom = ti.packed_rom(p, seed, M=128, w=32, R=R)

@@ -5,8 +5,8 @@
  *
  * Scope: the server-side hot path of the paper's encrypted processor -- every
  * two-input Homomorphic Gate of a circuit level (Section 2.1.2 "Homomorphic
- * Gates", "Bootstrapping in TFHE") and the CMUX Memory read and write units
- * (Section 8.2).  Key generation and encryption are client-side and not part of
+ * Gates", "Bootstrapping in TFHE"), the CMUX Memory read and write units
+ * (Section 8.2) and the circuit bootstrapping that feeds them TRGSW addresses.  Key generation and encryption are client-side and not part of
  * this library.
  *
  * Data conventions (all values Torus32 = uint32, arithmetic mod 2^32):
@@ -167,6 +167,8 @@ enum {
                                         one persistent launch */
     TFHE_STAGE_KEYSWITCH = 4,        /* SampleExtract + identity key switch (one launch) */
     TFHE_STAGE_CMUX = 5,             /* CMUX batches, tree levels, RAM write */
+    TFHE_STAGE_CB_BLIND_ROTATE = 6,  /* circuit bootstrapping: lvl2 BlindRotates (one launch) */
+    TFHE_STAGE_CB_KEYSWITCH = 7,     /* circuit bootstrapping: private key switches */
     TFHE_NUM_STAGES = 8
 };
 int tfhe_ctx_enable_timing(tfhe_ctx *ctx, int on);
@@ -267,6 +269,65 @@ int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_
  * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16. */
 int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, const uint32_t *new_cell,
                    uint32_t *cells, int form, void *stream);
+
+/* ---- Circuit Bootstrapping (Section 2.1.2 "Circuit Bootstrapping"; Section 8.2: the
+ * memory controller feeds TLWE address bits, which circuit bootstrapping turns into the
+ * TRGSW selectors of the CMUX Memory; Section 6.2(a) names it an open problem on GPUs
+ * because its modulus exceeds the 64-bit NTT prime).
+ *
+ * A lvl0 TLWE c of bit m becomes a lvl1 TRGSW of m in two steps:
+ *   1. for u = 1..l: ModSwitch c to Z_{2 N2}; BlindRotate over the lvl2 ring (degree N2,
+ *      64-bit torus: x -> round(x 2^64) mod 2^64) with BSK2 and the test vector
+ *      1/(2 Bg^u) sum_j X^j; SampleExtract; add 1/(2 Bg^u) to b.  Result: a lvl2 TLWE
+ *      u64[N2 + 1] of m / Bg^u.
+ *   2. TRGSW row u-1 = private functional key switch of that TLWE with f_0(x) = -s1[X] x
+ *      (phase -m s1 / Bg^u, i.e. m / Bg^u on the a column); row l+u-1 = the same with
+ *      f_1(x) = x (m / Bg^u on the b column).
+ * The lvl2 products are exact: each 64-bit key word is split into 32-bit halves, and
+ * each half's product with the digits (|sum| < 2^63) goes through the NTT over
+ * 2^64 - 2^32 + 1; the halves recombine mod 2^64.
+ *
+ * Key layouts (device pointers, caller-owned):
+ *   BSK2  u64[n][2 l2][2][N2]   BSK2[i] = TRGSW_lvl2(s0[i]) over the 64-bit torus, rows as
+ *                               for the lvl1 TRGSW with 1/Bg2^j = 2^(64 - j Bg2bit)
+ *   PKSK  u32[2][N2 + 1][t][2^basebit][2][N]
+ *                               PKSK[z][i][j][v] = TRLWE_lvl1(f_z(v k_i / 2^{(j+1) basebit})),
+ *                               k_i = s2[i] for i < N2, k_{N2} = -1 (so that the TLWE's b is
+ *                               input N2); entries with v = 0 are never read. */
+typedef struct tfhe_cb_params {
+    int32_t N2;          /* lvl2 ring degree: power of two, N..2048 */
+    int32_t l2;          /* lvl2 gadget levels, 1..8 */
+    int32_t Bg2bit;      /* log2 of the lvl2 gadget base, l2 * Bg2bit <= 63, 2 l2 N2 Bg2/2 < 2^31 */
+    int32_t pks_t;       /* private key-switching levels */
+    int32_t pks_basebit; /* log2 of its base, 1..8, pks_t * pks_basebit <= 32 */
+} tfhe_cb_params;
+
+/* Load the circuit-bootstrapping keys (layouts above) for the context's lvl0/lvl1
+ * parameters.  The context copies them (BSK2 as the NTT-domain transforms of its two
+ * 32-bit halves, u64[n][2 l2][2][2][N2]; PKSK without the v = 0 entries) on `stream`;
+ * the caller keeps ownership of its buffers.  TFHE_EUNSUPPORTED for parameters outside
+ * the ranges above; TFHE_ENOMEM if the copies do not fit (about 2.7 GB at N2 = 2048,
+ * N = 1024, t = 10, basebit = 3). */
+int tfhe_ctx_set_cb_keys(tfhe_ctx *ctx, const tfhe_cb_params *cbp, const uint64_t *bsk2,
+                         const uint32_t *pksk, void *stream);
+
+/* Circuit bootstrapping of R lvl0 TLWEs: in device u32[R][n+1] -> out device
+ * u32[R][2l][2][N] lvl1 TRGSWs (usable as CMUX selectors, e.g. tfhe_cmux_tree_read's
+ * addr_trgsw).  R*l lvl2 BlindRotates (one thread block each) then 2*R*l private key
+ * switches.  TFHE_ENOKEYS without tfhe_ctx_set_cb_keys.  Workspace u64[R][l][N2+1] is
+ * grown as needed.  Asynchronous on `stream`. */
+int tfhe_circuit_bootstrap(tfhe_ctx *ctx, const uint32_t *in, uint32_t *out, int R, void *stream);
+
+/* The two steps separately (for testing and custom schedules).
+ *   tfhe_cb_tlwe2: in device u32[R][n+1] -> out device u64[R][l][N2+1], the lvl2 TLWE of
+ *     m / Bg^u at [r][u-1].
+ *   tfhe_private_keyswitch: in device u64[J][N2+1] lvl2 TLWEs -> out device u32[J][2][N]
+ *     TRLWEs with phase f_z(phase of in[j]), z = 0 (f_0(x) = -s1[X] x) or 1 (f_1(x) = x):
+ *     out[j] = - sum_{i <= N2} sum_{k < t} PKSK[z][i][k][digit_k(a_i)] with a_{N2} = b and
+ *     the unsigned base-2^basebit digits of a_i rounded to t digits. */
+int tfhe_cb_tlwe2(tfhe_ctx *ctx, const uint32_t *in, uint64_t *out, int R, void *stream);
+int tfhe_private_keyswitch(tfhe_ctx *ctx, const uint64_t *in, uint32_t *out, int J, int z,
+                           void *stream);
 
 /* ---- Level scheduler (Section 6.2(d): circuit -> DAG -> levels of independent gates) */
 

@@ -46,8 +46,13 @@ EXPORTS = [
     "tfhe_mux_batch_noks",
     "tfhe_ram_cycle",
     "tfhe_rom_read",
+    "tfhe_ctx_set_cb_keys",
+    "tfhe_circuit_bootstrap",
+    "tfhe_cb_tlwe2",
+    "tfhe_private_keyswitch",
 ]
-STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux"]
+STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux",
+          "cb_blind_rotate", "cb_keyswitch"]
 NUM_STAGES = 8
 
 
@@ -61,6 +66,11 @@ class CParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("N", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("Bgbit", ctypes.c_int32), ("ks_t", ctypes.c_int32),
                 ("ks_basebit", ctypes.c_int32)]
+
+
+class CCbParams(ctypes.Structure):
+    _fields_ = [("N2", ctypes.c_int32), ("l2", ctypes.c_int32), ("Bg2bit", ctypes.c_int32),
+                ("pks_t", ctypes.c_int32), ("pks_basebit", ctypes.c_int32)]
 
 
 class CCircuit(ctypes.Structure):
@@ -109,6 +119,10 @@ def lib():
         "tfhe_mux_batch_noks": (i32, [vp, vp, i64, vp, vp, i32, i32, vp]),
         "tfhe_ram_cycle": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]),
         "tfhe_rom_read": (i32, [vp, vp, vp, i32, i32, vp, vp, i32, vp]),
+        "tfhe_ctx_set_cb_keys": (i32, [vp, ctypes.POINTER(CCbParams), vp, vp, vp]),
+        "tfhe_circuit_bootstrap": (i32, [vp, vp, vp, i32, vp]),
+        "tfhe_cb_tlwe2": (i32, [vp, vp, vp, i32, vp]),
+        "tfhe_private_keyswitch": (i32, [vp, vp, vp, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,6 +306,31 @@ class Context:
                                         _ptr(out_bits) if out_bits is not None else None, R,
                                         _stream(stream)), "rom_read")
         return out_trlwe, out_bits
+
+    def set_cb_keys(self, cbp, bsk2, pksk, stream=None):
+        """Circuit-bootstrapping keys: BSK2 u64[n][2 l2][2][N2] (a torch int64/uint64 tensor)
+        and PKSK u32[2][N2+1][t][2^basebit][2][N]."""
+        q = cbp.abi() if hasattr(cbp, "abi") else tuple(cbp)
+        self._check(lib().tfhe_ctx_set_cb_keys(self.h, ctypes.byref(CCbParams(*q)), _ptr(bsk2),
+                                               _ptr(pksk), _stream(stream)), "set_cb_keys")
+
+    def circuit_bootstrap(self, tlwe, out, stream=None):
+        """lvl0 TLWE [R][n+1] -> lvl1 TRGSW [R][2l][2][N]."""
+        self._check(lib().tfhe_circuit_bootstrap(self.h, _ptr(tlwe), _ptr(out), tlwe.shape[0],
+                                                 _stream(stream)), "circuit_bootstrap")
+        return out
+
+    def cb_tlwe2(self, tlwe, out, stream=None):
+        """Step 1 of circuit bootstrapping: lvl0 TLWE [R][n+1] -> lvl2 TLWE [R][l][N2+1]."""
+        self._check(lib().tfhe_cb_tlwe2(self.h, _ptr(tlwe), _ptr(out), tlwe.shape[0],
+                                        _stream(stream)), "cb_tlwe2")
+        return out
+
+    def private_keyswitch(self, tlwe2, out, z, stream=None):
+        """Step 2: lvl2 TLWE [J][N2+1] -> TRLWE [J][2][N] with f_0 = -s1[X] x or f_1 = x."""
+        self._check(lib().tfhe_private_keyswitch(self.h, _ptr(tlwe2), _ptr(out), tlwe2.shape[0],
+                                                 z, _stream(stream)), "private_keyswitch")
+        return out
 
     def plan(self, circuits, form=FORM_AUTO):
         return Plan(self, circuits, form)

@@ -56,6 +56,17 @@ struct tfhe_ctx {
     uint8_t *st_types = nullptr;
     int32_t *st_idx = nullptr;
 
+    // circuit bootstrapping (cb.cu)
+    bool has_cb_keys = false;
+    tfhe_cb_params cbp{};
+    int logN2 = 0;
+    uint64_t *bsk2_ntt = nullptr;  // [n][2 l2][2][2 halves][N2] NTT domain, scaled by N2^-1
+    uint32_t *pksk = nullptr;      // [2][N2+1][t][base - 1][2N], rows v = 1..base-1
+    uint64_t *psi2_fwd = nullptr, *psi2_inv = nullptr;  // twiddles for the lvl2 ring
+    uint64_t n2_inv = 0;
+    uint64_t *ws_cb = nullptr;  // lvl2 TLWEs [R][l][N2+1] between the two steps
+    size_t ws_cb_cap = 0;       // bytes
+
     TcWorkspace *tc = nullptr;
     // plan autotuner: the fastest (form, Karatsuba level) measured per batch width
     struct TuneEntry {
@@ -114,6 +125,8 @@ int tfhe_ensure_trgsw_ws(tfhe_ctx *ctx, size_t count);
 
 // ntt.cu
 int tfhe_ntt_setup(tfhe_ctx *ctx);
+// psi^{brv(k)}, psi^{-brv(k)} (psi a primitive 2N-th root of unity mod P) and N^{-1}
+int tfhe_make_twiddles(tfhe_ctx *ctx, int N, uint64_t **fwd, uint64_t **inv, uint64_t *n_inv);
 int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
                       cudaStream_t st);
 int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,

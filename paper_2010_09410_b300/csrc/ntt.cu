@@ -7,7 +7,7 @@
 // of N terms is below 2l * N * (Bg/2) * 2^32 (< 2^50 for l = 3, N = 1024, Bg = 64) <
 // P/2 in magnitude, so its residue mod P identifies the integer, which is then
 // reduced mod 2^32 (gl_lift_u32).
-#include "common.cuh"
+#include "ntt.cuh"
 
 // ---------------------------------------------------------------------------
 // Host: twiddles
@@ -33,8 +33,9 @@ static int bitrev(int x, int bits) {
     return r;
 }
 
-int tfhe_ntt_setup(tfhe_ctx *ctx) {
-    const int N = ctx->p.N, logN = ctx->logN;
+int tfhe_make_twiddles(tfhe_ctx *ctx, int N, uint64_t **fwd, uint64_t **inv, uint64_t *n_inv) {
+    int logN = 0;
+    while ((1 << logN) < N) logN++;
     // 7 generates the multiplicative group of Z_P (order 2^32 (2^32 - 1)).
     const uint64_t psi = h_powmod(7, (GL_P - 1) / (2 * (uint64_t)N));
     if (h_powmod(psi, N) != GL_P - 1)
@@ -45,57 +46,16 @@ int tfhe_ntt_setup(tfhe_ctx *ctx) {
         f[k] = h_powmod(psi, (uint64_t)bitrev(k, logN));
         g[k] = h_powmod(psi_inv, (uint64_t)bitrev(k, logN));
     }
-    ctx->n_inv = h_powmod((uint64_t)N, GL_P - 2);
-    if (cudaMalloc(&ctx->psi_fwd, N * 8) != cudaSuccess ||
-        cudaMalloc(&ctx->psi_inv, N * 8) != cudaSuccess)
+    *n_inv = h_powmod((uint64_t)N, GL_P - 2);
+    if (cudaMalloc(fwd, N * 8) != cudaSuccess || cudaMalloc(inv, N * 8) != cudaSuccess)
         return tfhe_set_error(ctx, TFHE_ENOMEM, "twiddle tables");
-    TFHE_CUDA_TRY(ctx, cudaMemcpy(ctx->psi_fwd, f.data(), N * 8, cudaMemcpyHostToDevice));
-    TFHE_CUDA_TRY(ctx, cudaMemcpy(ctx->psi_inv, g.data(), N * 8, cudaMemcpyHostToDevice));
+    TFHE_CUDA_TRY(ctx, cudaMemcpy(*fwd, f.data(), N * 8, cudaMemcpyHostToDevice));
+    TFHE_CUDA_TRY(ctx, cudaMemcpy(*inv, g.data(), N * 8, cudaMemcpyHostToDevice));
     return TFHE_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Device: in-place negacyclic transforms of `np` polynomials a[np][N] in shared memory
-// ---------------------------------------------------------------------------
-
-// Cooley-Tukey butterflies with twiddles psi^{brv(m+i)}: natural order in,
-// evaluations at the odd powers of psi (bit-reversed order) out.
-__device__ __forceinline__ void ntt_fwd(uint64_t *a, int np, int N, int logN,
-                                        const uint64_t *__restrict__ psi) {
-    const int half = N >> 1;
-    for (int s = 0; s < logN; s++) {
-        const int m = 1 << s, logt = logN - 1 - s, t = 1 << logt;
-        for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
-            const int poly = idx >> (logN - 1), b = idx & (half - 1);
-            const int i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
-            uint64_t *x = a + (size_t)poly * N;
-            const uint64_t S = __ldg(psi + m + i);
-            const uint64_t U = x[j], V = gl_mul(x[j + t], S);
-            x[j] = gl_add(U, V);
-            x[j + t] = gl_sub(U, V);
-        }
-        __syncthreads();
-    }
-}
-
-// Gentleman-Sande butterflies with psi^{-brv(h+i)}: bit-reversed in, natural out.
-// The factor N^{-1} is folded into the NTT-domain keys.
-__device__ __forceinline__ void ntt_inv(uint64_t *a, int np, int N, int logN,
-                                        const uint64_t *__restrict__ psi_inv) {
-    const int half = N >> 1;
-    for (int s = 0; s < logN; s++) {
-        const int logt = s, t = 1 << s, h = N >> (s + 1);
-        for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
-            const int poly = idx >> (logN - 1), b = idx & (half - 1);
-            const int i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
-            uint64_t *x = a + (size_t)poly * N;
-            const uint64_t S = __ldg(psi_inv + h + i);
-            const uint64_t U = x[j], V = x[j + t];
-            x[j] = gl_add(U, V);
-            x[j + t] = gl_mul(gl_sub(U, V), S);
-        }
-        __syncthreads();
-    }
+int tfhe_ntt_setup(tfhe_ctx *ctx) {
+    return tfhe_make_twiddles(ctx, ctx->p.N, &ctx->psi_fwd, &ctx->psi_inv, &ctx->n_inv);
 }
 
 // Polynomials (u32 words as integers in [0, 2^32)) -> NTT domain scaled by N^{-1}.
