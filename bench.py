@@ -42,6 +42,8 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
+    ap.add_argument("--cb-reads", type=int, default=64,
+                    help="cb workload: reads of 9 TLWE address bits each (576 bootstraps at 64)")
     ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle", "romp", "cb"],
                     help="level: the headline flat level (default); dag: 20,000-gate 60-level "
                          "DAG through the level scheduler; mixed: 16 uneven circuits "
@@ -483,11 +485,12 @@ def run_other(args):
                                         for L in plan.circuit_last_level]
             extra["circuit_gates"] = [c.num_gates for c in circs]
     elif args.workload == "cb":
-        R, v = 64, 9
+        R, v = args.cb_reads, 9
         q = ti.CB_STD
         cbk = ti.cb_keys(p, q, seed)
         ctx.set_cb_keys(q, torch.from_numpy(cbk.bsk2.view(np.int64)).cuda(), dev(cbk.pksk))
         ctx.sync()
+        torch.cuda.empty_cache()  # the caller's key copies are no longer needed
         rom = ti.cmux_rom(p, seed, v=v, R=R)
         abits = ((rom.addrs[:, None] >> np.arange(v)[None, :]) & 1).astype(np.uint8).reshape(-1)
         tl = dev(ti.encrypt_tlwe0_bits(p, seed, 97, k.s0, abits))
@@ -501,8 +504,8 @@ def run_other(args):
         units, unit = R * v, "circuit bootstraps/s"
         metric = ("circuit bootstraps/s (lvl0 TLWE -> lvl1 TRGSW over a Torus64 lvl2 ring), "
                   "feeding 64 CMUX-tree reads")
-        workload = ("64 reads x 9 TLWE address bits: 576 circuit bootstraps (N2=2048 l2=4 "
-                    "Bg2bit=9, private KS t=10 basebit=3) + 64 reads of a 512-row table, N=1024")
+        workload = (f"{R} reads x 9 TLWE address bits: {R * v} circuit bootstraps (N2=2048 l2=4 "
+                    f"Bg2bit=9, private KS t=10 basebit=3) + {R} reads of a 512-row table, N=1024")
         step()
         ctx.sync()
         ctx.enable_timing(True)
