@@ -63,6 +63,24 @@ def dist_env():
     return rank, world, local
 
 
+def shard_seed(base_seed, rank):
+    """Seed of rank `rank`'s shard of independent gates (weak scaling: every rank
+    bootstraps its own flat level of the same size; rank 0's is the 1-GPU workload)."""
+    return base_seed + 0x10000 * rank
+
+
+def reduce_max_sum(dist, ms, units, device):
+    """Whole-job timing over ranks: the slowest rank's time and the units all ranks
+    processed.  Returns (max ms, total units, units/s)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    tmax, utot = float(t.item()), float(u.item())
+    return tmax, utot, utot / (tmax / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -188,7 +206,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     tbuild.build()
     p = ti.STD
-    batch = ti.flat_level(args.gates)
+    batch = ti.flat_level(args.gates, seed=shard_seed(ti.SEED_FLAT, rank))
     k = batch.keys
     ctx = tb.Context(p, local)
     ctx.set_keys(torch.from_numpy(k.bsk.view(np.int32)).cuda(),
@@ -251,14 +269,14 @@ def run_ours(args):
         stages = ctx.stage_times()
         step_ms = [a.elapsed_time(b) for a, b in evs]
         total_ms = sum(step_ms)
+        units = args.gates * args.steps
+        rate = units / (total_ms / 1e3)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms, units, rate = reduce_max_sum(dist, total_ms, units, "cuda")
             dist.barrier()
         launches = sum(n for _, n in stages.values())
         results[name] = {"ms_total": total_ms, "ms_per_step": total_ms / args.steps,
-                         "gates_per_s": world * args.gates * args.steps / (total_ms / 1e3),
+                         "gates_per_s": rate,
                          "stages": stages, "clocks": clk, "decrypt_ok": ok,
                          "launches": launches}
 
