@@ -351,9 +351,10 @@ def peaks():
 # kernel, from one ncu capture of this bench's 4096-gate level; valid only while the
 # kernel source is byte-identical to the one captured (else reported as null).
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_tc_blind_rotate
-    #   -s 2 -c 1 python bench.py --steps 1 --warmup 3 --no-cpu-baseline --form tc
-    "k_tc_blind_rotate<2>": {"bytes": 100.73e9 + 103.71e9, "source_sha256": "06e8fa3d45f79ddfa8569c1cc784f182b9c0e875768d3d320ed34d5e101def4d"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #   --clock-control none -k regex:k_tc_blind_rotate -s 2 -c 1
+    #   python bench.py --steps 1 --warmup 3 --no-cpu-baseline --form tc
+    "k_tc_blind_rotate<2>": {"bytes": 99.14e9 + 102.56e9, "source_sha256": "6f3986cf9f300142e068be80bdd04c5b9713f948d378bb8a8877deb7ae890f6c"},
 }
 
 
