@@ -250,7 +250,10 @@ int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, in
 /* Batched CMUX (Section 2.1.2 "CMUX"): out[k] = d0[k] + C_k (.) (d1[k] - d0[k]) with
  * C_k = trgsw + (k / group) * (2l * 2 * N) -- consecutive runs of `group` CMUXes
  * share one TRGSW selector.  d1, d0, out: device u32[B][2][N]; out may alias d0 or
- * d1 (same k only).  trgsw: device u32[ceil(B / group)][2l][2][N]. */
+ * d1 (same k only).  trgsw: device u32[ceil(B / group)][2l][2][N].
+ * CMUX batches, trees and RAM writes run in the NTT form: form must be TFHE_FORM_NTT;
+ * TFHE_FORM_TC returns TFHE_EUNSUPPORTED (the tensor-core form covers the BlindRotate
+ * of gate batches, whose key is shared by the whole batch). */
 int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint32_t *d1,
                     const uint32_t *d0, uint32_t *out, int B, int form, void *stream);
 
@@ -258,7 +261,7 @@ int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint3
  * 2^v TRLWE rows.  Address bit j (least significant first) selects at tree level j:
  *   node_j[k] = CMUX(C_{r,j}, node_{j-1}[2k+1], node_{j-1}[2k]),  node_{-1} = table.
  * addr_trgsw: device u32[R][v][2l][2][N]; table: device u32[2^v][2][N];
- * out: device u32[R][2][N].  1 <= v <= 16. */
+ * out: device u32[R][2][N].  1 <= v <= 16.  form: TFHE_FORM_NTT (see tfhe_cmux_batch). */
 int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *table, int v,
                         uint32_t *out, int R, int form, void *stream);
 
@@ -266,7 +269,8 @@ int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_
  * cell c of the 2^v cells, r <- new_cell; for j = 0..v-1: r <- CMUX(S_j, r, cell_c)
  * with S_j = C_j if bit j of c is 1 else G - C_j (G the gadget TRGSW of 1); then
  * cell_c <- r.  addr_trgsw: device u32[v][2l][2][N]; new_cell: device u32[2][N];
- * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16. */
+ * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16.  form: TFHE_FORM_NTT
+ * (see tfhe_cmux_batch). */
 int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, const uint32_t *new_cell,
                    uint32_t *cells, int form, void *stream);
 
