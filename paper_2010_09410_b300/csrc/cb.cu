@@ -7,19 +7,22 @@
 // Z_{2 N2}, BlindRotate of the test vector 1/(2 Bg^u) sum_j X^j over the lvl2 ring,
 // SampleExtract, + 1/(2 Bg^u) on b: a lvl2 TLWE of m / Bg^u.
 //
-// Exact Torus64 external products with the NTT over P = 2^64 - 2^32 + 1: each key word
-// K = K_lo + 2^32 K_hi is kept as the transforms of its two 32-bit halves.  With digits
-// |d| <= Bg2/2, each half's product sum over 2 l2 rows of N2 terms is below
-// 2 l2 N2 (Bg2/2) 2^32 (2^54 at l2 = 4, N2 = 2048, Bg2 = 512) < P/2 in magnitude, so its
-// residue identifies the integer; the result is (V_lo + 2^32 V_hi) mod 2^64.  The
-// accumulator, the l2 digit polynomials of one TRLWE column and the four product
-// polynomials (a/b column x lo/hi half) stay in shared memory (160 KB at N2 = 2048).
+// Exact Torus64 external products: each key word K = K_lo + 2^32 K_hi is kept as the
+// transforms of its two 32-bit halves.  With digits |d| <= Bg2/2, each half's product sum
+// over 2 l2 rows of N2 terms is below 2 l2 N2 (Bg2/2) 2^32 (2^54 at l2 = 4, N2 = 2048,
+// Bg2 = 512).  It is computed by NTTs modulo two 30-bit primes and recombined by the CRT
+// (ntt32.cuh; the modulus, about 2^59.4, exceeds twice the bound), so it is the integer
+// itself, and (V_lo + 2^32 V_hi) mod 2^64 is the product.  The accumulator (2 x N2 u64),
+// the l2 digit polynomials of one TRLWE column and the four product polynomials (a/b
+// column x lo/hi half), each for both primes, stay in shared memory (160 KB at N2 = 2048).
 //
 // Step 2 (k_private_ks, one block per (lvl2 TLWE, function z)): the private functional
 // key switch out = - sum_{i <= N2} sum_k PKSK[z][i][k][digit_k(a_i)] (a_{N2} = b), the
 // digits staged in shared memory, the PKSK rows (8 KB TRLWEs at N = 1024) gathered with
 // 16-byte loads.
-#include "ntt.cuh"
+#include <vector>
+
+#include "ntt32.cuh"
 
 namespace {
 
@@ -43,26 +46,30 @@ __device__ __forceinline__ int32_t gadget_digit64(uint64_t u, int j /*1-based*/,
     return (int32_t)((u >> (64 - j * Bgbit)) & ((1ull << Bgbit) - 1)) - (1 << (Bgbit - 1));
 }
 
-// residue of an integer V with |V| < P/2 -> V mod 2^64 (V - P wraps to V + 2^32 - 1)
-__device__ __forceinline__ uint64_t gl_lift_u64(uint64_t v) {
-    return v > (GL_P >> 1) ? v - GL_P : v;
-}
-
-// BSK2 polynomials u64[polys][N] -> NTT domain of their 32-bit halves, u64[polys][2][N]
-// (lo, hi), scaled by N^{-1}.
-__global__ void k_bsk2_to_ntt(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int N,
-                              int logN, uint64_t n_inv, const uint64_t *__restrict__ psi) {
-    extern __shared__ uint64_t sm[];  // [2][N]
+// BSK2 polynomials u64[polys][N] -> the NTT-domain residues of their 32-bit halves,
+// u32[polys][2 primes][2 halves][N], in Montgomery form and scaled by N^{-1}:
+// f_p = N^{-1} 2^32 mod p.
+__global__ void k_bsk2_to_ntt32(const uint64_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                int N, int logN, const uint32_t *__restrict__ tw, uint32_t f1,
+                                uint32_t f2) {
+    extern __shared__ uint32_t sm32[];  // [2 primes][2 halves][N]
     const size_t poly = blockIdx.x;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const uint64_t w = src[poly * N + k];
-        sm[k] = (uint32_t)w;
-        sm[N + k] = w >> 32;
+        const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+        sm32[k] = lo % NP1;
+        sm32[N + k] = hi % NP1;
+        sm32[2 * N + k] = lo % NP2;
+        sm32[3 * N + k] = hi % NP2;
     }
     __syncthreads();
-    ntt_fwd(sm, 2, N, logN, psi);
-    for (int k = threadIdx.x; k < 2 * N; k += blockDim.x)
-        dst[poly * 2 * N + k] = gl_mul(sm[k], n_inv);
+    ntt32_fwd(sm32, 2, N, logN, tw);
+    for (int x = threadIdx.x; x < 4 * N; x += blockDim.x) {
+        const bool pr = x >= 2 * N;
+        const uint32_t p = pr ? NP2 : NP1;
+        const uint32_t v = red_below(sm32[x], p);
+        dst[poly * 4 * N + x] = (uint32_t)((uint64_t)v * (pr ? f2 : f1) % p);
+    }
 }
 
 // PKSK [2][N2+1][t][base][W] -> [2][N2+1][t][base-1][W]: drop the v = 0 entries.
@@ -81,12 +88,11 @@ __global__ void k_pksk_relayout(const uint32_t *__restrict__ src, uint32_t *__re
 __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
     int n, int N2, int logN2, int l2, int Bg2bit, int l, int Bgbit,
     const uint32_t *__restrict__ in, uint64_t *__restrict__ out,
-    const uint64_t *__restrict__ bsk2, const uint64_t *__restrict__ psi_f,
-    const uint64_t *__restrict__ psi_i) {
+    const uint32_t *__restrict__ bsk2, const uint32_t *__restrict__ tw) {
     extern __shared__ uint64_t sm[];
-    uint64_t *acc = sm;                      // [2][N2]
-    uint64_t *dig = acc + 2 * N2;            // [l2][N2]
-    uint64_t *prod = dig + (size_t)l2 * N2;  // [2 columns][2 halves][N2]
+    uint64_t *acc = sm;                                      // [2][N2]
+    uint32_t *dig = (uint32_t *)(acc + 2 * N2);              // [2 primes][l2][N2]
+    uint32_t *prod = dig + (size_t)2 * l2 * N2;              // [2 primes][2 columns x 2 halves][N2]
     const int job = blockIdx.x;
     const int r = job / l, u = job % l + 1;
     const uint32_t *c = in + (size_t)r * (n + 1);
@@ -100,47 +106,67 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
     }
     __syncthreads();
     const uint64_t off = gadget_offset64(l2, Bg2bit);
-    const size_t per = (size_t)2 * l2 * 4 * N2;  // words of one NTT-domain BSK2_i
+    const size_t per = (size_t)2 * l2 * 2 * 4 * N2;  // words of one NTT-domain BSK2_i
+    const size_t dplane = (size_t)l2 * N2, pplane = (size_t)4 * N2;
     for (int i = 0; i < n; i++) {
         const int a = (int)((uint32_t)(__ldg(c + i) + (1u << (sh - 1))) >> sh);
         if (a == 0) continue;  // X^0 ACC - ACC = 0: all-zero digits, the step is the identity
-        const uint64_t *key = bsk2 + (size_t)i * per;
+        const uint32_t *key = bsk2 + (size_t)i * per;
         for (int cc = 0; cc < 2; cc++) {
-            const uint64_t *p = acc + (size_t)cc * N2;
+            const uint64_t *pa = acc + (size_t)cc * N2;
             for (int j = threadIdx.x; j < N2; j += blockDim.x) {
-                const uint64_t uu = rot_coef64(p, N2, a, j) - p[j] + off;
-                for (int q = 0; q < l2; q++)
-                    dig[(size_t)q * N2 + j] = gl_from_i32(gadget_digit64(uu, q + 1, Bg2bit));
+                const uint64_t uu = rot_coef64(pa, N2, a, j) - pa[j] + off;
+                for (int q = 0; q < l2; q++) {
+                    const int32_t d = gadget_digit64(uu, q + 1, Bg2bit);
+                    dig[(size_t)q * N2 + j] = res_of_i32(d, NP1);
+                    dig[dplane + (size_t)q * N2 + j] = res_of_i32(d, NP2);
+                }
             }
             __syncthreads();
-            ntt_fwd(dig, l2, N2, logN2, psi_f);
+            ntt32_fwd_r8(dig, l2, N2, logN2, tw);
+            // pointwise: sum over this column's l2 rows of digit x key, per prime, for the
+            // four outputs (a/b column x lo/hi half); Montgomery-reduced every 4 rows
             for (int k = threadIdx.x; k < N2; k += blockDim.x) {
-                uint64_t s00 = 0, s01 = 0, s10 = 0, s11 = 0;
-                if (cc) {
-                    s00 = prod[k];
-                    s01 = prod[N2 + k];
-                    s10 = prod[2 * N2 + k];
-                    s11 = prod[3 * N2 + k];
+#pragma unroll
+                for (int pr = 0; pr < 2; pr++) {
+                    const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
+                    uint32_t rs[4];
+#pragma unroll
+                    for (int o = 0; o < 4; o++) rs[o] = cc ? prod[pr * pplane + (size_t)o * N2 + k] : 0u;
+                    uint64_t t4[4] = {0, 0, 0, 0};
+                    for (int q = 0; q < l2; q++) {
+                        const uint32_t dv = red_below(dig[pr * dplane + (size_t)q * N2 + k], p);
+                        // key words of row cc*l2+q, columns 0/1, this prime, halves lo/hi
+                        const uint32_t *kr = key + ((size_t)(cc * l2 + q) * 2 * 4 + pr * 2) * N2 + k;
+                        t4[0] += (uint64_t)dv * __ldg(kr);           // a column, lo half
+                        t4[1] += (uint64_t)dv * __ldg(kr + N2);      // a column, hi half
+                        t4[2] += (uint64_t)dv * __ldg(kr + 4 * N2);  // b column, lo half
+                        t4[3] += (uint64_t)dv * __ldg(kr + 5 * N2);  // b column, hi half
+                        if ((q & 3) == 3 || q == l2 - 1) {  // < 4 p^2 < p 2^32: reduce
+#pragma unroll
+                            for (int o = 0; o < 4; o++) {
+                                rs[o] = red_below(rs[o] + redc32(t4[o], p, ninv), p2);
+                                t4[o] = 0;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = 0; o < 4; o++) prod[pr * pplane + (size_t)o * N2 + k] = rs[o];
                 }
-                for (int q = 0; q < l2; q++) {
-                    const uint64_t dv = dig[(size_t)q * N2 + k];
-                    const uint64_t *kr = key + (size_t)(cc * l2 + q) * 4 * N2 + k;
-                    s00 = gl_add(s00, gl_mul(dv, __ldg(kr)));           // a column, lo half
-                    s01 = gl_add(s01, gl_mul(dv, __ldg(kr + N2)));      // a column, hi half
-                    s10 = gl_add(s10, gl_mul(dv, __ldg(kr + 2 * N2)));  // b column, lo half
-                    s11 = gl_add(s11, gl_mul(dv, __ldg(kr + 3 * N2)));  // b column, hi half
-                }
-                prod[k] = s00;
-                prod[N2 + k] = s01;
-                prod[2 * N2 + k] = s10;
-                prod[3 * N2 + k] = s11;
             }
             __syncthreads();
         }
-        ntt_inv(prod, 4, N2, logN2, psi_i);
+        ntt32_inv_r8(prod, 4, N2, logN2, tw);
         for (int j = threadIdx.x; j < N2; j += blockDim.x) {
-            acc[j] += gl_lift_u64(prod[j]) + (gl_lift_u64(prod[N2 + j]) << 32);
-            acc[N2 + j] += gl_lift_u64(prod[2 * N2 + j]) + (gl_lift_u64(prod[3 * N2 + j]) << 32);
+#pragma unroll
+            for (int col = 0; col < 2; col++) {
+                const size_t o_lo = (size_t)(col * 2) * N2 + j, o_hi = o_lo + N2;
+                const int64_t vlo = crt_centred(red_below(prod[o_lo], NP1),
+                                                red_below(prod[pplane + o_lo], NP2));
+                const int64_t vhi = crt_centred(red_below(prod[o_hi], NP1),
+                                                red_below(prod[pplane + o_hi], NP2));
+                acc[(size_t)col * N2 + j] += (uint64_t)vlo + ((uint64_t)vhi << 32);
+            }
         }
         __syncthreads();
     }
@@ -204,7 +230,30 @@ __global__ void __launch_bounds__(PKS_THREADS) k_private_ks(
     }
 }
 
-size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4) * q.N2 * 8; }
+int bitrev32(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// smallest generator of Z_p^*: g^((p-1)/f) != 1 for every prime factor f of p - 1
+uint32_t primitive_root(uint32_t p) {
+    std::vector<uint32_t> fs;
+    uint32_t m = p - 1;
+    for (uint32_t f = 2; f * f <= m; f++)
+        if (m % f == 0) {
+            fs.push_back(f);
+            while (m % f == 0) m /= f;
+        }
+    if (m > 1) fs.push_back(m);
+    for (uint32_t g = 2;; g++) {
+        bool ok = true;
+        for (uint32_t f : fs) ok = ok && powmod64(g, (p - 1) / f, p) != 1;
+        if (ok) return g;
+    }
+}
+
+size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4) * q.N2 * 8; }  // u64 acc + 2 primes x u32
 size_t cb_ks_smem(const tfhe_cb_params &q) { return (size_t)(q.N2 + 1) * q.pks_t; }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -225,8 +274,7 @@ int launch_cb_blind_rotate(tfhe_ctx *ctx, const uint32_t *in, uint64_t *out, int
                                             (int)smem));
     StageTimer tm(ctx, TFHE_STAGE_CB_BLIND_ROTATE, st);
     k_cb_blind_rotate<<<R * p.l, 1024, smem, st>>>(p.n, q.N2, ctx->logN2, q.l2, q.Bg2bit, p.l,
-                                                   p.Bgbit, in, out, ctx->bsk2_ntt, ctx->psi2_fwd,
-                                                   ctx->psi2_inv);
+                                                   p.Bgbit, in, out, ctx->bsk2_ntt, ctx->cb_tw);
     tm.stop();
     return tfhe_check_launch(ctx, "cb_blind_rotate");
 }
@@ -248,6 +296,35 @@ int launch_private_ks(tfhe_ctx *ctx, const uint64_t *in, uint32_t *out, int J, i
 
 }  // namespace
 
+int tfhe_make_twiddles32(tfhe_ctx *ctx, int N, uint32_t **tw) {
+    int logN = 0;
+    while ((1 << logN) < N) logN++;
+    std::vector<uint32_t> h((size_t)2 * 4 * N);
+    const uint32_t primes[2] = {NP1, NP2};
+    for (int pr = 0; pr < 2; pr++) {
+        const uint32_t p = primes[pr];
+        if ((p - 1) % (2 * (uint32_t)N) != 0)
+            return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no 2N-th root of unity mod the NTT prime");
+        const uint64_t psi = powmod64(primitive_root(p), (p - 1) / (2 * (uint64_t)N), p);
+        if (powmod64(psi, N, p) != p - 1)
+            return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "no primitive 2N-th root of unity");
+        const uint64_t psi_inv = powmod64(psi, p - 2, p);
+        uint32_t *T = h.data() + (size_t)pr * 4 * N;
+        for (int k = 0; k < N; k++) {
+            const uint32_t w = (uint32_t)powmod64(psi, bitrev32(k, logN), p);
+            const uint32_t wi = (uint32_t)powmod64(psi_inv, bitrev32(k, logN), p);
+            T[k] = w;
+            T[N + k] = (uint32_t)(((uint64_t)w << 32) / p);
+            T[2 * N + k] = wi;
+            T[3 * N + k] = (uint32_t)(((uint64_t)wi << 32) / p);
+        }
+    }
+    if (cudaMalloc(tw, h.size() * 4) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "twiddle tables");
+    TFHE_CUDA_TRY(ctx, cudaMemcpy(*tw, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
+    return TFHE_OK;
+}
+
 extern "C" int tfhe_ctx_set_cb_keys(tfhe_ctx *ctx, const tfhe_cb_params *cbp, const uint64_t *bsk2,
                                     const uint32_t *pksk, void *stream) {
     if (!ctx) return TFHE_EINVAL;
@@ -257,11 +334,11 @@ extern "C" int tfhe_ctx_set_cb_keys(tfhe_ctx *ctx, const tfhe_cb_params *cbp, co
     const tfhe_cb_params q = *cbp;
     int logN2 = 0;
     while ((1 << logN2) < q.N2) logN2++;
-    // exactness of the split-key products: 2 l2 N2 2^(Bg2bit-1) 2^32 < 2^63
+    // exactness of the split-key products: 2 l2 N2 2^(Bg2bit-1) 2^32 <= 2^58 < P1 P2 / 2
     int log2l2 = 0;
     while ((1 << log2l2) < 2 * q.l2) log2l2++;
     if (!is_pow2(q.N2) || q.N2 < 256 || q.N2 > 2048 || q.l2 < 1 || q.l2 > 8 || q.Bg2bit < 1 ||
-        q.Bg2bit > 16 || q.l2 * q.Bg2bit > 63 || log2l2 + logN2 + q.Bg2bit - 1 + 32 > 62 ||
+        q.Bg2bit > 16 || q.l2 * q.Bg2bit > 63 || log2l2 + logN2 + q.Bg2bit - 1 + 32 > 58 ||
         q.pks_t < 1 || q.pks_basebit < 1 || q.pks_basebit > 8 || q.pks_t * q.pks_basebit > 32 ||
         p.l * p.Bgbit > 62 || cb_br_smem(q) > 227 * 1024 || cb_ks_smem(q) > 64 * 1024 ||
         2 * p.N > 4 * PKS_THREADS * PKS_MAXQ)
@@ -269,13 +346,12 @@ extern "C" int tfhe_ctx_set_cb_keys(tfhe_ctx *ctx, const tfhe_cb_params *cbp, co
     cudaStream_t st = (cudaStream_t)stream;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     ctx->has_cb_keys = false;
-    if (ctx->psi2_fwd && ctx->cbp.N2 != q.N2) {
-        cudaFree(ctx->psi2_fwd);
-        cudaFree(ctx->psi2_inv);
-        ctx->psi2_fwd = ctx->psi2_inv = nullptr;
+    if (ctx->cb_tw && ctx->cbp.N2 != q.N2) {
+        cudaFree(ctx->cb_tw);
+        ctx->cb_tw = nullptr;
     }
-    if (!ctx->psi2_fwd) {
-        const int rc = tfhe_make_twiddles(ctx, q.N2, &ctx->psi2_fwd, &ctx->psi2_inv, &ctx->n2_inv);
+    if (!ctx->cb_tw) {
+        const int rc = tfhe_make_twiddles32(ctx, q.N2, &ctx->cb_tw);
         if (rc != TFHE_OK) return rc;
     }
     const size_t polys = (size_t)p.n * 2 * q.l2 * 2;
@@ -286,14 +362,18 @@ extern "C" int tfhe_ctx_set_cb_keys(tfhe_ctx *ctx, const tfhe_cb_params *cbp, co
     if (ctx->pksk) cudaFree(ctx->pksk);
     ctx->bsk2_ntt = nullptr;
     ctx->pksk = nullptr;
-    if (cudaMalloc(&ctx->bsk2_ntt, polys * 2 * q.N2 * 8) != cudaSuccess)
+    if (cudaMalloc(&ctx->bsk2_ntt, polys * 4 * q.N2 * 4) != cudaSuccess)
         return tfhe_set_error(ctx, TFHE_ENOMEM, "set_cb_keys: NTT-domain BSK2");
     if (cudaMalloc(&ctx->pksk, pk_rows * W * 4) != cudaSuccess)
         return tfhe_set_error(ctx, TFHE_ENOMEM, "set_cb_keys: private key-switching keys");
     ctx->cbp = q;
     ctx->logN2 = logN2;
-    k_bsk2_to_ntt<<<(unsigned)polys, 512, 2 * q.N2 * 8, st>>>(bsk2, ctx->bsk2_ntt, q.N2, logN2,
-                                                             ctx->n2_inv, ctx->psi2_fwd);
+    const uint32_t ninv1 = (uint32_t)powmod64(q.N2, NP1 - 2, NP1);
+    const uint32_t ninv2 = (uint32_t)powmod64(q.N2, NP2 - 2, NP2);
+    const uint32_t f1 = (uint32_t)(((uint64_t)ninv1 << 32) % NP1);  // N2^{-1} 2^32 mod P1
+    const uint32_t f2 = (uint32_t)(((uint64_t)ninv2 << 32) % NP2);
+    k_bsk2_to_ntt32<<<(unsigned)polys, 512, 4 * q.N2 * 4, st>>>(bsk2, ctx->bsk2_ntt, q.N2, logN2,
+                                                               ctx->cb_tw, f1, f2);
     int rc = tfhe_check_launch(ctx, "bsk2_to_ntt");
     if (rc != TFHE_OK) return rc;
     k_pksk_relayout<<<8192, 256, 0, st>>>(pksk, ctx->pksk, pk_rows, base, (int)W);

@@ -60,10 +60,10 @@ struct tfhe_ctx {
     bool has_cb_keys = false;
     tfhe_cb_params cbp{};
     int logN2 = 0;
-    uint64_t *bsk2_ntt = nullptr;  // [n][2 l2][2][2 halves][N2] NTT domain, scaled by N2^-1
+    uint32_t *bsk2_ntt = nullptr;  // [n][2 l2][2][2 primes][2 halves][N2] residues, NTT domain,
+                                   // Montgomery form, scaled by N2^-1
     uint32_t *pksk = nullptr;      // [2][N2+1][t][base - 1][2N], rows v = 1..base-1
-    uint64_t *psi2_fwd = nullptr, *psi2_inv = nullptr;  // twiddles for the lvl2 ring
-    uint64_t n2_inv = 0;
+    uint32_t *cb_tw = nullptr;     // two-prime twiddles for the lvl2 ring [2][4][N2]
     uint64_t *ws_cb = nullptr;  // lvl2 TLWEs [R][l][N2+1] between the two steps
     size_t ws_cb_cap = 0;       // bytes
 

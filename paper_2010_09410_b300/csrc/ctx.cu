@@ -79,8 +79,7 @@ extern "C" void tfhe_ctx_destroy(tfhe_ctx *ctx) {
     free_dev(ctx->ws_ram);
     free_dev(ctx->bsk2_ntt);
     free_dev(ctx->pksk);
-    free_dev(ctx->psi2_fwd);
-    free_dev(ctx->psi2_inv);
+    free_dev(ctx->cb_tw);
     free_dev(ctx->ws_cb);
     free_dev(ctx->st_in);
     free_dev(ctx->st_out);
