@@ -14,7 +14,8 @@
 // (ntt32.cuh; the modulus, about 2^59.4, exceeds twice the bound), so it is the integer
 // itself, and (V_lo + 2^32 V_hi) mod 2^64 is the product.  The accumulator (2 x N2 u64),
 // the l2 digit polynomials of one TRLWE column and the four product polynomials (a/b
-// column x lo/hi half), each for both primes, stay in shared memory (160 KB at N2 = 2048).
+// column x lo/hi half), each for both primes, and the twiddles stay in shared memory
+// (224 KB at N2 = 2048).
 //
 // Step 2 (k_private_ks, one block per (lvl2 TLWE, function z)): the private functional
 // key switch out = - sum_{i <= N2} sum_k PKSK[z][i][k][digit_k(a_i)] (a_{N2} = b), the
@@ -89,10 +90,13 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
     int n, int N2, int logN2, int l2, int Bg2bit, int l, int Bgbit,
     const uint32_t *__restrict__ in, uint64_t *__restrict__ out,
     const uint32_t *__restrict__ bsk2, const uint32_t *__restrict__ tw) {
-    extern __shared__ uint64_t sm[];
+    extern __shared__ __align__(16) uint64_t sm[];
     uint64_t *acc = sm;                                      // [2][N2]
     uint32_t *dig = (uint32_t *)(acc + 2 * N2);              // [2 primes][l2][N2]
     uint32_t *prod = dig + (size_t)2 * l2 * N2;              // [2 primes][2 columns x 2 halves][N2]
+    uint32_t *tws = prod + (size_t)2 * 4 * N2;               // twiddles [2 primes][4][N2]
+    for (int x = threadIdx.x; x < 2 * N2; x += blockDim.x)
+        reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
     const int job = blockIdx.x;
     const int r = job / l, u = job % l + 1;
     const uint32_t *c = in + (size_t)r * (n + 1);
@@ -114,49 +118,68 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
         const uint32_t *key = bsk2 + (size_t)i * per;
         for (int cc = 0; cc < 2; cc++) {
             const uint64_t *pa = acc + (size_t)cc * N2;
-            for (int j = threadIdx.x; j < N2; j += blockDim.x) {
-                const uint64_t uu = rot_coef64(pa, N2, a, j) - pa[j] + off;
+            // two consecutive coefficients per thread: 8-byte digit stores
+            for (int j = 2 * threadIdx.x; j < N2; j += 2 * blockDim.x) {
+                const ulonglong2 own = *reinterpret_cast<const ulonglong2 *>(pa + j);
+                const uint64_t u0 = rot_coef64(pa, N2, a, j) - own.x + off;
+                const uint64_t u1 = rot_coef64(pa, N2, a, j + 1) - own.y + off;
                 for (int q = 0; q < l2; q++) {
-                    const int32_t d = gadget_digit64(uu, q + 1, Bg2bit);
-                    dig[(size_t)q * N2 + j] = res_of_i32(d, NP1);
-                    dig[dplane + (size_t)q * N2 + j] = res_of_i32(d, NP2);
+                    const int32_t d0 = gadget_digit64(u0, q + 1, Bg2bit);
+                    const int32_t d1 = gadget_digit64(u1, q + 1, Bg2bit);
+                    *reinterpret_cast<uint2 *>(dig + (size_t)q * N2 + j) =
+                        make_uint2(res_of_i32(d0, NP1), res_of_i32(d1, NP1));
+                    *reinterpret_cast<uint2 *>(dig + dplane + (size_t)q * N2 + j) =
+                        make_uint2(res_of_i32(d0, NP2), res_of_i32(d1, NP2));
                 }
             }
             __syncthreads();
-            ntt32_fwd_r8(dig, l2, N2, logN2, tw);
+            ntt32_fwd_r8(dig, l2, N2, logN2, tws);
             // pointwise: sum over this column's l2 rows of digit x key, per prime, for the
-            // four outputs (a/b column x lo/hi half); Montgomery-reduced every 4 rows
-            for (int k = threadIdx.x; k < N2; k += blockDim.x) {
+            // four outputs (a/b column x lo/hi half); two consecutive coefficients per
+            // thread (8-byte loads), Montgomery-reduced every 4 rows
+            for (int it = threadIdx.x; it < N2; it += blockDim.x) {
+                const int pr = it >= (N2 >> 1);
+                const int k = 2 * (it - (pr ? (N2 >> 1) : 0));
+                const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
+                uint32_t *pp = prod + pr * pplane + k;
+                uint2 rs[4];
 #pragma unroll
-                for (int pr = 0; pr < 2; pr++) {
-                    const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
-                    uint32_t rs[4];
+                for (int o = 0; o < 4; o++)
+                    rs[o] = cc ? *reinterpret_cast<const uint2 *>(pp + (size_t)o * N2) : make_uint2(0, 0);
+                uint64_t ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
+#pragma unroll 4
+                for (int q = 0; q < l2; q++) {
+                    const uint2 dd = *reinterpret_cast<const uint2 *>(dig + pr * dplane + (size_t)q * N2 + k);
+                    const uint32_t d0 = red_below(dd.x, p), d1 = red_below(dd.y, p);
+                    // key words of row cc*l2+q, this prime: a column lo/hi, b column lo/hi
+                    const uint32_t *kr = key + ((size_t)(cc * l2 + q) * 2 * 4 + pr * 2) * N2 + k;
+                    const uint2 k0 = __ldg(reinterpret_cast<const uint2 *>(kr));
+                    const uint2 k1 = __ldg(reinterpret_cast<const uint2 *>(kr + N2));
+                    const uint2 k2 = __ldg(reinterpret_cast<const uint2 *>(kr + 4 * N2));
+                    const uint2 k3 = __ldg(reinterpret_cast<const uint2 *>(kr + 5 * N2));
+                    ta[0] += (uint64_t)d0 * k0.x;
+                    tb[0] += (uint64_t)d1 * k0.y;
+                    ta[1] += (uint64_t)d0 * k1.x;
+                    tb[1] += (uint64_t)d1 * k1.y;
+                    ta[2] += (uint64_t)d0 * k2.x;
+                    tb[2] += (uint64_t)d1 * k2.y;
+                    ta[3] += (uint64_t)d0 * k3.x;
+                    tb[3] += (uint64_t)d1 * k3.y;
+                    if ((q & 3) == 3 || q == l2 - 1) {  // < 4 p^2 < p 2^32: reduce
 #pragma unroll
-                    for (int o = 0; o < 4; o++) rs[o] = cc ? prod[pr * pplane + (size_t)o * N2 + k] : 0u;
-                    uint64_t t4[4] = {0, 0, 0, 0};
-                    for (int q = 0; q < l2; q++) {
-                        const uint32_t dv = red_below(dig[pr * dplane + (size_t)q * N2 + k], p);
-                        // key words of row cc*l2+q, columns 0/1, this prime, halves lo/hi
-                        const uint32_t *kr = key + ((size_t)(cc * l2 + q) * 2 * 4 + pr * 2) * N2 + k;
-                        t4[0] += (uint64_t)dv * __ldg(kr);           // a column, lo half
-                        t4[1] += (uint64_t)dv * __ldg(kr + N2);      // a column, hi half
-                        t4[2] += (uint64_t)dv * __ldg(kr + 4 * N2);  // b column, lo half
-                        t4[3] += (uint64_t)dv * __ldg(kr + 5 * N2);  // b column, hi half
-                        if ((q & 3) == 3 || q == l2 - 1) {  // < 4 p^2 < p 2^32: reduce
-#pragma unroll
-                            for (int o = 0; o < 4; o++) {
-                                rs[o] = red_below(rs[o] + redc32(t4[o], p, ninv), p2);
-                                t4[o] = 0;
-                            }
+                        for (int o = 0; o < 4; o++) {
+                            rs[o].x = red_below(rs[o].x + redc32(ta[o], p, ninv), p2);
+                            rs[o].y = red_below(rs[o].y + redc32(tb[o], p, ninv), p2);
+                            ta[o] = tb[o] = 0;
                         }
                     }
-#pragma unroll
-                    for (int o = 0; o < 4; o++) prod[pr * pplane + (size_t)o * N2 + k] = rs[o];
                 }
+#pragma unroll
+                for (int o = 0; o < 4; o++) *reinterpret_cast<uint2 *>(pp + (size_t)o * N2) = rs[o];
             }
             __syncthreads();
         }
-        ntt32_inv_r8(prod, 4, N2, logN2, tw);
+        ntt32_inv_r8(prod, 4, N2, logN2, tws);
         for (int j = threadIdx.x; j < N2; j += blockDim.x) {
 #pragma unroll
             for (int col = 0; col < 2; col++) {
@@ -253,7 +276,8 @@ uint32_t primitive_root(uint32_t p) {
     }
 }
 
-size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4) * q.N2 * 8; }  // u64 acc + 2 primes x u32
+// u64 accumulator, digits and products for both primes (u32), twiddles [2][4][N2] (u32)
+size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4 + 4) * q.N2 * 8; }
 size_t cb_ks_smem(const tfhe_cb_params &q) { return (size_t)(q.N2 + 1) * q.pks_t; }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }

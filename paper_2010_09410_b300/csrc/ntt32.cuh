@@ -115,6 +115,7 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
 }
 
 // ---- register-blocked transforms: radix-2^R passes (R <= 3 stages per pass) ------------
+// (tw may point to global or to shared memory)
 //
 // A forward pass over stages s .. s+R-1 (t = N >> (s+1) at stage s) works on groups of
 // 2^R elements e_k = 2t i + x0 + k t / 2^(R-1), i < 2^s the stage-s block, x0 < t / 2^(R-1);
@@ -125,7 +126,7 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
 // butterflies, twiddles and order within each group as the stage-by-stage loops above.
 template <int R>
 __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int logN, int s,
-                                               const uint32_t *__restrict__ tw) {
+                                               const uint32_t *tw) {
     constexpr int G = 1 << R;
     const int t = N >> (s + 1);
     const int logst = logN - s - R;          // log2 of the element stride inside a group
@@ -148,7 +149,7 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int l
             for (int k = 0; k < G; k++) {
                 if (k & half) continue;
                 const int blk = ((1 << s) << q) + (i << q) + (k >> (R - q));
-                const uint32_t V = shoup_mul(v[k + half], __ldg(T + blk), __ldg(T + N + blk), p);
+                const uint32_t V = shoup_mul(v[k + half], T[blk], T[N + blk], p);
                 const uint32_t U = v[k];
                 v[k] = red_below(U + V, p2);
                 v[k + half] = red_below(U - V + p2, p2);
@@ -162,7 +163,7 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int l
 
 template <int R>
 __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int logN, int s,
-                                               const uint32_t *__restrict__ tw) {
+                                               const uint32_t *tw) {
     constexpr int G = 1 << R;
     const int t = 1 << s;
     const int lgroups = logN - R;
@@ -185,7 +186,7 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int l
                 const int blk = (N >> (s + q + 1)) + (i << (R - 1 - q)) + (k >> (q + 1));
                 const uint32_t U = v[k], V = v[k + dist];
                 v[k] = red_below(U + V, p2);
-                v[k + dist] = shoup_mul(U - V + p2, __ldg(T + 2 * N + blk), __ldg(T + 3 * N + blk), p);
+                v[k + dist] = shoup_mul(U - V + p2, T[2 * N + blk], T[3 * N + blk], p);
             }
         }
 #pragma unroll
@@ -196,7 +197,7 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int l
 
 // Whole transforms by passes of three stages (and one shorter pass at the end).
 __device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int N, int logN,
-                                             const uint32_t *__restrict__ tw) {
+                                             const uint32_t *tw) {
     int s = 0;
     for (; s + 3 <= logN; s += 3) ntt32_fwd_pass<3>(a, np, N, logN, s, tw);
     if (logN - s == 2) ntt32_fwd_pass<2>(a, np, N, logN, s, tw);
@@ -204,7 +205,7 @@ __device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int N, int log
 }
 
 __device__ __forceinline__ void ntt32_inv_r8(uint32_t *a, int np, int N, int logN,
-                                             const uint32_t *__restrict__ tw) {
+                                             const uint32_t *tw) {
     int s = 0;
     for (; s + 3 <= logN; s += 3) ntt32_inv_pass<3>(a, np, N, logN, s, tw);
     if (logN - s == 2) ntt32_inv_pass<2>(a, np, N, logN, s, tw);
