@@ -15,7 +15,7 @@
 // itself, and (V_lo + 2^32 V_hi) mod 2^64 is the product.  The accumulator (2 x N2 u64),
 // the l2 digit polynomials of one TRLWE column and the four product polynomials (a/b
 // column x lo/hi half), each for both primes, and the twiddles stay in shared memory
-// (224 KB at N2 = 2048).
+// (224 KB at N2 = 2048); the digit and product polynomials are stored swizzled (swz).
 //
 // Step 2 (k_private_ks, one block per (lvl2 TLWE, function z)): the private functional
 // key switch out = - sum_{i <= N2} sum_k PKSK[z][i][k][digit_k(a_i)] (a_{N2} = b), the
@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
                 for (int q = 0; q < l2; q++) {
                     const int32_t d0 = gadget_digit64(u0, q + 1, Bg2bit);
                     const int32_t d1 = gadget_digit64(u1, q + 1, Bg2bit);
-                    *reinterpret_cast<uint2 *>(dig + (size_t)q * N2 + j) =
+                    *reinterpret_cast<uint2 *>(dig + (size_t)q * N2 + swz(j)) =
                         make_uint2(res_of_i32(d0, NP1), res_of_i32(d1, NP1));
-                    *reinterpret_cast<uint2 *>(dig + dplane + (size_t)q * N2 + j) =
+                    *reinterpret_cast<uint2 *>(dig + dplane + (size_t)q * N2 + swz(j)) =
                         make_uint2(res_of_i32(d0, NP2), res_of_i32(d1, NP2));
                 }
             }
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
                 const int pr = it >= (N2 >> 1);
                 const int k = 2 * (it - (pr ? (N2 >> 1) : 0));
                 const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
-                uint32_t *pp = prod + pr * pplane + k;
+                uint32_t *pp = prod + pr * pplane + swz(k);
                 uint2 rs[4];
 #pragma unroll
                 for (int o = 0; o < 4; o++)
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
                 uint64_t ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
 #pragma unroll 4
                 for (int q = 0; q < l2; q++) {
-                    const uint2 dd = *reinterpret_cast<const uint2 *>(dig + pr * dplane + (size_t)q * N2 + k);
+                    const uint2 dd = *reinterpret_cast<const uint2 *>(dig + pr * dplane + (size_t)q * N2 + swz(k));
                     const uint32_t d0 = red_below(dd.x, p), d1 = red_below(dd.y, p);
                     // key words of row cc*l2+q, this prime: a column lo/hi, b column lo/hi
                     const uint32_t *kr = key + ((size_t)(cc * l2 + q) * 2 * 4 + pr * 2) * N2 + k;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
         for (int j = threadIdx.x; j < N2; j += blockDim.x) {
 #pragma unroll
             for (int col = 0; col < 2; col++) {
-                const size_t o_lo = (size_t)(col * 2) * N2 + j, o_hi = o_lo + N2;
+                const size_t o_lo = (size_t)(col * 2) * N2 + swz(j), o_hi = o_lo + N2;
                 const int64_t vlo = crt_centred(red_below(prod[o_lo], NP1),
                                                 red_below(prod[pplane + o_lo], NP2));
                 const int64_t vhi = crt_centred(red_below(prod[o_hi], NP1),

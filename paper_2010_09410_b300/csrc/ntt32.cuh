@@ -117,6 +117,12 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
 // ---- register-blocked transforms: radix-2^R passes (R <= 3 stages per pass) ------------
 // (tw may point to global or to shared memory)
 //
+// The polynomials these transforms work on are stored swizzled: coefficient e of a
+// polynomial sits at word swz(e) = e ^ (((e >> 5) & 7) << 2), which permutes aligned
+// 4-word groups inside each 32-word row.  Strided passes then spread a warp's accesses
+// over all banks, and groups of 2 or 4 consecutive coefficients stay contiguous and
+// aligned, so the passes whose groups are contiguous use 16-byte accesses.
+//
 // A forward pass over stages s .. s+R-1 (t = N >> (s+1) at stage s) works on groups of
 // 2^R elements e_k = 2t i + x0 + k t / 2^(R-1), i < 2^s the stage-s block, x0 < t / 2^(R-1);
 // stage s + q pairs k and k + 2^(R-1-q) with the twiddle of its block 2^q i + (k >> (R-q)).
@@ -124,6 +130,40 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
 // e_k = 2^R t i + x0 + k t, x0 < t; stage s + q pairs k and k + 2^q, block 2^(R-1-q) i +
 // (k >> (q+1)), twiddle index (N >> (s+q+1)) + block.  One barrier per pass; the same
 // butterflies, twiddles and order within each group as the stage-by-stage loops above.
+__device__ __forceinline__ int swz(int e) { return e ^ (((e >> 5) & 7) << 2); }
+
+// load / store the 2^R coefficients e0 + k*st of a group (contiguous when st == 1)
+template <int G>
+__device__ __forceinline__ void grp_load(const uint32_t *x, int e0, int st, uint32_t *v) {
+    if (G >= 4 && st == 1) {
+#pragma unroll
+        for (int k = 0; k < G; k += 4) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(x + swz(e0 + k));
+            v[k] = w.x; v[k + 1] = w.y; v[k + 2] = w.z; v[k + 3] = w.w;
+        }
+    } else if (G == 2 && st == 1) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(x + swz(e0));
+        v[0] = w.x; v[1] = w.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k++) v[k] = x[swz(e0 + k * st)];
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void grp_store(uint32_t *x, int e0, int st, const uint32_t *v) {
+    if (G >= 4 && st == 1) {
+#pragma unroll
+        for (int k = 0; k < G; k += 4)
+            *reinterpret_cast<uint4 *>(x + swz(e0 + k)) = make_uint4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else if (G == 2 && st == 1) {
+        *reinterpret_cast<uint2 *>(x + swz(e0)) = make_uint2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k++) x[swz(e0 + k * st)] = v[k];
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int logN, int s,
                                                const uint32_t *tw) {
@@ -137,11 +177,11 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int l
         const int pr = poly >= np;
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
         const int i = gidx >> logst, x0 = gidx & (st - 1);
-        uint32_t *x = a + (size_t)poly * N + (size_t)i * 2 * t + x0;
+        uint32_t *x = a + (size_t)poly * N;
+        const int e0 = i * 2 * t + x0;
         const uint32_t *T = tw + (size_t)pr * 4 * N;
         uint32_t v[G];
-#pragma unroll
-        for (int k = 0; k < G; k++) v[k] = x[k * st];
+        grp_load<G>(x, e0, st, v);
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const int half = G >> (q + 1);
@@ -155,8 +195,7 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int l
                 v[k + half] = red_below(U - V + p2, p2);
             }
         }
-#pragma unroll
-        for (int k = 0; k < G; k++) x[k * st] = v[k];
+        grp_store<G>(x, e0, st, v);
     }
     __syncthreads();
 }
@@ -172,11 +211,11 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int l
         const int pr = poly >= np;
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
         const int i = gidx >> s, x0 = gidx & (t - 1);
-        uint32_t *x = a + (size_t)poly * N + ((size_t)i << (s + R)) + x0;
+        uint32_t *x = a + (size_t)poly * N;
+        const int e0 = (i << (s + R)) + x0;
         const uint32_t *T = tw + (size_t)pr * 4 * N;
         uint32_t v[G];
-#pragma unroll
-        for (int k = 0; k < G; k++) v[k] = x[k * t];
+        grp_load<G>(x, e0, t, v);
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const int dist = 1 << q;
@@ -189,8 +228,7 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int l
                 v[k + dist] = shoup_mul(U - V + p2, T[2 * N + blk], T[3 * N + blk], p);
             }
         }
-#pragma unroll
-        for (int k = 0; k < G; k++) x[k * t] = v[k];
+        grp_store<G>(x, e0, t, v);
     }
     __syncthreads();
 }
