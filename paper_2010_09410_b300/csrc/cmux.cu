@@ -59,7 +59,7 @@ extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
     if (form == TFHE_FORM_NTT) {
         rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
         if (rc != TFHE_OK) return rc;
-        rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
+        rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
         if (rc != TFHE_OK) return rc;
         sel_ntt = ctx->ws_trgsw_ntt;
     }
@@ -114,9 +114,9 @@ extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
                                                        cells, st);
     rc = tfhe_ensure_trgsw_ws(ctx, (size_t)2 * v);
     if (rc != TFHE_OK) return rc;
-    rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
+    rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
     if (rc != TFHE_OK) return rc;
-    rc = tfhe_trgsw_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
+    rc = tfhe_sel_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
     if (rc != TFHE_OK) return rc;
     return tfhe_ram_write_ntt(ctx, ctx->ws_trgsw_ntt, ctx->ws_trgsw_ntt + (size_t)v * per, v,
                               new_cell, cells, st);
@@ -178,9 +178,9 @@ extern "C" int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, 
     rc = tfhe_ensure_trgsw_ws(ctx, (size_t)2 * v);
     if (rc != TFHE_OK) return rc;
     const uint64_t *c_ntt = ctx->ws_trgsw_ntt, *gmc_ntt = ctx->ws_trgsw_ntt + (size_t)v * per;
-    rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
+    rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);
     if (rc == TFHE_OK)
-        rc = tfhe_trgsw_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
+        rc = tfhe_sel_to_ntt(ctx, ctx->ws_gmc, ctx->ws_trgsw_ntt + (size_t)v * per, (size_t)v, st);
     if (rc != TFHE_OK) return rc;
 
     // read unit: the w bit blocks' CMUX trees share the address (selector stride 0)
@@ -270,7 +270,7 @@ extern "C" int tfhe_rom_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const ui
     const size_t per = (size_t)2 * p.l * 2 * p.N;
     // selectors in the NTT domain, every read's v address bits
     int rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
-    if (rc == TFHE_OK) rc = tfhe_trgsw_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
+    if (rc == TFHE_OK) rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
     if (rc != TFHE_OK) return rc;
     const uint64_t *sel = ctx->ws_trgsw_ntt;
     // scratch: two accumulators and one rotated copy per read

@@ -37,6 +37,8 @@ struct tfhe_ctx {
     uint64_t *psi_fwd = nullptr;
     uint64_t *psi_inv = nullptr;
     uint64_t n_inv = 0;
+    // two-prime twiddles for CMUX products at ring degree N ([2][4][N], ntt32.cuh)
+    uint32_t *tw32 = nullptr;
 
     // per-batch workspaces (grown on demand)
     int ws_cap = 0;              // capacity in gates / CMUXes
@@ -129,6 +131,10 @@ int tfhe_ntt_setup(tfhe_ctx *ctx);
 int tfhe_make_twiddles(tfhe_ctx *ctx, int N, uint64_t **fwd, uint64_t **inv, uint64_t *n_inv);
 int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
                       cudaStream_t st);
+// CMUX selectors -> the two-prime NTT form read by tfhe_cmux_ntt and tfhe_ram_write_ntt
+// (same size as tfhe_trgsw_to_ntt's output: per TRGSW 2l * 2 * N words of 8 bytes)
+int tfhe_sel_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
+                    cudaStream_t st);
 int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                           cudaStream_t st);
 int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st);

@@ -71,6 +71,7 @@ extern "C" void tfhe_ctx_destroy(tfhe_ctx *ctx) {
     free_dev(ctx->ksk);
     free_dev(ctx->psi_fwd);
     free_dev(ctx->psi_inv);
+    free_dev(ctx->tw32);
     free_dev(ctx->ws_bar);
     free_dev(ctx->ws_acc);
     free_dev(ctx->ws_tmp);

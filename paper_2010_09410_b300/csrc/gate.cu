@@ -579,7 +579,7 @@ extern "C" int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group,
     if (form == TFHE_FORM_TC) return tfhe_cmux_tc(ctx, trgsw, g, st);
     rc = tfhe_ensure_trgsw_ws(ctx, (size_t)ny);
     if (rc != TFHE_OK) return rc;
-    rc = tfhe_trgsw_to_ntt(ctx, trgsw, ctx->ws_trgsw_ntt, (size_t)ny, st);
+    rc = tfhe_sel_to_ntt(ctx, trgsw, ctx->ws_trgsw_ntt, (size_t)ny, st);
     if (rc != TFHE_OK) return rc;
     return tfhe_cmux_ntt(ctx, ctx->ws_trgsw_ntt, g, st);
 }

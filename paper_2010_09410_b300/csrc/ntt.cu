@@ -8,6 +8,7 @@
 // P/2 in magnitude, so its residue mod P identifies the integer, which is then
 // reduced mod 2^32 (gl_lift_u32).
 #include "ntt.cuh"
+#include "ntt32.cuh"
 
 // ---------------------------------------------------------------------------
 // Host: twiddles
@@ -55,7 +56,9 @@ int tfhe_make_twiddles(tfhe_ctx *ctx, int N, uint64_t **fwd, uint64_t **inv, uin
 }
 
 int tfhe_ntt_setup(tfhe_ctx *ctx) {
-    return tfhe_make_twiddles(ctx, ctx->p.N, &ctx->psi_fwd, &ctx->psi_inv, &ctx->n_inv);
+    const int rc = tfhe_make_twiddles(ctx, ctx->p.N, &ctx->psi_fwd, &ctx->psi_inv, &ctx->n_inv);
+    if (rc != TFHE_OK) return rc;
+    return tfhe_make_twiddles32(ctx, ctx->p.N, &ctx->tw32);
 }
 
 // Polynomials (u32 words as integers in [0, 2^32)) -> NTT domain scaled by N^{-1}.
@@ -143,17 +146,86 @@ __global__ void __launch_bounds__(1024) k_blind_rotate_ntt(
     for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = acc[j];
 }
 
+// CMUX external products (tree reads, write bars, CMUX batches) use the two-prime NTT of
+// ntt32.cuh: selectors are kept as u32[2l][2][2 primes][N] residues of their NTT-domain
+// polynomials (Montgomery form, scaled by N^{-1}; tfhe_sel_to_ntt).  A product sum
+// sum_r d_r k_r with |d| <= Bg/2 and k < 2^32 over 2l rows of N terms is below
+// 2l N (Bg/2) 2^32 (2^49.6 at l = 3, N = 1024, Bg = 64) < P1 P2 / 2, so the CRT gives it
+// exactly and its residue mod 2^32 is taken.
+
+// prod (u32[2 primes][2][N], swizzled) receives the residues of C (.) d for the TRLWE d
+// (u32[2][N] in shared memory) and the selector `key`; dig is u32[2 primes][2l][N].
+__device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__restrict__ key,
+                                          uint32_t *dig, uint32_t *prod, int N, int logN, int l,
+                                          int Bgbit, const uint32_t *tw) {
+    const uint32_t off = gadget_offset(l, Bgbit);
+    const size_t dplane = (size_t)2 * l * N, pplane = (size_t)2 * N;
+    // digits, two consecutive coefficients per thread; rows c*l + q (a, then b)
+    for (int j = 2 * threadIdx.x; j < N; j += 2 * blockDim.x) {
+        for (int c = 0; c < 2; c++) {
+            const uint2 dv = *reinterpret_cast<const uint2 *>(d + (size_t)c * N + j);
+            const uint32_t u0 = dv.x + off, u1 = dv.y + off;
+            for (int q = 0; q < l; q++) {
+                const int32_t d0 = gadget_digit(u0, q + 1, Bgbit), d1 = gadget_digit(u1, q + 1, Bgbit);
+                const size_t row = (size_t)(c * l + q) * N + swz(j);
+                *reinterpret_cast<uint2 *>(dig + row) = make_uint2(res_of_i32(d0, NP1), res_of_i32(d1, NP1));
+                *reinterpret_cast<uint2 *>(dig + dplane + row) =
+                    make_uint2(res_of_i32(d0, NP2), res_of_i32(d1, NP2));
+            }
+        }
+    }
+    __syncthreads();
+    ntt32_fwd_r8(dig, 2 * l, N, logN, tw);
+    // pointwise, two consecutive coefficients per thread, Montgomery-reduced every 4 rows
+    for (int it = threadIdx.x; it < N; it += blockDim.x) {
+        const int pr = it >= (N >> 1);
+        const int k = 2 * (it - (pr ? (N >> 1) : 0));
+        const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
+        uint2 rs[2] = {make_uint2(0, 0), make_uint2(0, 0)};
+        uint64_t ta[2] = {0, 0}, tb[2] = {0, 0};
+#pragma unroll 6
+        for (int r = 0; r < 2 * l; r++) {
+            const uint2 dd = *reinterpret_cast<const uint2 *>(dig + pr * dplane + (size_t)r * N + swz(k));
+            const uint32_t d0 = red_below(dd.x, p), d1 = red_below(dd.y, p);
+            const uint32_t *kr = key + ((size_t)r * 4 + pr) * N + k;  // [r][column][prime][N]
+            const uint2 k0 = __ldg(reinterpret_cast<const uint2 *>(kr));
+            const uint2 k1 = __ldg(reinterpret_cast<const uint2 *>(kr + 2 * N));
+            ta[0] += (uint64_t)d0 * k0.x;
+            tb[0] += (uint64_t)d1 * k0.y;
+            ta[1] += (uint64_t)d0 * k1.x;
+            tb[1] += (uint64_t)d1 * k1.y;
+            if ((r & 3) == 3 || r == 2 * l - 1) {  // < 4 p^2 < p 2^32: reduce
+#pragma unroll
+                for (int o = 0; o < 2; o++) {
+                    rs[o].x = red_below(rs[o].x + redc32(ta[o], p, ninv), p2);
+                    rs[o].y = red_below(rs[o].y + redc32(tb[o], p, ninv), p2);
+                    ta[o] = tb[o] = 0;
+                }
+            }
+        }
+        *reinterpret_cast<uint2 *>(prod + pr * pplane + swz(k)) = rs[0];
+        *reinterpret_cast<uint2 *>(prod + pr * pplane + N + swz(k)) = rs[1];
+    }
+    __syncthreads();
+    ntt32_inv_r8(prod, 2, N, logN, tw);
+}
+
+// word j of polynomial c of the product, mod 2^32
+__device__ __forceinline__ uint32_t prod32_word(const uint32_t *prod, int N, int c, int j) {
+    const size_t o = (size_t)c * N + swz(j);
+    return (uint32_t)crt_centred(red_below(prod[o], NP1), red_below(prod[(size_t)2 * N + o], NP2));
+}
+
 // One block per CMUX (x, y) = (blockIdx.x, blockIdx.y) of the geometry g:
 // out = d0 + C_y (.) (d1 - d0).  out may alias d0 or d1 of the same CMUX.
 __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bgbit,
                                                   const uint64_t *__restrict__ sel, CmuxGeom g,
-                                                  const uint64_t *__restrict__ psi_f,
-                                                  const uint64_t *__restrict__ psi_i) {
-    extern __shared__ uint64_t sm[];
-    uint64_t *dig = sm;
-    uint64_t *prod = sm + (size_t)2 * l * N;
-    uint32_t *diff = (uint32_t *)(prod + (size_t)2 * N);
-    uint32_t *base = diff + 2 * N;
+                                                  const uint32_t *__restrict__ tw) {
+    extern __shared__ __align__(16) uint32_t smc[];
+    uint32_t *dig = smc;                          // [2][2l][N]
+    uint32_t *prod = dig + (size_t)2 * 2 * l * N;  // [2][2][N]
+    uint32_t *diff = prod + (size_t)4 * N;         // [2][N]
+    uint32_t *base = diff + 2 * N;                 // [2][N]
     const int64_t x = blockIdx.x, y = blockIdx.y;
     if (y * g.nx + x >= g.count) return;
     const uint32_t *a1 = g.d1 + x * g.dx + y * g.dy, *a0 = g.d0 + x * g.dx + y * g.dy;
@@ -163,10 +235,12 @@ __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bg
         diff[j] = a1[j] - x0;
     }
     __syncthreads();
-    const size_t per = (size_t)2 * l * 2 * N;
-    extprod_ntt(diff, sel + (size_t)y * g.sy * per, dig, prod, N, logN, l, Bgbit, psi_f, psi_i);
+    const size_t per = (size_t)2 * l * 2 * N;  // one selector, in u64 units
+    extprod32(diff, reinterpret_cast<const uint32_t *>(sel + (size_t)y * g.sy * per), dig, prod, N,
+              logN, l, Bgbit, tw);
     uint32_t *o = g.out + x * g.ox + y * g.oy;
-    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = base[j] + gl_lift_u32(prod[j]);
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
+        o[j] = base[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
 }
 
 // One block per RAM cell c (write bar, Section 8.2): r = new; for j < v:
@@ -176,12 +250,11 @@ __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, i
                                                        const uint64_t *__restrict__ gmc_ntt,
                                                        const uint32_t *__restrict__ new_cell,
                                                        uint32_t *cells,
-                                                       const uint64_t *__restrict__ psi_f,
-                                                       const uint64_t *__restrict__ psi_i) {
-    extern __shared__ uint64_t sm[];
-    uint64_t *dig = sm;
-    uint64_t *prod = sm + (size_t)2 * l * N;
-    uint32_t *diff = (uint32_t *)(prod + (size_t)2 * N);
+                                                       const uint32_t *__restrict__ tw) {
+    extern __shared__ __align__(16) uint32_t smc[];
+    uint32_t *dig = smc;
+    uint32_t *prod = dig + (size_t)2 * 2 * l * N;
+    uint32_t *diff = prod + (size_t)4 * N;
     uint32_t *r = diff + 2 * N;
     uint32_t *old = r + 2 * N;
     const size_t c = blockIdx.x;
@@ -196,11 +269,52 @@ __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, i
         for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) diff[j] = r[j] - old[j];
         __syncthreads();
         const uint64_t *S = (((c >> b) & 1) ? c_ntt : gmc_ntt) + (size_t)b * per;
-        extprod_ntt(diff, S, dig, prod, N, logN, l, Bgbit, psi_f, psi_i);
-        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) r[j] = old[j] + gl_lift_u32(prod[j]);
+        extprod32(diff, reinterpret_cast<const uint32_t *>(S), dig, prod, N, logN, l, Bgbit, tw);
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
+            r[j] = old[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
         __syncthreads();
     }
     for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) cell[j] = r[j];
+}
+
+// Polynomials (u32 words) -> the residues of their NTT-domain values mod both primes,
+// u32[poly][2 primes][N], Montgomery form, scaled by N^{-1} (f_p = N^{-1} 2^32 mod p).
+__global__ void k_polys_to_ntt32(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                 int N, int logN, const uint32_t *__restrict__ tw, uint32_t f1,
+                                 uint32_t f2) {
+    extern __shared__ uint32_t sp[];  // [2 primes][N]
+    const size_t poly = blockIdx.x;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint32_t w = src[poly * N + k];
+        sp[k] = w % NP1;
+        sp[N + k] = w % NP2;
+    }
+    __syncthreads();
+    ntt32_fwd(sp, 1, N, logN, tw);
+    for (int x = threadIdx.x; x < 2 * N; x += blockDim.x) {
+        const bool pr = x >= N;
+        const uint32_t p = pr ? NP2 : NP1;
+        dst[poly * 2 * N + x] = (uint32_t)((uint64_t)red_below(sp[x], p) * (pr ? f2 : f1) % p);
+    }
+}
+
+int tfhe_sel_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
+                    cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    const size_t polys = count * 2 * p.l * 2;
+    if (polys == 0) return TFHE_OK;
+    const uint32_t f1 = (uint32_t)((powmod64(p.N, NP1 - 2, NP1) << 32) % NP1);
+    const uint32_t f2 = (uint32_t)((powmod64(p.N, NP2 - 2, NP2) << 32) % NP2);
+    k_polys_to_ntt32<<<(unsigned)polys, 256, 2 * p.N * 4, st>>>(
+        trgsw, reinterpret_cast<uint32_t *>(out), p.N, ctx->logN, ctx->tw32, f1, f2);
+    return tfhe_check_launch(ctx, "polys_to_ntt32");
+}
+
+bool tfhe_cmux_exact(const tfhe_ctx *ctx) {
+    const tfhe_params &p = ctx->p;
+    int lg = 0;
+    while ((1 << lg) < 2 * p.l) lg++;
+    return lg + ctx->logN + p.Bgbit - 1 + 32 <= 58;  // 2l N (Bg/2) 2^32 <= 2^58 < P1 P2 / 2
 }
 
 int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t count,
@@ -236,20 +350,22 @@ int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int
 }
 
 static size_t cmux_smem(const tfhe_params &p) {
-    return (size_t)2 * p.l * p.N * 8 + (size_t)2 * p.N * 8 + (size_t)6 * p.N * 4;
+    // digits and products for both primes, difference and base (or r and old) polynomials
+    return (size_t)2 * 2 * p.l * p.N * 4 + (size_t)4 * p.N * 4 + (size_t)4 * p.N * 4;
 }
 
 int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
     if (g.count == 0) return TFHE_OK;
+    if (!tfhe_cmux_exact(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "CMUX: 2l N Bg/2 2^32 exceeds the NTT bound");
     const size_t smem = cmux_smem(p);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_cmux_ntt,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
     dim3 grid(g.nx, g.ny);
     StageTimer tm(ctx, TFHE_STAGE_CMUX, st);
-    k_cmux_ntt<<<grid, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, sel_ntt, g, ctx->psi_fwd,
-                                        ctx->psi_inv);
+    k_cmux_ntt<<<grid, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, sel_ntt, g, ctx->tw32);
     tm.stop();
     return tfhe_check_launch(ctx, "cmux_ntt");
 }
@@ -257,13 +373,15 @@ int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cud
 int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
                        const uint32_t *new_cell, uint32_t *cells, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
+    if (!tfhe_cmux_exact(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "RAM write: 2l N Bg/2 2^32 exceeds the NTT bound");
     const size_t smem = cmux_smem(p) + (size_t)2 * p.N * 4;
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_ram_write_ntt,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
     StageTimer tm(ctx, TFHE_STAGE_CMUX, st);
     k_ram_write_ntt<<<1u << v, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, v, c_ntt, gmc_ntt,
-                                               new_cell, cells, ctx->psi_fwd, ctx->psi_inv);
+                                               new_cell, cells, ctx->tw32);
     tm.stop();
     return tfhe_check_launch(ctx, "ram_write_ntt");
 }
