@@ -82,7 +82,12 @@ enum {
  *     with the key split into byte planes (exact in bf16, fp32 accumulation kept
  *     below 2^24, recombined mod 2^32).  Needs N = 1024 and 2l * Bgbit fitting the
  *     exactness budget; otherwise the call returns TFHE_EUNSUPPORTED. */
-enum { TFHE_FORM_NTT = 0, TFHE_FORM_TC = 1 };
+enum { TFHE_FORM_NTT = 0, TFHE_FORM_TC = 1, TFHE_FORM_NTT2 = 2 };
+/*   TFHE_FORM_NTT2: one thread block per gate like TFHE_FORM_NTT, with each external
+ *     product computed by NTTs modulo the two 30-bit primes 998244353 and 754974721 in
+ *     32-bit lanes and recombined by the Chinese remainder theorem (exact while
+ *     2l N (Bg/2) 2^32 <= 2^58, else TFHE_EUNSUPPORTED).  The fastest form for narrow
+ *     levels; the CMUX batches, trees and RAM writes always use this arithmetic. */
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int tfhe_version(void);
@@ -183,7 +188,7 @@ int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches);
  *          a bad type or index gives that gate an all-zero output and records
  *          TFHE_EINVAL in the device error word (see tfhe_ctx_sync)
  * out:     device u32[G][n+1]; must not overlap rows of `in` read by this call
- * form:    TFHE_FORM_NTT or TFHE_FORM_TC
+ * form:    TFHE_FORM_NTT, TFHE_FORM_TC or TFHE_FORM_NTT2
  * Each gate: linear combination, ModSwitch to Z_2N, BlindRotate of the test vector
  * (n CMUXes against BSK), SampleExtract, identity key switch. */
 int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
@@ -251,9 +256,10 @@ int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, in
  * C_k = trgsw + (k / group) * (2l * 2 * N) -- consecutive runs of `group` CMUXes
  * share one TRGSW selector.  d1, d0, out: device u32[B][2][N]; out may alias d0 or
  * d1 (same k only).  trgsw: device u32[ceil(B / group)][2l][2][N].
- * CMUX batches, trees and RAM writes run in the NTT form: form must be TFHE_FORM_NTT;
- * TFHE_FORM_TC returns TFHE_EUNSUPPORTED (the tensor-core form covers the BlindRotate
- * of gate batches, whose key is shared by the whole batch). */
+ * CMUX batches, trees and RAM writes run in the NTT form (the two-prime arithmetic of
+ * TFHE_FORM_NTT2): form TFHE_FORM_NTT or TFHE_FORM_NTT2; TFHE_FORM_TC returns
+ * TFHE_EUNSUPPORTED (the tensor-core form covers the BlindRotate of gate batches, whose
+ * key is shared by the whole batch). */
 int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint32_t *d1,
                     const uint32_t *d0, uint32_t *out, int B, int form, void *stream);
 

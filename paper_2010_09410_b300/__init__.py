@@ -22,6 +22,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPO
           -6: "ENOKEYS"}
 FORM_NTT = 0
 FORM_TC = 1
+FORM_NTT2 = 2
 FORM_AUTO = -1
 TC_SINGLE_SM = 0
 TC_SM_PAIR = 1

@@ -28,7 +28,7 @@ __global__ void k_gadget_minus(const uint32_t *__restrict__ c, uint32_t *__restr
 
 static int check_common(tfhe_ctx *ctx, int v, int form) {
     if (v < 1 || v > 16) return tfhe_set_error(ctx, TFHE_EINVAL, "v must be in 1..16");
-    if (form != TFHE_FORM_NTT && form != TFHE_FORM_TC)
+    if (form != TFHE_FORM_NTT && form != TFHE_FORM_TC && form != TFHE_FORM_NTT2)
         return tfhe_set_error(ctx, TFHE_EINVAL, "unknown form");
     if (form == TFHE_FORM_TC && !tfhe_tc_supported(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form not supported here");
@@ -56,7 +56,7 @@ extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
     rc = tfhe_ensure_workspace(ctx, R * M0);
     if (rc != TFHE_OK) return rc;
     const uint64_t *sel_ntt = nullptr;
-    if (form == TFHE_FORM_NTT) {
+    if (form != TFHE_FORM_TC) {
         rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
         if (rc != TFHE_OK) return rc;
         rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
@@ -71,7 +71,7 @@ extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
         uint32_t *o = (j == v - 1) ? out : buf[j & 1];
         CmuxGeom g{in + N2, in, o, 2 * N2, in_ystride, N2, (int64_t)M * N2, (int64_t)v,
                    M, R, (int64_t)R * M};
-        if (form == TFHE_FORM_NTT)
+        if (form != TFHE_FORM_TC)
             rc = tfhe_cmux_ntt(ctx, sel_ntt + (size_t)j * per, g, st);
         else
             rc = tfhe_cmux_tc(ctx, addr_trgsw + (size_t)j * per, g, st);

@@ -32,6 +32,7 @@ struct tfhe_ctx {
     uint64_t *bsk_ntt = nullptr;  // [n][2l][2][N] NTT domain (bit-reversed), scaled by N^-1
     uint32_t *bsk_raw = nullptr;  // [n][2l][2][N] as given
     uint32_t *ksk = nullptr;      // [N][t][base - 1][n_pad], rows v = 1..base-1
+    uint32_t *bsk_ntt2 = nullptr; // [n][2l][2][2 primes][N] two-prime NTT form (TFHE_FORM_NTT2)
 
     // NTT twiddles: psi^{brv(k)} and psi^{-brv(k)}, psi a primitive 2N-th root of unity
     uint64_t *psi_fwd = nullptr;
@@ -137,6 +138,10 @@ int tfhe_sel_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_t 
                     cudaStream_t st);
 int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                           cudaStream_t st);
+int tfhe_blind_rotate_ntt2(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                           cudaStream_t st);
+// products of the CMUX / two-prime forms are exact for these parameters
+bool tfhe_cmux_exact(const tfhe_ctx *ctx);
 int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st);
 int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
                        const uint32_t *new_cell, uint32_t *cells, cudaStream_t st);

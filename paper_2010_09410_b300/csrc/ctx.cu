@@ -68,6 +68,7 @@ extern "C" void tfhe_ctx_destroy(tfhe_ctx *ctx) {
     tfhe_tc_free(ctx);
     free_dev(ctx->bsk_ntt);
     free_dev(ctx->bsk_raw);
+    free_dev(ctx->bsk_ntt2);
     free_dev(ctx->ksk);
     free_dev(ctx->psi_fwd);
     free_dev(ctx->psi_inv);
@@ -131,6 +132,12 @@ extern "C" int tfhe_ctx_set_keys(tfhe_ctx *ctx, const uint32_t *bsk, const uint3
                                        cudaMemcpyDeviceToDevice, st));
     int rc = tfhe_trgsw_to_ntt(ctx, bsk, ctx->bsk_ntt, (size_t)p.n, st);
     if (rc != TFHE_OK) return rc;
+    if (tfhe_cmux_exact(ctx)) {  // BSK in the two-prime NTT form (TFHE_FORM_NTT2)
+        if (!ctx->bsk_ntt2 && cudaMalloc(&ctx->bsk_ntt2, bsk_words * 8) != cudaSuccess)
+            return tfhe_set_error(ctx, TFHE_ENOMEM, "set_keys: two-prime NTT-domain BSK");
+        rc = tfhe_sel_to_ntt(ctx, bsk, reinterpret_cast<uint64_t *>(ctx->bsk_ntt2), (size_t)p.n, st);
+        if (rc != TFHE_OK) return rc;
+    }
     k_ksk_relayout<<<4096, 256, 0, st>>>(ksk, ctx->ksk, p.N, p.ks_t, base, p.n + 1, ctx->n_pad);
     rc = tfhe_check_launch(ctx, "ksk relayout");
     if (rc != TFHE_OK) return rc;

@@ -480,6 +480,12 @@ static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t
 
 static int check_form(tfhe_ctx *ctx, int form) {
     if (form == TFHE_FORM_NTT) return TFHE_OK;
+    if (form == TFHE_FORM_NTT2) {
+        if (!tfhe_cmux_exact(ctx) || !ctx->bsk_ntt2)
+            return tfhe_set_error(ctx, TFHE_EUNSUPPORTED,
+                                  "two-prime NTT form needs 2l N Bg/2 2^32 <= 2^58");
+        return TFHE_OK;
+    }
     if (form == TFHE_FORM_TC) {
         if (!tfhe_tc_supported(ctx))
             return tfhe_set_error(ctx, TFHE_EUNSUPPORTED,
@@ -493,6 +499,7 @@ static int check_form(tfhe_ctx *ctx, int form) {
 static int blind_rotate_dispatch(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                                  int form, cudaStream_t st, int tc_level = -1) {
     if (form == TFHE_FORM_TC) return tfhe_blind_rotate_tc(ctx, bar, acc, G, st, tc_level);
+    if (form == TFHE_FORM_NTT2) return tfhe_blind_rotate_ntt2(ctx, bar, acc, G, st);
     return tfhe_blind_rotate_ntt(ctx, bar, acc, G, st);
 }
 

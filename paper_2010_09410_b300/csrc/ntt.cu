@@ -243,6 +243,50 @@ __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bg
         o[j] = base[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
 }
 
+// Per-gate BlindRotate in the two-prime NTT form (TFHE_FORM_NTT2): as k_blind_rotate_ntt,
+// with each external product computed by extprod32 against the BSK in the two-prime NTT
+// form (u32[n][2l][2][2 primes][N]).  Shared memory: digits, products, accumulator,
+// rotation difference and the twiddle table (112 KB at N = 1024, l = 3).
+__global__ void __launch_bounds__(1024) k_blind_rotate_ntt2(
+    int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
+    uint32_t *__restrict__ acc_out, const uint32_t *__restrict__ bsk2p,
+    const uint32_t *__restrict__ tw) {
+    extern __shared__ __align__(16) uint32_t smb[];
+    uint32_t *dig = smb;                          // [2][2l][N]
+    uint32_t *prod = dig + (size_t)4 * l * N;      // [2][2][N]
+    uint32_t *acc = prod + (size_t)4 * N;          // [2][N]
+    uint32_t *diff = acc + 2 * N;                  // [2][N]
+    uint32_t *tws = diff + 2 * N;                  // [2][4][N]
+    for (int x = threadIdx.x; x < 2 * N; x += blockDim.x)
+        reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
+    const size_t g = blockIdx.x;
+    const uint32_t *mb = bar + g * (n + 1);
+    const uint32_t mu = 1u << 29;
+    const int M = 2 * N;
+    const int bb = (int)(mb[n] % (uint32_t)M);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        acc[j] = 0;
+        acc[N + j] = ((j + bb) % M) < N ? mu : 0u - mu;
+    }
+    __syncthreads();
+    const size_t per = (size_t)2 * l * 2 * 2 * N;  // words of one BSK_i
+    for (int i = 0; i < n; i++) {
+        const int a = (int)(mb[i] % (uint32_t)M);
+        if (a == 0) continue;  // X^0 ACC - ACC = 0 has all-zero digits: the step is the identity
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            diff[j] = rot_coef(acc, N, a, j) - acc[j];
+            diff[N + j] = rot_coef(acc + N, N, a, j) - acc[N + j];
+        }
+        __syncthreads();
+        extprod32(diff, bsk2p + (size_t)i * per, dig, prod, N, logN, l, Bgbit, tws);
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
+            acc[j] += prod32_word(prod, N, j >= N, j >= N ? j - N : j);
+        __syncthreads();
+    }
+    uint32_t *o = acc_out + g * 2 * N;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = acc[j];
+}
+
 // One block per RAM cell c (write bar, Section 8.2): r = new; for j < v:
 // r = CMUX(S_j, r, cell_c) with S_j = C_j when bit j of c is 1 and G - C_j otherwise.
 __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, int Bgbit, int v,
@@ -347,6 +391,28 @@ int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int
                                                  ctx->bsk_ntt, ctx->psi_fwd, ctx->psi_inv);
     tm.stop();
     return tfhe_check_launch(ctx, "blind_rotate_ntt");
+}
+
+int tfhe_blind_rotate_ntt2(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                           cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (G == 0) return TFHE_OK;
+    if (!ctx->bsk_ntt2)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "two-prime NTT form not available here");
+    const size_t smem = ((size_t)4 * p.l * p.N + (size_t)16 * p.N) * 4;
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt2,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    if (!ctx->sms)
+        TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount,
+                                                  ctx->device));
+    // one block per SM of 1024 threads while there are SMs to spare, else two of 512
+    const int threads = G <= ctx->sms ? 1024 : 512;
+    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_NTT, st);
+    k_blind_rotate_ntt2<<<G, threads, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar, acc,
+                                                  ctx->bsk_ntt2, ctx->tw32);
+    tm.stop();
+    return tfhe_check_launch(ctx, "blind_rotate_ntt2");
 }
 
 static size_t cmux_smem(const tfhe_params &p) {

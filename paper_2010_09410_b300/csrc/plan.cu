@@ -53,13 +53,18 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
 
 // Form and Karatsuba level for a level of `width` gates when the caller lets the plan
 // choose (form = -1).  After tfhe_ctx_autotune: the measured winner at the nearest tuned
-// width (log scale).  Before: a rule from a B300 sweep at N = 1024 (per-level ms, 630
-// steps): the NTT form is faster up to about 300 gates (30-39 ms, one block per gate),
-// Karatsuba level 1 from there to about 2,500 gates (49-75 ms), level 2 beyond.
+// width (log scale).  Before: a rule from a B300 sweep at N = 1024, n = 630 (ms per
+// level; NTT / two-prime NTT / tensor core L1 / L2): 64 gates 18.8 / 10.2 / 41.6 / 38.7;
+// 256: 34.0 / 16.7 / 44.8 / 44.8; 768: 94.6 / 44.7 / 46.6 / 49.7; 1024: 110 / 51.8 /
+// 48.8 / 52.1; 2048: 216 / 101 / 71.0 / 67.6; 4096: 428 / 200 / 137 / 120.  So the
+// two-prime per-gate form up to about 900 gates, Karatsuba level 1 to about 2,000,
+// level 2 beyond (the per-gate NTT form over 2^64 - 2^32 + 1 when the two-prime form
+// is not available: up to about 400 gates).
 static void plan_pick(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
     *level = -1;
+    const int ntt = ctx->bsk_ntt2 ? TFHE_FORM_NTT2 : TFHE_FORM_NTT;  // the faster per-gate form
     if (!tfhe_tc_supported(ctx)) {
-        *form = TFHE_FORM_NTT;
+        *form = ntt;
         return;
     }
     if (!ctx->tune.empty()) {
@@ -76,13 +81,13 @@ static void plan_pick(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
         *level = best->level;
         return;
     }
-    if (width < 384) {
-        *form = TFHE_FORM_NTT;
+    if (width < (ctx->bsk_ntt2 ? 896 : 384)) {
+        *form = ntt;
         return;
     }
     *form = TFHE_FORM_TC;
     const int L = tfhe_tc_level(ctx);
-    *level = (width < 2560 && L > 1) ? 1 : L;
+    *level = (width < 2048 && L > 1) ? 1 : L;
 }
 
 // Size the context's workspaces for every level of the plan (a later call of another
@@ -106,8 +111,10 @@ extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, in
     *out = nullptr;
     if (!circuits || num_circuits < 1)
         return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: no circuits");
-    if (form != -1 && form != TFHE_FORM_NTT && form != TFHE_FORM_TC)
+    if (form != -1 && form != TFHE_FORM_NTT && form != TFHE_FORM_TC && form != TFHE_FORM_NTT2)
         return tfhe_set_error(ctx, TFHE_EINVAL, "circuit_plan: unknown form");
+    if (form == TFHE_FORM_NTT2 && !ctx->bsk_ntt2)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "circuit_plan: two-prime NTT form unsupported");
     if (form == TFHE_FORM_TC && !tfhe_tc_supported(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "circuit_plan: tensor-core form unsupported");
     // levels per gate: level(g) = 1 + max(level of its input wires), primaries at -1
@@ -342,8 +349,9 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream) {
         k_tune_inputs<<<256, 256, 0, st>>>(in, 2 * (size_t)max_gates * w1, types, idx, max_gates);
         rc = tfhe_check_launch(ctx, "tune_inputs");
     }
-    // candidates: the NTT form, and the tensor-core form at every supported level
+    // candidates: the per-gate NTT forms, and the tensor-core form at every supported level
     std::vector<std::pair<int, int>> cand = {{TFHE_FORM_NTT, -1}};
+    if (ctx->bsk_ntt2) cand.push_back({TFHE_FORM_NTT2, -1});
     if (tfhe_tc_supported(ctx))
         for (int L = 0; L <= 2; L++)
             if (tfhe_tc_ensure_level(ctx, L, st) == TFHE_OK) cand.push_back({TFHE_FORM_TC, L});
@@ -378,7 +386,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream) {
         // form's per-gate cost falls as its tiles fill, so only the NTT form's standing
         // can only get worse at larger widths
         for (size_t ci = 0; ci < cand.size(); ci++)
-            if (cand[ci].first == TFHE_FORM_NTT && ms[ci] > 2 * best.ms) alive[ci] = false;
+            if (cand[ci].first != TFHE_FORM_TC && ms[ci] > 2 * best.ms) alive[ci] = false;
         table.push_back(best);
     }
     if (rc == TFHE_OK) rc = tfhe_ctx_sync(ctx, stream);

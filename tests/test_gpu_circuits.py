@@ -133,24 +133,24 @@ def test_16_mixed_circuits_interleaved(torch_cuda):
 def test_autotuned_plan_matches_fixed_forms(torch_cuda):
     """The autotuner's table covers the width ladder with valid choices, and a plan that
     follows it (per-level form and Karatsuba level) gives the same words as plans fixed
-    to the NTT form and to the tensor-core form."""
+    to each form."""
     torch = torch_cuda
     p = ti.STD
     ctx, k = gpu_context(p, ti.SEED_FLAT)
     table = ctx.autotune(512)
     assert [w for w, _, _, _ in table] == [64, 128, 256, 512]
     for w, form, level, ms in table:
-        assert form in (0, 1) and ms > 0
-        assert (form == 0 and level == -1) or (form == 1 and level in (0, 1, 2))
+        assert form in (0, 1, 2) and ms > 0
+        assert (form in (0, 2) and level == -1) or (form == 1 and level in (0, 1, 2))
     c = ti.layered_dag(ti.SEED_DAG, total=2400, levels=6, num_inputs=256, lo=50, hi=800, stream=7)
     bits = ti.random_bits(ti.SEED_DAG, 990, c.num_inputs)
     dev_in = to_dev(ti.encrypt_tlwe0_bits(p, ti.SEED_DAG, 991, k.s0, bits))
     outs = []
-    for form in (-1, 0, 1):
+    for form in (-1, 0, 1, 2):
         plan = ctx.plan([c], form)
         out = torch.zeros((c.num_gates, p.n + 1), dtype=torch.int32, device="cuda")
         plan.run(dev_in, out)
         ctx.sync()
         outs.append(from_dev(out))
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
     assert np.array_equal(orc.tlwe_decrypt(k.s0, outs[0]), plain_eval(c, bits))

@@ -8,7 +8,7 @@ from conftest import from_dev, gpu_context, to_dev
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [0]
+FORMS = [0, 2]
 
 
 @pytest.mark.parametrize("form", FORMS)

@@ -20,7 +20,7 @@ def oracle_circuit(p, k, c, inp):
     return wires[c.num_inputs:]
 
 
-@pytest.mark.parametrize("form", [-1, 0])
+@pytest.mark.parametrize("form", [-1, 0, 2])
 def test_toy_dag_matches_oracle(torch_cuda, form):
     import paper_2010_09410_b300 as tb
     p = ti.TOY
