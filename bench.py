@@ -375,6 +375,9 @@ def kernel_traffic(key, src):
 def roofline(form, r, G, p, tc_level):
     """Roofline of the dominant kernel of the measured form.
 
+    Two-prime NTT form: k_blind_rotate_ntt2, the same transforms and products modulo two
+    30-bit primes; each 32-bit modular multiply counted as 3 32-bit multiplies (Shoup).
+
     NTT form: k_blind_rotate_ntt, bound by integer ALU throughput.  Algorithmic work per
     gate and BlindRotate step: 2l forward and 2 inverse N-point NTTs (N/2 log2 N
     butterflies each, one modular multiply per butterfly) and 4lN pointwise products:
@@ -394,6 +397,17 @@ def roofline(form, r, G, p, tc_level):
     mp, kind = peaks()
     logN = p.N.bit_length() - 1
     steps = p.n  # every step counted (a zero rotation, probability 1/2N, is skipped)
+    if form == "ntt2":
+        ms, launches = r["stages"]["blind_rotate_ntt"]
+        per_launch_s = ms / 1e3 / max(launches, 1)
+        mulmods = 2 * ((2 * p.l + 2) * (p.N // 2) * logN + 4 * p.l * p.N)  # both primes
+        ops = G * steps * mulmods * 3
+        achieved = ops / per_launch_s / 1e12
+        peak = 148 * 128 * mp.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        return {"bound": "alu", "kernel": "k_blind_rotate_ntt2", "achieved": achieved,
+                "peak": peak, "unit": "T int32-mul-op/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": "derived from SM count, lanes and max clock",
+                "work": f"{mulmods} 32-bit mulmods/gate-step (two primes) x 3 int32 multiplies"}
     if form == "ntt":
         ms, launches = r["stages"]["blind_rotate_ntt"]
         per_launch_s = ms / 1e3 / max(launches, 1)
