@@ -586,7 +586,8 @@ def run_other(args):
         cells0 = dev(rc.cells)
         cells = cells0.clone()
         rdata = torch.zeros((w, p.n + 1), dtype=torch.int32, device="cuda")
-        form = tb.FORM_TC if args.form != "ntt" else tb.FORM_NTT
+        # best: each bootstrap batch takes the form chosen for its width
+        form = {"best": -1, "ntt": tb.FORM_NTT, "ntt2": tb.FORM_NTT2, "tc": tb.FORM_TC}[args.form]
 
         def step():
             cells.copy_(cells0)
@@ -602,7 +603,7 @@ def run_other(args):
               (got[:, :p.n].astype(np.int64) * k.s0.astype(np.int64)).sum(1)) & 0xFFFFFFFF
         extra["decrypt_ok"] = bool(np.array_equal((ph < (1 << 31)).astype(np.uint8),
                                                   rc.cell_bits[:, rc.addr]))
-        extra["form"] = "tc" if form == tb.FORM_TC else "ntt"
+        extra["form"] = {-1: "auto per batch width", 0: "ntt", 1: "tc", 2: "ntt2"}[form]
     elif args.workload == "mux":
         G = 2048
         bits = ti.random_bits(seed, 60, 3 * G)

@@ -375,7 +375,10 @@ int tfhe_rom_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *tab
  * bit) gives the controlled data; each block's write bar takes it at the address; every
  * cell is refreshed by SampleExtract, key switching, ModSwitch and BlindRotate.  The
  * CMUX steps run in the NTT form; `form` selects the BlindRotate form of the MUX and
- * refresh bootstraps (w * 2^v + 2w bootstraps per cycle).  w * 2^v <= 2^24. */
+ * refresh bootstraps (w * 2^v + 2w bootstraps per cycle), or -1 to let each of the two
+ * bootstrap batches take the form chosen for its width (tfhe_ctx_autotune's table when
+ * present, else the level scheduler's fixed rule: e.g. the two-prime form for the 2w MUX
+ * bootstraps and the tensor-core form for the 4096 refreshes).  w * 2^v <= 2^24. */
 int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, int w, const uint32_t *flag,
                    const uint32_t *wdata, uint32_t *cells, uint32_t *rdata, int form, void *stream);
 

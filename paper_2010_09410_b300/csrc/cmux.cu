@@ -139,8 +139,14 @@ extern "C" int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, 
                               const uint32_t *flag, const uint32_t *wdata, uint32_t *cells,
                               uint32_t *rdata, int form, void *stream) {
     if (!ctx) return TFHE_EINVAL;
-    int rc = check_common(ctx, v, form);
+    int rc = check_common(ctx, v, form == -1 ? TFHE_FORM_NTT : form);
     if (rc != TFHE_OK) return rc;
+    // form -1: each bootstrap batch takes the form chosen for its width
+    int form_mux = form, form_refresh = form, lv = -1;
+    if (form == -1) {
+        tfhe_pick_form(ctx, 2 * (int64_t)w, &form_mux, &lv);
+        tfhe_pick_form(ctx, (int64_t)w << v, &form_refresh, &lv);
+    }
     if (w < 1 || ((int64_t)w << v) > (1 << 24))
         return tfhe_set_error(ctx, TFHE_EINVAL, "ram_cycle: w must be >= 1 and w * 2^v <= 2^24");
     if (!addr_trgsw || !flag || !wdata || !cells || !rdata)
@@ -210,18 +216,18 @@ extern "C" int tfhe_ram_cycle(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, 
                                        cudaMemcpyDeviceToDevice, st));
     k_ram_mux_idx<<<(w + 127) / 128, 128, 0, st>>>(w, idx3);
     rc = tfhe_check_launch(ctx, "ram_mux_idx");
-    if (rc == TFHE_OK) rc = tfhe_mux_batch_impl(ctx, min, 1 + 2 * (int64_t)w, idx3, S + o_ctl, w, form,
-                                                true, st);
+    if (rc == TFHE_OK) rc = tfhe_mux_batch_impl(ctx, min, 1 + 2 * (int64_t)w, idx3, S + o_ctl, w,
+                                                form_mux, true, st);
     if (rc != TFHE_OK) return rc;
-    // write unit: each block's write bar selects the controlled data at the address ...
-    for (int b = 0; b < w && rc == TFHE_OK; b++)
-        rc = tfhe_ram_write_ntt(ctx, c_ntt, gmc_ntt, v, S + o_ctl + (size_t)b * N2,
-                                cells + ((size_t)b << v) * N2, st);
+    // write unit: each block's write bar selects the controlled data at the address (one
+    // launch over all w blocks) ...
+    rc = tfhe_ram_write_ntt(ctx, c_ntt, gmc_ntt, v, S + o_ctl, cells, st, w, (int64_t)N2);
     if (rc != TFHE_OK) return rc;
     // ... and every cell is refreshed: SE, IKS, ModSwitch, BlindRotate back to a TRLWE
     rc = tfhe_launch_extract_keyswitch(ctx, cells, S + o_l0, (int)cells_n, nullptr, nullptr, 0, st);
     if (rc == TFHE_OK) rc = tfhe_launch_modswitch_rows(ctx, S + o_l0, S + o_bar, cells_n, st);
-    if (rc == TFHE_OK) rc = tfhe_blind_rotate_form(ctx, S + o_bar, cells, (int)cells_n, form, st);
+    if (rc == TFHE_OK)
+        rc = tfhe_blind_rotate_form(ctx, S + o_bar, cells, (int)cells_n, form_refresh, st);
     return rc;
 }
 

@@ -143,8 +143,11 @@ int tfhe_blind_rotate_ntt2(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, in
 // products of the CMUX / two-prime forms are exact for these parameters
 bool tfhe_cmux_exact(const tfhe_ctx *ctx);
 int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cudaStream_t st);
+// write bars of `blocks` RAM bit blocks of 2^v cells each: block b takes new_cell +
+// b * new_stride and updates cells + b * 2^v * 2N (words)
 int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
-                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st);
+                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st,
+                       int blocks = 1, int64_t new_stride = 0);
 
 // tc.cu
 int tfhe_tc_supported(const tfhe_ctx *ctx);
@@ -175,6 +178,9 @@ int tfhe_launch_modswitch_rows(tfhe_ctx *ctx, const uint32_t *in, uint32_t *bar,
                                cudaStream_t st);
 int tfhe_blind_rotate_form(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
                            cudaStream_t st);
+// plan.cu: the form (and Karatsuba level, -1 for the context's) a batch of `width` gates
+// runs in when the caller lets the library choose: the autotuner's table, else a fixed rule
+void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level);
 // gate.cu: tfhe_gate_batch with the tensor-core Karatsuba level chosen per call (-1: the
 // context's level)
 int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,

@@ -289,11 +289,13 @@ __global__ void __launch_bounds__(1024) k_blind_rotate_ntt2(
 
 // One block per RAM cell c (write bar, Section 8.2): r = new; for j < v:
 // r = CMUX(S_j, r, cell_c) with S_j = C_j when bit j of c is 1 and G - C_j otherwise.
+// blockIdx.y is the bit block: its controlled data is new_cell + y * new_stride and its
+// cells start at cells + y * 2^v * 2N.
 __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, int Bgbit, int v,
                                                        const uint64_t *__restrict__ c_ntt,
                                                        const uint64_t *__restrict__ gmc_ntt,
                                                        const uint32_t *__restrict__ new_cell,
-                                                       uint32_t *cells,
+                                                       int64_t new_stride, uint32_t *cells,
                                                        const uint32_t *__restrict__ tw) {
     extern __shared__ __align__(16) uint32_t smc[];
     uint32_t *dig = smc;
@@ -302,9 +304,10 @@ __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, i
     uint32_t *r = diff + 2 * N;
     uint32_t *old = r + 2 * N;
     const size_t c = blockIdx.x;
-    uint32_t *cell = cells + c * 2 * N;
+    uint32_t *cell = cells + (((size_t)blockIdx.y << v) + c) * 2 * N;
+    const uint32_t *nc = new_cell + (size_t)blockIdx.y * new_stride;
     for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
-        r[j] = new_cell[j];
+        r[j] = nc[j];
         old[j] = cell[j];
     }
     __syncthreads();
@@ -437,7 +440,8 @@ int tfhe_cmux_ntt(tfhe_ctx *ctx, const uint64_t *sel_ntt, const CmuxGeom &g, cud
 }
 
 int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc_ntt, int v,
-                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st) {
+                       const uint32_t *new_cell, uint32_t *cells, cudaStream_t st, int blocks,
+                       int64_t new_stride) {
     const tfhe_params &p = ctx->p;
     if (!tfhe_cmux_exact(ctx))
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "RAM write: 2l N Bg/2 2^32 exceeds the NTT bound");
@@ -446,8 +450,9 @@ int tfhe_ram_write_ntt(tfhe_ctx *ctx, const uint64_t *c_ntt, const uint64_t *gmc
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
     StageTimer tm(ctx, TFHE_STAGE_CMUX, st);
-    k_ram_write_ntt<<<1u << v, 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, v, c_ntt, gmc_ntt,
-                                               new_cell, cells, ctx->tw32);
+    k_ram_write_ntt<<<dim3(1u << v, blocks), 256, smem, st>>>(p.N, ctx->logN, p.l, p.Bgbit, v, c_ntt,
+                                                            gmc_ntt, new_cell, new_stride, cells,
+                                                            ctx->tw32);
     tm.stop();
     return tfhe_check_launch(ctx, "ram_write_ntt");
 }

@@ -60,7 +60,7 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
 // two-prime per-gate form up to about 900 gates, Karatsuba level 1 to about 2,000,
 // level 2 beyond (the per-gate NTT form over 2^64 - 2^32 + 1 when the two-prime form
 // is not available: up to about 400 gates).
-static void plan_pick(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
+void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
     *level = -1;
     const int ntt = ctx->bsk_ntt2 ? TFHE_FORM_NTT2 : TFHE_FORM_NTT;  // the faster per-gate form
     if (!tfhe_tc_supported(ctx)) {
@@ -195,7 +195,7 @@ extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, in
     for (int L = 0; L < num_levels; L++) {
         const int64_t w = plan->level_off[L + 1] - plan->level_off[L];
         max_w = std::max(max_w, w);
-        if (form == -1) plan_pick(ctx, w, &plan->level_form[L], &plan->level_tc[L]);
+        if (form == -1) tfhe_pick_form(ctx, w, &plan->level_form[L], &plan->level_tc[L]);
     }
     const size_t wb = (size_t)ctx->p.n + 1;
     if (cudaSetDevice(ctx->device) != cudaSuccess ||

@@ -19,7 +19,7 @@ def run_cycle(torch, ctx, p, rc, v, form):
     return from_dev(rdata), from_dev(cells)
 
 
-@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2, -1])
 @pytest.mark.parametrize("flag_bit,stream", [(0, 11), (1, 12)])
 def test_ram_cycle_toy_bit_exact(torch_cuda, form, flag_bit, stream):
     p, v, w = ti.TOY, 3, 3
