@@ -188,7 +188,9 @@ int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches);
  *          a bad type or index gives that gate an all-zero output and records
  *          TFHE_EINVAL in the device error word (see tfhe_ctx_sync)
  * out:     device u32[G][n+1]; must not overlap rows of `in` read by this call
- * form:    TFHE_FORM_NTT, TFHE_FORM_TC or TFHE_FORM_NTT2
+ * form:    TFHE_FORM_NTT, TFHE_FORM_TC, TFHE_FORM_NTT2, or -1 for the form (and Karatsuba
+ *          level) chosen for the batch width: tfhe_ctx_autotune's table when present, else
+ *          the level scheduler's fixed rule (the two-prime form below about 900 gates)
  * Each gate: linear combination, ModSwitch to Z_2N, BlindRotate of the test vector
  * (n CMUXes against BSK), SampleExtract, identity key switch. */
 int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
@@ -201,7 +203,8 @@ int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uin
  * AND third), whose TRLWEs are summed with (0, 1/8 X^0); tfhe_mux_batch then applies
  * SampleExtract and the identity key switch (out: device u32[G][n+1] TLWE lvl0), while
  * tfhe_mux_batch_noks returns the summed TRLWE (out_trlwe: device u32[G][2][N]).
- * in: device u32[num_in][n+1]; idx3: device int32[G][3]; form as for tfhe_gate_batch.
+ * in: device u32[num_in][n+1]; idx3: device int32[G][3]; form as for tfhe_gate_batch
+ * (-1 chooses by the width 2G).
  * Host-detectable errors return before launch; a MUX with an index outside
  * [0, num_in) gets an all-zero output and TFHE_EINVAL at the next tfhe_ctx_sync.
  * Asynchronous on `stream`; workspaces for 2G bootstraps are grown as needed. */
@@ -247,6 +250,7 @@ int tfhe_gate_batch_noalloc(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
  *   tfhe_extract_keyswitch: acc device u32[G][2][N] -> out device u32[G][n+1]:
  *     SampleExtract of coefficient 0 and identity key switch (Section 2.1.2
  *     "Sample Extraction and Identity Key Switching"). */
+/* (form as for tfhe_gate_batch, -1 included) */
 int tfhe_blind_rotate(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
                       void *stream);
 int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,

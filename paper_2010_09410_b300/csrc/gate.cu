@@ -524,6 +524,7 @@ int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const
     if (!in || !types || !in_idx || !out || num_in < 1)
         return tfhe_set_error(ctx, TFHE_EINVAL, "gate_batch: null pointer or num_in < 1");
     if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "gate_batch: keys not set");
+    if (form == -1) tfhe_pick_form(ctx, G, &form, &tc_level);  // chosen for the batch width
     int rc = check_form(ctx, form);
     if (rc != TFHE_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -550,10 +551,12 @@ extern "C" int tfhe_blind_rotate(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *a
     if (G == 0) return TFHE_OK;
     if (!bar || !acc) return tfhe_set_error(ctx, TFHE_EINVAL, "blind_rotate: null pointer");
     if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "blind_rotate: keys not set");
+    int level = -1;
+    if (form == -1) tfhe_pick_form(ctx, G, &form, &level);  // chosen for the batch width
     int rc = check_form(ctx, form);
     if (rc != TFHE_OK) return rc;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    return blind_rotate_dispatch(ctx, bar, acc, G, form, (cudaStream_t)stream);
+    return blind_rotate_dispatch(ctx, bar, acc, G, form, (cudaStream_t)stream, level);
 }
 
 extern "C" int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
@@ -663,6 +666,10 @@ static int mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const in
         return tfhe_set_error(ctx, TFHE_EINVAL, "mux_batch: null pointer or num_in < 1");
     if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "mux_batch: keys not set");
     if ((int64_t)G * 2 > 0x7FFFFFFF) return tfhe_set_error(ctx, TFHE_EINVAL, "mux_batch: G too large");
+    if (form == -1) {  // chosen for the width of the 2G bootstraps
+        int lv = -1;
+        tfhe_pick_form(ctx, 2 * (int64_t)G, &form, &lv);
+    }
     int rc = check_form(ctx, form);
     if (rc != TFHE_OK) return rc;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

@@ -9,7 +9,7 @@ from conftest import from_dev, gpu_context, to_dev
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [0, 1, 2]
+FORMS = [0, 1, 2, -1]
 
 
 def empty(torch, *shape):

@@ -9,7 +9,7 @@ from conftest import from_dev, gpu_context, to_dev
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [0, 1, 2]
+FORMS = [0, 1, 2, -1]
 CASES = [(c, a, b) for c in (0, 1) for a in (0, 1) for b in (0, 1)]
 
 
