@@ -124,6 +124,19 @@ int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates);
  * device error word. */
 int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
 
+/* Failure-detection probe (the paper has no counterpart).  Enqueues on `stream` one
+ * bounded device wait of the kind the library's persistent kernels use between blocks:
+ * poll *flag (device u32) with acquire loads until it is >= target, and give up after
+ * max_cycles SM clock cycles (0 .. 8e9; about 2 GHz on B300), recording TFHE_ETIMEOUT
+ * in the context's device error word.  tfhe_ctx_sync then returns TFHE_ETIMEOUT and clears
+ * the word; the context stays usable.  Meant for testing the time-out path with a flag
+ * that nothing sets, or with one set by the host or by work ordered before this call;
+ * waiting for a kernel running concurrently on another stream is not supported (nothing
+ * guarantees that the two run at the same time).  TFHE_EINVAL for a null flag or
+ * max_cycles out of range. */
+int tfhe_ctx_probe_wait(tfhe_ctx *ctx, const uint32_t *flag, uint32_t target, int64_t max_cycles,
+                        void *stream);
+
 /* Karatsuba levels of the tensor-core form (0, 1 or 2; -1 selects the default: 2 for
  * N >= 1024, 1 for N = 512, else 0).  Level L computes each negacyclic product as 3^L Toeplitz products of
  * size N / 2^L (3/4 of the multiply-adds per level); results are identical for every

@@ -51,6 +51,7 @@ EXPORTS = [
     "tfhe_circuit_bootstrap",
     "tfhe_cb_tlwe2",
     "tfhe_private_keyswitch",
+    "tfhe_ctx_probe_wait",
 ]
 STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux",
           "cb_blind_rotate", "cb_keyswitch"]
@@ -124,6 +125,7 @@ def lib():
         "tfhe_circuit_bootstrap": (i32, [vp, vp, vp, i32, vp]),
         "tfhe_cb_tlwe2": (i32, [vp, vp, vp, i32, vp]),
         "tfhe_private_keyswitch": (i32, [vp, vp, vp, i32, i32, vp]),
+        "tfhe_ctx_probe_wait": (i32, [vp, vp, ctypes.c_uint32, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -231,6 +233,12 @@ class Context:
 
     def reserve(self, max_gates: int):
         self._check(lib().tfhe_ctx_reserve(self.h, max_gates), "reserve")
+
+    def probe_wait(self, flag, target: int, max_cycles: int, stream=None):
+        """One bounded device wait on flag (device u32) >= target; a time-out shows up as
+        TFHE_ETIMEOUT at the next sync."""
+        self._check(lib().tfhe_ctx_probe_wait(self.h, _ptr(flag), target, max_cycles,
+                                              _stream(stream)), "probe_wait")
 
     def sync(self, stream=None):
         self._check(lib().tfhe_ctx_sync(self.h, _stream(stream)), "sync")

@@ -201,6 +201,35 @@ extern "C" int tfhe_ctx_reserve(tfhe_ctx *ctx, int max_gates) {
     return tfhe_tc_reserve(ctx, max_gates, -1);
 }
 
+// One bounded device wait, the kind the persistent kernels use between blocks: poll
+// *flag with acquire loads until it reaches `target`, give up after max_cycles SM clock
+// cycles and record TFHE_ETIMEOUT in the context's error word.  One thread, no trap.
+__global__ void k_probe_wait(const uint32_t *flag, uint32_t target, long long max_cycles,
+                             int *err) {
+    if (threadIdx.x != 0) return;
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= target) return;
+        if (clock64() - t0 > max_cycles) {
+            atomicCAS(err, 0, TFHE_ETIMEOUT);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+extern "C" int tfhe_ctx_probe_wait(tfhe_ctx *ctx, const uint32_t *flag, uint32_t target,
+                                   int64_t max_cycles, void *stream) {
+    if (!ctx) return TFHE_EINVAL;
+    if (!flag || max_cycles < 0 || max_cycles > 8000000000LL)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "probe_wait: null flag or max_cycles out of range");
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    k_probe_wait<<<1, 32, 0, (cudaStream_t)stream>>>(flag, target, (long long)max_cycles, ctx->d_err);
+    return tfhe_check_launch(ctx, "probe_wait");
+}
+
 extern "C" int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream) {
     if (!ctx) return TFHE_EINVAL;
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
