@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
     uint64_t *acc = sm;                                      // [2][N2]
     uint32_t *dig = (uint32_t *)(acc + 2 * N2);              // [2 primes][l2][N2]
     uint32_t *prod = dig + (size_t)2 * l2 * N2;              // [2 primes][2 columns x 2 halves][N2]
-    uint32_t *tws = prod + (size_t)2 * 4 * N2;               // twiddles [2 primes][4][N2]
+    uint32_t *tws = prod + (size_t)2 * 4 * N2;               // twiddles [2 primes][2][N2][2]
     for (int x = threadIdx.x; x < 2 * N2; x += blockDim.x)
         reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
     const int job = blockIdx.x;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
                 }
             }
             __syncthreads();
-            ntt32_fwd_r8(dig, l2, N2, logN2, tws);
+            ntt32_fwd_r8(dig, l2, logN2, tws);
             // pointwise: sum over this column's l2 rows of digit x key, per prime, for the
             // four outputs (a/b column x lo/hi half); two consecutive coefficients per
             // thread (8-byte loads), Montgomery-reduced every 4 rows
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
             }
             __syncthreads();
         }
-        ntt32_inv_r8(prod, 4, N2, logN2, tws);
+        ntt32_inv_r8(prod, 4, logN2, tws);
         for (int j = threadIdx.x; j < N2; j += blockDim.x) {
 #pragma unroll
             for (int col = 0; col < 2; col++) {
@@ -276,7 +276,7 @@ uint32_t primitive_root(uint32_t p) {
     }
 }
 
-// u64 accumulator, digits and products for both primes (u32), twiddles [2][4][N2] (u32)
+// u64 accumulator, digits and products for both primes (u32), twiddles [2][2][N2][2] (u32)
 size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4 + 4) * q.N2 * 8; }
 size_t cb_ks_smem(const tfhe_cb_params &q) { return (size_t)(q.N2 + 1) * q.pks_t; }
 
@@ -337,10 +337,10 @@ int tfhe_make_twiddles32(tfhe_ctx *ctx, int N, uint32_t **tw) {
         for (int k = 0; k < N; k++) {
             const uint32_t w = (uint32_t)powmod64(psi, bitrev32(k, logN), p);
             const uint32_t wi = (uint32_t)powmod64(psi_inv, bitrev32(k, logN), p);
-            T[k] = w;
-            T[N + k] = (uint32_t)(((uint64_t)w << 32) / p);
-            T[2 * N + k] = wi;
-            T[3 * N + k] = (uint32_t)(((uint64_t)wi << 32) / p);
+            T[2 * k] = w;
+            T[2 * k + 1] = (uint32_t)(((uint64_t)w << 32) / p);
+            T[2 * N + 2 * k] = wi;
+            T[2 * N + 2 * k + 1] = (uint32_t)(((uint64_t)wi << 32) / p);
         }
     }
     if (cudaMalloc(tw, h.size() * 4) != cudaSuccess)

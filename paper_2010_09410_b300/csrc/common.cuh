@@ -38,7 +38,7 @@ struct tfhe_ctx {
     uint64_t *psi_fwd = nullptr;
     uint64_t *psi_inv = nullptr;
     uint64_t n_inv = 0;
-    // two-prime twiddles for CMUX products at ring degree N ([2][4][N], ntt32.cuh)
+    // two-prime twiddles for CMUX products at ring degree N ([2][2][N][2], ntt32.cuh)
     uint32_t *tw32 = nullptr;
 
     // per-batch workspaces (grown on demand)
@@ -66,7 +66,7 @@ struct tfhe_ctx {
     uint32_t *bsk2_ntt = nullptr;  // [n][2 l2][2][2 primes][2 halves][N2] residues, NTT domain,
                                    // Montgomery form, scaled by N2^-1
     uint32_t *pksk = nullptr;      // [2][N2+1][t][base - 1][2N], rows v = 1..base-1
-    uint32_t *cb_tw = nullptr;     // two-prime twiddles for the lvl2 ring [2][4][N2]
+    uint32_t *cb_tw = nullptr;     // two-prime twiddles for the lvl2 ring [2][2][N2][2]
     uint64_t *ws_cb = nullptr;  // lvl2 TLWEs [R][l][N2+1] between the two steps
     size_t ws_cb_cap = 0;       // bytes
 

@@ -175,7 +175,7 @@ __device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__r
         }
     }
     __syncthreads();
-    ntt32_fwd_r8(dig, 2 * l, N, logN, tw);
+    ntt32_fwd_r8(dig, 2 * l, logN, tw);
     // pointwise, two consecutive coefficients per thread, Montgomery-reduced every 4 rows
     for (int it = threadIdx.x; it < N; it += blockDim.x) {
         const int pr = it >= (N >> 1);
@@ -207,7 +207,7 @@ __device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__r
         *reinterpret_cast<uint2 *>(prod + pr * pplane + N + swz(k)) = rs[1];
     }
     __syncthreads();
-    ntt32_inv_r8(prod, 2, N, logN, tw);
+    ntt32_inv_r8(prod, 2, logN, tw);
 }
 
 // word j of polynomial c of the product, mod 2^32
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(1024) k_blind_rotate_ntt2(
     uint32_t *prod = dig + (size_t)4 * l * N;      // [2][2][N]
     uint32_t *acc = prod + (size_t)4 * N;          // [2][N]
     uint32_t *diff = acc + 2 * N;                  // [2][N]
-    uint32_t *tws = diff + 2 * N;                  // [2][4][N]
+    uint32_t *tws = diff + 2 * N;                  // [2][2][N][2]
     for (int x = threadIdx.x; x < 2 * N; x += blockDim.x)
         reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
     const size_t g = blockIdx.x;

@@ -11,8 +11,10 @@
 // steps.
 //
 // Layout: the transforms work in place on shared memory a[2 primes][np][N], prime-major;
-// the twiddle table is tw[2 primes][4][N]: psi^{brv(k)}, its Shoup quotient,
-// psi^{-brv(k)} and its quotient, psi a primitive 2N-th root of unity mod the prime.
+// the twiddle table is tw[2 primes][2][N][2]: for each prime the forward pairs
+// (psi^{brv(k)}, its Shoup quotient), then the inverse pairs (psi^{-brv(k)}, quotient),
+// psi a primitive 2N-th root of unity mod the prime.  A pair is one 8-byte load, and the
+// consecutive pairs a radix-8 group needs are one or two 16-byte loads.
 #pragma once
 
 #include "common.cuh"
@@ -84,7 +86,7 @@ __device__ __forceinline__ void ntt32_fwd(uint32_t *a, int np, int N, int logN,
             const int i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
             uint32_t *x = a + (size_t)poly * N;
             const uint32_t *T = tw + (size_t)pr * 4 * N;
-            const uint32_t V = shoup_mul(x[j + t], __ldg(T + m + i), __ldg(T + N + m + i), p);
+            const uint32_t V = shoup_mul(x[j + t], __ldg(T + 2 * (m + i)), __ldg(T + 2 * (m + i) + 1), p);
             const uint32_t U = x[j];
             x[j] = red_below(U + V, p2);
             x[j + t] = red_below(U - V + p2, p2);
@@ -108,7 +110,8 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
             const uint32_t *T = tw + (size_t)pr * 4 * N;
             const uint32_t U = x[j], V = x[j + t];
             x[j] = red_below(U + V, p2);
-            x[j + t] = shoup_mul(U - V + p2, __ldg(T + 2 * N + h + i), __ldg(T + 3 * N + h + i), p);
+            x[j + t] = shoup_mul(U - V + p2, __ldg(T + 2 * N + 2 * (h + i)),
+                                 __ldg(T + 2 * N + 2 * (h + i) + 1), p);
         }
         __syncthreads();
     }
@@ -130,125 +133,183 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
 // e_k = 2^R t i + x0 + k t, x0 < t; stage s + q pairs k and k + 2^q, block 2^(R-1-q) i +
 // (k >> (q+1)), twiddle index (N >> (s+q+1)) + block.  One barrier per pass; the same
 // butterflies, twiddles and order within each group as the stage-by-stage loops above.
+//
+// The ring degree and the stage are template parameters, so a group's addresses are
+// swz(e_0) combined with constants: the swizzle is linear over GF(2) and the bits of
+// k * stride are disjoint from those of e_0, so swz(e_k) = swz(e_0) ^ swz(k * stride),
+// an add folded into the access wherever the constant cannot meet the bits of swz(e_0).
+//
+// Forward butterflies are Harvey's lazy form: values stay in [0, 4p) between stages (4p <
+// 2^32 for both primes), only U is brought below 2p, and the last pass brings every output
+// below 2p.  Inverse butterflies keep [0, 2p).  Callers see [0, 2p) in and out as before.
 __device__ __forceinline__ int swz(int e) { return e ^ (((e >> 5) & 7) << 2); }
 
-// load / store the 2^R coefficients e0 + k*st of a group (contiguous when st == 1)
-template <int G>
-__device__ __forceinline__ void grp_load(const uint32_t *x, int e0, int st, uint32_t *v) {
-    if (G >= 4 && st == 1) {
+template <int LOGST, int R>
+__device__ __forceinline__ int grp_off(int sb, int k) {
+    const int c = swz(k << LOGST);  // a constant once k is unrolled
+    const int m = ((1 << LOGST) - 1) | ~((1 << (LOGST + R)) - 1) | 0x1c;  // bits swz(e_0) may hold
+    return (c & m) == 0 ? sb + c : sb ^ c;
+}
+
+// load / store the 2^R coefficients of a group, sb = swz(e_0), stride 2^LOGST
+template <int LOGST, int R>
+__device__ __forceinline__ void grp_load(const uint32_t *x, int sb, uint32_t *v) {
+    constexpr int G = 1 << R;
+    if constexpr (LOGST == 0 && G >= 4) {
 #pragma unroll
         for (int k = 0; k < G; k += 4) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(x + swz(e0 + k));
+            const uint4 w = *reinterpret_cast<const uint4 *>(x + grp_off<0, R>(sb, k));
             v[k] = w.x; v[k + 1] = w.y; v[k + 2] = w.z; v[k + 3] = w.w;
         }
-    } else if (G == 2 && st == 1) {
-        const uint2 w = *reinterpret_cast<const uint2 *>(x + swz(e0));
+    } else if constexpr (LOGST == 0 && G == 2) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(x + sb);
         v[0] = w.x; v[1] = w.y;
     } else {
 #pragma unroll
-        for (int k = 0; k < G; k++) v[k] = x[swz(e0 + k * st)];
+        for (int k = 0; k < G; k++) v[k] = x[grp_off<LOGST, R>(sb, k)];
     }
 }
 
-template <int G>
-__device__ __forceinline__ void grp_store(uint32_t *x, int e0, int st, const uint32_t *v) {
-    if (G >= 4 && st == 1) {
+template <int LOGST, int R>
+__device__ __forceinline__ void grp_store(uint32_t *x, int sb, const uint32_t *v) {
+    constexpr int G = 1 << R;
+    if constexpr (LOGST == 0 && G >= 4) {
 #pragma unroll
         for (int k = 0; k < G; k += 4)
-            *reinterpret_cast<uint4 *>(x + swz(e0 + k)) = make_uint4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-    } else if (G == 2 && st == 1) {
-        *reinterpret_cast<uint2 *>(x + swz(e0)) = make_uint2(v[0], v[1]);
+            *reinterpret_cast<uint4 *>(x + grp_off<0, R>(sb, k)) =
+                make_uint4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else if constexpr (LOGST == 0 && G == 2) {
+        *reinterpret_cast<uint2 *>(x + sb) = make_uint2(v[0], v[1]);
     } else {
 #pragma unroll
-        for (int k = 0; k < G; k++) x[swz(e0 + k * st)] = v[k];
+        for (int k = 0; k < G; k++) x[grp_off<LOGST, R>(sb, k)] = v[k];
     }
 }
 
-template <int R>
-__device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int N, int logN, int s,
-                                               const uint32_t *tw) {
-    constexpr int G = 1 << R;
-    const int t = N >> (s + 1);
-    const int logst = logN - s - R;          // log2 of the element stride inside a group
-    const int st = 1 << logst;
-    const int lgroups = logN - R;            // log2 of the groups per polynomial
-    for (int idx = threadIdx.x; idx < (2 * np) << lgroups; idx += blockDim.x) {
-        const int poly = idx >> lgroups, gidx = idx & ((1 << lgroups) - 1);
+// np consecutive (twiddle, quotient) pairs starting at pair index b (b a multiple of np;
+// np is a constant once the callers' stage loops are unrolled)
+__device__ __forceinline__ void tw_pairs(const uint32_t *T, int b, int np, uint32_t *w) {
+    if (np == 1) {
+        const uint2 x = *reinterpret_cast<const uint2 *>(T + 2 * b);
+        w[0] = x.x; w[1] = x.y;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 2 * np; m += 4) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(T + 2 * b + m);
+            w[m] = x.x; w[m + 1] = x.y; w[m + 2] = x.z; w[m + 3] = x.w;
+        }
+    }
+}
+
+template <int LOGN, int S, int R, bool LAST>
+__device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, const uint32_t *tw) {
+    constexpr int N = 1 << LOGN, G = 1 << R;
+    constexpr int LOGST = LOGN - S - R;  // log2 of the element stride inside a group
+    constexpr int LG = LOGN - R;         // log2 of the groups per polynomial
+    for (int idx = threadIdx.x; idx < (2 * np) << LG; idx += blockDim.x) {
+        const int poly = idx >> LG, gidx = idx & ((1 << LG) - 1);
         const int pr = poly >= np;
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
-        const int i = gidx >> logst, x0 = gidx & (st - 1);
+        const int i = gidx >> LOGST;
+        const int sb = swz((i << (LOGST + R)) | (gidx & ((1 << LOGST) - 1)));
         uint32_t *x = a + (size_t)poly * N;
-        const int e0 = i * 2 * t + x0;
-        const uint32_t *T = tw + (size_t)pr * 4 * N;
+        const uint32_t *T = tw + (size_t)pr * 4 * N;  // forward pairs
         uint32_t v[G];
-        grp_load<G>(x, e0, st, v);
+        grp_load<LOGST, R>(x, sb, v);
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const int half = G >> (q + 1);
+            uint32_t w[G];  // 2^q pairs: blocks ((2^S + i) << q) + j, j < 2^q
+            tw_pairs(T, ((1 << S) + i) << q, 1 << q, w);
 #pragma unroll
             for (int k = 0; k < G; k++) {
                 if (k & half) continue;
-                const int blk = ((1 << s) << q) + (i << q) + (k >> (R - q));
-                const uint32_t V = shoup_mul(v[k + half], T[blk], T[N + blk], p);
-                const uint32_t U = v[k];
-                v[k] = red_below(U + V, p2);
-                v[k + half] = red_below(U - V + p2, p2);
+                const int j = k >> (R - q);
+                const uint32_t V = shoup_mul(v[k + half], w[2 * j], w[2 * j + 1], p);
+                const uint32_t U = red_below(v[k], p2);
+                v[k] = U + V;
+                v[k + half] = U - V + p2;
             }
         }
-        grp_store<G>(x, e0, st, v);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int k = 0; k < G; k++) v[k] = red_below(v[k], p2);
+        }
+        grp_store<LOGST, R>(x, sb, v);
     }
     __syncthreads();
 }
 
-template <int R>
-__device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int N, int logN, int s,
-                                               const uint32_t *tw) {
-    constexpr int G = 1 << R;
-    const int t = 1 << s;
-    const int lgroups = logN - R;
-    for (int idx = threadIdx.x; idx < (2 * np) << lgroups; idx += blockDim.x) {
-        const int poly = idx >> lgroups, gidx = idx & ((1 << lgroups) - 1);
+template <int LOGN, int S, int R>
+__device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, const uint32_t *tw) {
+    constexpr int N = 1 << LOGN, G = 1 << R;
+    constexpr int LG = LOGN - R;
+    for (int idx = threadIdx.x; idx < (2 * np) << LG; idx += blockDim.x) {
+        const int poly = idx >> LG, gidx = idx & ((1 << LG) - 1);
         const int pr = poly >= np;
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
-        const int i = gidx >> s, x0 = gidx & (t - 1);
+        const int i = gidx >> S;
+        const int sb = swz((i << (S + R)) | (gidx & ((1 << S) - 1)));
         uint32_t *x = a + (size_t)poly * N;
-        const int e0 = (i << (s + R)) + x0;
-        const uint32_t *T = tw + (size_t)pr * 4 * N;
+        const uint32_t *T = tw + (size_t)pr * 4 * N + 2 * N;  // inverse pairs
         uint32_t v[G];
-        grp_load<G>(x, e0, t, v);
+        grp_load<S, R>(x, sb, v);
 #pragma unroll
         for (int q = 0; q < R; q++) {
             const int dist = 1 << q;
+            uint32_t w[G];  // 2^(R-1-q) pairs from (N >> (S+q+1)) + (i << (R-1-q))
+            tw_pairs(T, (N >> (S + q + 1)) + (i << (R - 1 - q)), 1 << (R - 1 - q), w);
 #pragma unroll
             for (int k = 0; k < G; k++) {
                 if (k & dist) continue;
-                const int blk = (N >> (s + q + 1)) + (i << (R - 1 - q)) + (k >> (q + 1));
+                const int j = k >> (q + 1);
                 const uint32_t U = v[k], V = v[k + dist];
                 v[k] = red_below(U + V, p2);
-                v[k + dist] = shoup_mul(U - V + p2, T[2 * N + blk], T[3 * N + blk], p);
+                v[k + dist] = shoup_mul(U - V + p2, w[2 * j], w[2 * j + 1], p);
             }
         }
-        grp_store<G>(x, e0, t, v);
+        grp_store<S, R>(x, sb, v);
     }
     __syncthreads();
 }
 
 // Whole transforms by passes of three stages (and one shorter pass at the end).
-__device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int N, int logN,
-                                             const uint32_t *tw) {
-    int s = 0;
-    for (; s + 3 <= logN; s += 3) ntt32_fwd_pass<3>(a, np, N, logN, s, tw);
-    if (logN - s == 2) ntt32_fwd_pass<2>(a, np, N, logN, s, tw);
-    else if (logN - s == 1) ntt32_fwd_pass<1>(a, np, N, logN, s, tw);
+template <int LOGN, int S>
+__device__ __forceinline__ void ntt32_fwd_from(uint32_t *a, int np, const uint32_t *tw) {
+    constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
+    if constexpr (R > 0) {
+        ntt32_fwd_pass<LOGN, S, R, S + R == LOGN>(a, np, tw);
+        ntt32_fwd_from<LOGN, S + R>(a, np, tw);
+    }
 }
 
-__device__ __forceinline__ void ntt32_inv_r8(uint32_t *a, int np, int N, int logN,
-                                             const uint32_t *tw) {
-    int s = 0;
-    for (; s + 3 <= logN; s += 3) ntt32_inv_pass<3>(a, np, N, logN, s, tw);
-    if (logN - s == 2) ntt32_inv_pass<2>(a, np, N, logN, s, tw);
-    else if (logN - s == 1) ntt32_inv_pass<1>(a, np, N, logN, s, tw);
+template <int LOGN, int S>
+__device__ __forceinline__ void ntt32_inv_from(uint32_t *a, int np, const uint32_t *tw) {
+    constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
+    if constexpr (R > 0) {
+        ntt32_inv_pass<LOGN, S, R>(a, np, tw);
+        ntt32_inv_from<LOGN, S + R>(a, np, tw);
+    }
 }
 
-// host: the twiddle table tw[2][4][N] (device allocation) for ring degree N
+// Ring degrees are validated to 256 .. 2048 where contexts and lvl2 keys are set up.
+__device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int logN, const uint32_t *tw) {
+    switch (logN) {
+    case 8: ntt32_fwd_from<8, 0>(a, np, tw); break;
+    case 9: ntt32_fwd_from<9, 0>(a, np, tw); break;
+    case 10: ntt32_fwd_from<10, 0>(a, np, tw); break;
+    case 11: ntt32_fwd_from<11, 0>(a, np, tw); break;
+    }
+}
+
+__device__ __forceinline__ void ntt32_inv_r8(uint32_t *a, int np, int logN, const uint32_t *tw) {
+    switch (logN) {
+    case 8: ntt32_inv_from<8, 0>(a, np, tw); break;
+    case 9: ntt32_inv_from<9, 0>(a, np, tw); break;
+    case 10: ntt32_inv_from<10, 0>(a, np, tw); break;
+    case 11: ntt32_inv_from<11, 0>(a, np, tw); break;
+    }
+}
+
+// host: the twiddle table tw[2][2][N][2] (device allocation) for ring degree N
 int tfhe_make_twiddles32(tfhe_ctx *ctx, int N, uint32_t **tw);
