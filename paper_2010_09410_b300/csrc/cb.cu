@@ -13,9 +13,10 @@
 // Bg2 = 512).  It is computed by NTTs modulo two 30-bit primes and recombined by the CRT
 // (ntt32.cuh; the modulus, about 2^59.4, exceeds twice the bound), so it is the integer
 // itself, and (V_lo + 2^32 V_hi) mod 2^64 is the product.  The accumulator (2 x N2 u64),
-// the l2 digit polynomials of one TRLWE column and the four product polynomials (a/b
-// column x lo/hi half), each for both primes, and the twiddles stay in shared memory
-// (224 KB at N2 = 2048); the digit and product polynomials are stored swizzled (swz).
+// the 2 l2 digit polynomials of both TRLWE columns for both primes (transformed together;
+// the four product polynomials, a/b column x lo/hi half, then overwrite the first four),
+// and the twiddles stay in shared memory (224 KB at N2 = 2048); digit and product
+// polynomials are stored swizzled (swz).
 //
 // Step 2 (k_private_ks, one block per (lvl2 TLWE, function z)): the private functional
 // key switch out = - sum_{i <= N2} sum_k PKSK[z][i][k][digit_k(a_i)] (a_{N2} = b), the
@@ -86,15 +87,19 @@ __global__ void k_pksk_relayout(const uint32_t *__restrict__ src, uint32_t *__re
 }
 
 // Step 1 for job = r * l + (u - 1): in u32[R][n+1] -> out u64[R][l][N2+1].
-__global__ void __launch_bounds__(1024) k_cb_blind_rotate(
+constexpr int CB_THREADS = 512;  // 128 registers a thread: more key loads in flight
+
+__host__ __device__ constexpr int cb_rows(int l2) { return 2 * l2 > 4 ? 2 * l2 : 4; }
+
+__global__ void __launch_bounds__(CB_THREADS, 1) k_cb_blind_rotate(
     int n, int N2, int logN2, int l2, int Bg2bit, int l, int Bgbit,
     const uint32_t *__restrict__ in, uint64_t *__restrict__ out,
     const uint32_t *__restrict__ bsk2, const uint32_t *__restrict__ tw) {
     extern __shared__ __align__(16) uint64_t sm[];
+    const int rows = cb_rows(l2);
     uint64_t *acc = sm;                                      // [2][N2]
-    uint32_t *dig = (uint32_t *)(acc + 2 * N2);              // [2 primes][l2][N2]
-    uint32_t *prod = dig + (size_t)2 * l2 * N2;              // [2 primes][2 columns x 2 halves][N2]
-    uint32_t *tws = prod + (size_t)2 * 4 * N2;               // twiddles [2 primes][2][N2][2]
+    uint32_t *dig = (uint32_t *)(acc + 2 * N2);              // [2 primes][rows][N2]
+    uint32_t *tws = dig + (size_t)2 * rows * N2;             // twiddles [2 primes][2][N2][2]
     for (int x = threadIdx.x; x < 2 * N2; x += blockDim.x)
         reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
     const int job = blockIdx.x;
@@ -111,83 +116,88 @@ __global__ void __launch_bounds__(1024) k_cb_blind_rotate(
     __syncthreads();
     const uint64_t off = gadget_offset64(l2, Bg2bit);
     const size_t per = (size_t)2 * l2 * 2 * 4 * N2;  // words of one NTT-domain BSK2_i
-    const size_t dplane = (size_t)l2 * N2, pplane = (size_t)4 * N2;
+    const size_t pplane = (size_t)rows * N2;          // words of one prime's rows
+    // Every block reads the same key row at about the same time; each starts its pointwise
+    // sweep at its own offset (a multiple of 32 items, so warps stay coalesced) to spread
+    // the concurrent requests over the L2 slices.
+    const int rot = ((blockIdx.x * 37) & ((N2 >> 5) - 1)) << 5;
     for (int i = 0; i < n; i++) {
         const int a = (int)((uint32_t)(__ldg(c + i) + (1u << (sh - 1))) >> sh);
         if (a == 0) continue;  // X^0 ACC - ACC = 0: all-zero digits, the step is the identity
         const uint32_t *key = bsk2 + (size_t)i * per;
-        for (int cc = 0; cc < 2; cc++) {
-            const uint64_t *pa = acc + (size_t)cc * N2;
-            // two consecutive coefficients per thread: 8-byte digit stores
-            for (int j = 2 * threadIdx.x; j < N2; j += 2 * blockDim.x) {
+        // digits of both columns, rows cc * l2 + q; two consecutive coefficients per thread
+        for (int j = 2 * threadIdx.x; j < N2; j += 2 * blockDim.x) {
+            for (int cc = 0; cc < 2; cc++) {
+                const uint64_t *pa = acc + (size_t)cc * N2;
                 const ulonglong2 own = *reinterpret_cast<const ulonglong2 *>(pa + j);
                 const uint64_t u0 = rot_coef64(pa, N2, a, j) - own.x + off;
                 const uint64_t u1 = rot_coef64(pa, N2, a, j + 1) - own.y + off;
                 for (int q = 0; q < l2; q++) {
                     const int32_t d0 = gadget_digit64(u0, q + 1, Bg2bit);
                     const int32_t d1 = gadget_digit64(u1, q + 1, Bg2bit);
-                    *reinterpret_cast<uint2 *>(dig + (size_t)q * N2 + swz(j)) =
-                        make_uint2(res_of_i32(d0, NP1), res_of_i32(d1, NP1));
-                    *reinterpret_cast<uint2 *>(dig + dplane + (size_t)q * N2 + swz(j)) =
+                    uint32_t *dr = dig + (size_t)(cc * l2 + q) * N2 + swz(j);
+                    *reinterpret_cast<uint2 *>(dr) = make_uint2(res_of_i32(d0, NP1), res_of_i32(d1, NP1));
+                    *reinterpret_cast<uint2 *>(dr + pplane) =
                         make_uint2(res_of_i32(d0, NP2), res_of_i32(d1, NP2));
                 }
             }
-            __syncthreads();
-            ntt32_fwd_r8(dig, l2, logN2, tws);
-            // pointwise: sum over this column's l2 rows of digit x key, per prime, for the
-            // four outputs (a/b column x lo/hi half); two consecutive coefficients per
-            // thread (8-byte loads), Montgomery-reduced every 4 rows
-            for (int it = threadIdx.x; it < N2; it += blockDim.x) {
-                const int pr = it >= (N2 >> 1);
-                const int k = 2 * (it - (pr ? (N2 >> 1) : 0));
-                const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
-                uint32_t *pp = prod + pr * pplane + swz(k);
-                uint2 rs[4];
+        }
+        __syncthreads();
+        ntt32_fwd_r8(dig, 2 * l2, logN2, tws, (int)pplane);
+        // pointwise: per prime and pair of coefficients, the sums over the 2 l2 rows of
+        // digit x key for the four outputs (a/b column x lo/hi half), Montgomery-reduced
+        // every 4 rows; the outputs overwrite rows 0..3 of the same coefficients, which
+        // only this thread reads.
+        for (int it0 = threadIdx.x; it0 < N2; it0 += blockDim.x) {
+            const int it = (it0 + rot) & (N2 - 1);
+            const int pr = it >= (N2 >> 1);
+            const int k = 2 * (it - (pr ? (N2 >> 1) : 0));
+            const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
+            uint32_t *pp = dig + pr * pplane + swz(k);
+            uint2 rs[4];
 #pragma unroll
-                for (int o = 0; o < 4; o++)
-                    rs[o] = cc ? *reinterpret_cast<const uint2 *>(pp + (size_t)o * N2) : make_uint2(0, 0);
-                uint64_t ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
+            for (int o = 0; o < 4; o++) rs[o] = make_uint2(0, 0);
+            uint64_t ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
 #pragma unroll 4
-                for (int q = 0; q < l2; q++) {
-                    const uint2 dd = *reinterpret_cast<const uint2 *>(dig + pr * dplane + (size_t)q * N2 + swz(k));
-                    const uint32_t d0 = red_below(dd.x, p), d1 = red_below(dd.y, p);
-                    // key words of row cc*l2+q, this prime: a column lo/hi, b column lo/hi
-                    const uint32_t *kr = key + ((size_t)(cc * l2 + q) * 2 * 4 + pr * 2) * N2 + k;
-                    const uint2 k0 = __ldg(reinterpret_cast<const uint2 *>(kr));
-                    const uint2 k1 = __ldg(reinterpret_cast<const uint2 *>(kr + N2));
-                    const uint2 k2 = __ldg(reinterpret_cast<const uint2 *>(kr + 4 * N2));
-                    const uint2 k3 = __ldg(reinterpret_cast<const uint2 *>(kr + 5 * N2));
-                    ta[0] += (uint64_t)d0 * k0.x;
-                    tb[0] += (uint64_t)d1 * k0.y;
-                    ta[1] += (uint64_t)d0 * k1.x;
-                    tb[1] += (uint64_t)d1 * k1.y;
-                    ta[2] += (uint64_t)d0 * k2.x;
-                    tb[2] += (uint64_t)d1 * k2.y;
-                    ta[3] += (uint64_t)d0 * k3.x;
-                    tb[3] += (uint64_t)d1 * k3.y;
-                    if ((q & 3) == 3 || q == l2 - 1) {  // < 4 p^2 < p 2^32: reduce
+            for (int rr = 0; rr < 2 * l2; rr++) {
+                const uint2 dd = *reinterpret_cast<const uint2 *>(pp + (size_t)rr * N2);
+                const uint32_t d0 = red_below(dd.x, p), d1 = red_below(dd.y, p);
+                // key words of row rr, this prime: a column lo/hi, b column lo/hi
+                const uint32_t *kr = key + ((size_t)rr * 2 * 4 + pr * 2) * N2 + k;
+                const uint2 k0 = __ldg(reinterpret_cast<const uint2 *>(kr));
+                const uint2 k1 = __ldg(reinterpret_cast<const uint2 *>(kr + N2));
+                const uint2 k2 = __ldg(reinterpret_cast<const uint2 *>(kr + 4 * N2));
+                const uint2 k3 = __ldg(reinterpret_cast<const uint2 *>(kr + 5 * N2));
+                ta[0] += (uint64_t)d0 * k0.x;
+                tb[0] += (uint64_t)d1 * k0.y;
+                ta[1] += (uint64_t)d0 * k1.x;
+                tb[1] += (uint64_t)d1 * k1.y;
+                ta[2] += (uint64_t)d0 * k2.x;
+                tb[2] += (uint64_t)d1 * k2.y;
+                ta[3] += (uint64_t)d0 * k3.x;
+                tb[3] += (uint64_t)d1 * k3.y;
+                if ((rr & 3) == 3 || rr == 2 * l2 - 1) {  // < 4 p^2 < p 2^32: reduce
 #pragma unroll
-                        for (int o = 0; o < 4; o++) {
-                            rs[o].x = red_below(rs[o].x + redc32(ta[o], p, ninv), p2);
-                            rs[o].y = red_below(rs[o].y + redc32(tb[o], p, ninv), p2);
-                            ta[o] = tb[o] = 0;
-                        }
+                    for (int o = 0; o < 4; o++) {
+                        rs[o].x = red_below(rs[o].x + redc32(ta[o], p, ninv), p2);
+                        rs[o].y = red_below(rs[o].y + redc32(tb[o], p, ninv), p2);
+                        ta[o] = tb[o] = 0;
                     }
                 }
-#pragma unroll
-                for (int o = 0; o < 4; o++) *reinterpret_cast<uint2 *>(pp + (size_t)o * N2) = rs[o];
             }
-            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < 4; o++) *reinterpret_cast<uint2 *>(pp + (size_t)o * N2) = rs[o];
         }
-        ntt32_inv_r8(prod, 4, logN2, tws);
+        __syncthreads();
+        ntt32_inv_r8(dig, 4, logN2, tws, (int)pplane);
         for (int j = threadIdx.x; j < N2; j += blockDim.x) {
 #pragma unroll
             for (int col = 0; col < 2; col++) {
                 const size_t o_lo = (size_t)(col * 2) * N2 + swz(j), o_hi = o_lo + N2;
-                const int64_t vlo = crt_centred(red_below(prod[o_lo], NP1),
-                                                red_below(prod[pplane + o_lo], NP2));
-                const int64_t vhi = crt_centred(red_below(prod[o_hi], NP1),
-                                                red_below(prod[pplane + o_hi], NP2));
+                const int64_t vlo = crt_centred(red_below(dig[o_lo], NP1),
+                                                red_below(dig[pplane + o_lo], NP2));
+                const int64_t vhi = crt_centred(red_below(dig[o_hi], NP1),
+                                                red_below(dig[pplane + o_hi], NP2));
                 acc[(size_t)col * N2 + j] += (uint64_t)vlo + ((uint64_t)vhi << 32);
             }
         }
@@ -276,8 +286,8 @@ uint32_t primitive_root(uint32_t p) {
     }
 }
 
-// u64 accumulator, digits and products for both primes (u32), twiddles [2][2][N2][2] (u32)
-size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + q.l2 + 4 + 4) * q.N2 * 8; }
+// u64 accumulator, digits (then products) of both primes (u32), twiddles [2][2][N2][2] (u32)
+size_t cb_br_smem(const tfhe_cb_params &q) { return (size_t)(2 + cb_rows(q.l2) + 4) * q.N2 * 8; }
 size_t cb_ks_smem(const tfhe_cb_params &q) { return (size_t)(q.N2 + 1) * q.pks_t; }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -297,7 +307,7 @@ int launch_cb_blind_rotate(tfhe_ctx *ctx, const uint32_t *in, uint64_t *out, int
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
     StageTimer tm(ctx, TFHE_STAGE_CB_BLIND_ROTATE, st);
-    k_cb_blind_rotate<<<R * p.l, 1024, smem, st>>>(p.n, q.N2, ctx->logN2, q.l2, q.Bg2bit, p.l,
+    k_cb_blind_rotate<<<R * p.l, CB_THREADS, smem, st>>>(p.n, q.N2, ctx->logN2, q.l2, q.Bg2bit, p.l,
                                                    p.Bgbit, in, out, ctx->bsk2_ntt, ctx->cb_tw);
     tm.stop();
     return tfhe_check_launch(ctx, "cb_blind_rotate");

@@ -202,7 +202,7 @@ __device__ __forceinline__ void tw_pairs(const uint32_t *T, int b, int np, uint3
 }
 
 template <int LOGN, int S, int R, bool LAST>
-__device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, const uint32_t *tw) {
+__device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int pst, const uint32_t *tw) {
     constexpr int N = 1 << LOGN, G = 1 << R;
     constexpr int LOGST = LOGN - S - R;  // log2 of the element stride inside a group
     constexpr int LG = LOGN - R;         // log2 of the groups per polynomial
@@ -212,7 +212,7 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, const uint32
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
         const int i = gidx >> LOGST;
         const int sb = swz((i << (LOGST + R)) | (gidx & ((1 << LOGST) - 1)));
-        uint32_t *x = a + (size_t)poly * N;
+        uint32_t *x = a + (size_t)pr * pst + (size_t)(poly - (pr ? np : 0)) * N;
         const uint32_t *T = tw + (size_t)pr * 4 * N;  // forward pairs
         uint32_t v[G];
         grp_load<LOGST, R>(x, sb, v);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, const uint32
 }
 
 template <int LOGN, int S, int R>
-__device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, const uint32_t *tw) {
+__device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int pst, const uint32_t *tw) {
     constexpr int N = 1 << LOGN, G = 1 << R;
     constexpr int LG = LOGN - R;
     for (int idx = threadIdx.x; idx < (2 * np) << LG; idx += blockDim.x) {
@@ -250,7 +250,7 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, const uint32
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p;
         const int i = gidx >> S;
         const int sb = swz((i << (S + R)) | (gidx & ((1 << S) - 1)));
-        uint32_t *x = a + (size_t)poly * N;
+        uint32_t *x = a + (size_t)pr * pst + (size_t)(poly - (pr ? np : 0)) * N;
         const uint32_t *T = tw + (size_t)pr * 4 * N + 2 * N;  // inverse pairs
         uint32_t v[G];
         grp_load<S, R>(x, sb, v);
@@ -275,39 +275,44 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, const uint32
 
 // Whole transforms by passes of three stages (and one shorter pass at the end).
 template <int LOGN, int S>
-__device__ __forceinline__ void ntt32_fwd_from(uint32_t *a, int np, const uint32_t *tw) {
+__device__ __forceinline__ void ntt32_fwd_from(uint32_t *a, int np, int pst, const uint32_t *tw) {
     constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
     if constexpr (R > 0) {
-        ntt32_fwd_pass<LOGN, S, R, S + R == LOGN>(a, np, tw);
-        ntt32_fwd_from<LOGN, S + R>(a, np, tw);
+        ntt32_fwd_pass<LOGN, S, R, S + R == LOGN>(a, np, pst, tw);
+        ntt32_fwd_from<LOGN, S + R>(a, np, pst, tw);
     }
 }
 
 template <int LOGN, int S>
-__device__ __forceinline__ void ntt32_inv_from(uint32_t *a, int np, const uint32_t *tw) {
+__device__ __forceinline__ void ntt32_inv_from(uint32_t *a, int np, int pst, const uint32_t *tw) {
     constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
     if constexpr (R > 0) {
-        ntt32_inv_pass<LOGN, S, R>(a, np, tw);
-        ntt32_inv_from<LOGN, S + R>(a, np, tw);
+        ntt32_inv_pass<LOGN, S, R>(a, np, pst, tw);
+        ntt32_inv_from<LOGN, S + R>(a, np, pst, tw);
     }
 }
 
-// Ring degrees are validated to 256 .. 2048 where contexts and lvl2 keys are set up.
-__device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int logN, const uint32_t *tw) {
+// Ring degrees are validated to 256 .. 2048 where contexts and lvl2 keys are set up.  The
+// np polynomials of prime 2 start pst words after those of prime 1 (default: np N).
+__device__ __forceinline__ void ntt32_fwd_r8(uint32_t *a, int np, int logN, const uint32_t *tw,
+                                             int pst = -1) {
+    if (pst < 0) pst = np << logN;
     switch (logN) {
-    case 8: ntt32_fwd_from<8, 0>(a, np, tw); break;
-    case 9: ntt32_fwd_from<9, 0>(a, np, tw); break;
-    case 10: ntt32_fwd_from<10, 0>(a, np, tw); break;
-    case 11: ntt32_fwd_from<11, 0>(a, np, tw); break;
+    case 8: ntt32_fwd_from<8, 0>(a, np, pst, tw); break;
+    case 9: ntt32_fwd_from<9, 0>(a, np, pst, tw); break;
+    case 10: ntt32_fwd_from<10, 0>(a, np, pst, tw); break;
+    case 11: ntt32_fwd_from<11, 0>(a, np, pst, tw); break;
     }
 }
 
-__device__ __forceinline__ void ntt32_inv_r8(uint32_t *a, int np, int logN, const uint32_t *tw) {
+__device__ __forceinline__ void ntt32_inv_r8(uint32_t *a, int np, int logN, const uint32_t *tw,
+                                             int pst = -1) {
+    if (pst < 0) pst = np << logN;
     switch (logN) {
-    case 8: ntt32_inv_from<8, 0>(a, np, tw); break;
-    case 9: ntt32_inv_from<9, 0>(a, np, tw); break;
-    case 10: ntt32_inv_from<10, 0>(a, np, tw); break;
-    case 11: ntt32_inv_from<11, 0>(a, np, tw); break;
+    case 8: ntt32_inv_from<8, 0>(a, np, pst, tw); break;
+    case 9: ntt32_inv_from<9, 0>(a, np, pst, tw); break;
+    case 10: ntt32_inv_from<10, 0>(a, np, pst, tw); break;
+    case 11: ntt32_inv_from<11, 0>(a, np, pst, tw); break;
     }
 }
 
