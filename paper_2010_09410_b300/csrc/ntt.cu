@@ -155,9 +155,16 @@ __global__ void __launch_bounds__(1024) k_blind_rotate_ntt(
 
 // prod (u32[2 primes][2][N], swizzled) receives the residues of C (.) d for the TRLWE d
 // (u32[2][N] in shared memory) and the selector `key`; dig is u32[2 primes][2l][N].
+// The pointwise sweep starts at item rot (a multiple of 32 below N, so warps stay
+// coalesced): blocks that read the same selector at about the same time pass different
+// offsets (sweep_rot) and spread their requests over the L2 slices.
+__device__ __forceinline__ int sweep_rot(int N) {
+    return (((int)blockIdx.x * 37 + (int)blockIdx.y * 11) & ((N >> 5) - 1)) << 5;
+}
+
 __device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__restrict__ key,
                                           uint32_t *dig, uint32_t *prod, int N, int logN, int l,
-                                          int Bgbit, const uint32_t *tw) {
+                                          int Bgbit, const uint32_t *tw, int rot) {
     const uint32_t off = gadget_offset(l, Bgbit);
     const size_t dplane = (size_t)2 * l * N, pplane = (size_t)2 * N;
     // digits, two consecutive coefficients per thread; rows c*l + q (a, then b)
@@ -177,7 +184,8 @@ __device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__r
     __syncthreads();
     ntt32_fwd_r8(dig, 2 * l, logN, tw);
     // pointwise, two consecutive coefficients per thread, Montgomery-reduced every 4 rows
-    for (int it = threadIdx.x; it < N; it += blockDim.x) {
+    for (int it0 = threadIdx.x; it0 < N; it0 += blockDim.x) {
+        const int it = (it0 + rot) & (N - 1);
         const int pr = it >= (N >> 1);
         const int k = 2 * (it - (pr ? (N >> 1) : 0));
         const uint32_t p = pr ? NP2 : NP1, p2 = 2 * p, ninv = pr ? NP2_NINV : NP1_NINV;
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bg
     __syncthreads();
     const size_t per = (size_t)2 * l * 2 * N;  // one selector, in u64 units
     extprod32(diff, reinterpret_cast<const uint32_t *>(sel + (size_t)y * g.sy * per), dig, prod, N,
-              logN, l, Bgbit, tw);
+              logN, l, Bgbit, tw, sweep_rot(N));
     uint32_t *o = g.out + x * g.ox + y * g.oy;
     for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
         o[j] = base[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(1024) k_blind_rotate_ntt2(
             diff[N + j] = rot_coef(acc + N, N, a, j) - acc[N + j];
         }
         __syncthreads();
-        extprod32(diff, bsk2p + (size_t)i * per, dig, prod, N, logN, l, Bgbit, tws);
+        extprod32(diff, bsk2p + (size_t)i * per, dig, prod, N, logN, l, Bgbit, tws, 0);
         for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
             acc[j] += prod32_word(prod, N, j >= N, j >= N ? j - N : j);
         __syncthreads();
@@ -316,7 +324,8 @@ __global__ void __launch_bounds__(256) k_ram_write_ntt(int N, int logN, int l, i
         for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) diff[j] = r[j] - old[j];
         __syncthreads();
         const uint64_t *S = (((c >> b) & 1) ? c_ntt : gmc_ntt) + (size_t)b * per;
-        extprod32(diff, reinterpret_cast<const uint32_t *>(S), dig, prod, N, logN, l, Bgbit, tw);
+        extprod32(diff, reinterpret_cast<const uint32_t *>(S), dig, prod, N, logN, l, Bgbit, tw,
+                  sweep_rot(N));
         for (int j = threadIdx.x; j < 2 * N; j += blockDim.x)
             r[j] = old[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
         __syncthreads();
