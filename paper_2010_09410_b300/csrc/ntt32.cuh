@@ -117,7 +117,7 @@ __device__ __forceinline__ void ntt32_inv(uint32_t *a, int np, int N, int logN,
     }
 }
 
-// ---- register-blocked transforms: radix-2^R passes (R <= 3 stages per pass) ------------
+// ---- register-blocked transforms: radix-2^R passes (R <= 4 stages per pass) ------------
 // (tw may point to global or to shared memory)
 //
 // The polynomials these transforms work on are stored swizzled: coefficient e of a
@@ -273,10 +273,20 @@ __device__ __forceinline__ void ntt32_inv_pass(uint32_t *a, int np, int pst, con
     __syncthreads();
 }
 
-// Whole transforms by passes of three stages (and one shorter pass at the end).
+// Stages per pass.  Radix-16 passes cut the per-group overhead where the swizzle keeps
+// them free of bank conflicts: forward 4+3+4 (N = 2048), 4+3+3 (N = 1024); inverse 4+3+4,
+// 3+3+4; otherwise passes of three stages and a shorter one at the end.
+template <int LOGN, int S, bool FWD>
+__host__ __device__ constexpr int ntt32_pass_r() {
+    if (LOGN == 11 && (S == 0 || S == 7)) return 4;
+    if (LOGN == 10 && ((FWD && S == 0) || (!FWD && S == 6))) return 4;
+    return LOGN - S < 3 ? LOGN - S : 3;
+}
+
+// Whole transforms by passes.
 template <int LOGN, int S>
 __device__ __forceinline__ void ntt32_fwd_from(uint32_t *a, int np, int pst, const uint32_t *tw) {
-    constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
+    constexpr int R = ntt32_pass_r<LOGN, S, true>();
     if constexpr (R > 0) {
         ntt32_fwd_pass<LOGN, S, R, S + R == LOGN>(a, np, pst, tw);
         ntt32_fwd_from<LOGN, S + R>(a, np, pst, tw);
@@ -285,7 +295,7 @@ __device__ __forceinline__ void ntt32_fwd_from(uint32_t *a, int np, int pst, con
 
 template <int LOGN, int S>
 __device__ __forceinline__ void ntt32_inv_from(uint32_t *a, int np, int pst, const uint32_t *tw) {
-    constexpr int R = LOGN - S < 3 ? LOGN - S : 3;
+    constexpr int R = ntt32_pass_r<LOGN, S, false>();
     if constexpr (R > 0) {
         ntt32_inv_pass<LOGN, S, R>(a, np, pst, tw);
         ntt32_inv_from<LOGN, S + R>(a, np, pst, tw);
