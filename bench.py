@@ -141,10 +141,10 @@ class ClockSampler:
 # oracle (CPU) timing: the cpu_baseline leg and the reference arm
 # ---------------------------------------------------------------------------
 
-def oracle_gates_per_s(batch, sample_gates):
+def oracle_gates_per_s(batch, sample_gates, threads=None):
     import oracle as orc
     import tfhe_inputs as ti
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     k = batch.keys
     gates = list(range(sample_gates))
     t0 = time.perf_counter()
@@ -330,9 +330,12 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = oracle_sample_size()
         v, cores, dt = oracle_gates_per_s(batch, sample)
+        v1, _, dt1 = oracle_gates_per_s(batch, 2, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "gates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{sample} of the {args.gates} gates, one gate per "
-                                          f"thread, {dt:.1f} s wall"}
+                                          f"thread, {dt:.1f} s wall",
+                                "single_thread": {"value": v1, "unit": "gates/s",
+                                                  "sample": f"2 gates on 1 thread, {dt1:.1f} s wall"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
