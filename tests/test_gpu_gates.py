@@ -93,6 +93,28 @@ def test_flat_level_4096_sampled(torch_cuda, form):
     assert np.array_equal(got[sample], want)
 
 
+@pytest.mark.parametrize("G", [149, 301])
+def test_two_prime_form_wider_than_the_sms(torch_cuda, G):
+    """Levels wider than the SM count run the two-prime form as two 512-thread blocks per
+    SM, at odd widths too.  Every word equals the NTT form's over 2^64 - 2^32 + 1 (an
+    independent product), all outputs decrypt to the plaintext gates, and the first, a
+    middle and the last two gates match the oracle word for word."""
+    p = ti.STD
+    ctx, k = gpu_context(p, ti.SEED_FLAT)
+    b = ti.flat_level(G)
+    outs = {}
+    for form in (0, 2):
+        out = empty(torch_cuda, G, p.n + 1)
+        ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=form)
+        ctx.sync()
+        outs[form] = from_dev(out)
+    assert np.array_equal(outs[2], outs[0])
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, outs[2]), b.expected)
+    sample = [0, G // 2, G - 2, G - 1]
+    want = orc.gate_batch(p, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=sample)
+    assert np.array_equal(outs[2][sample], want)
+
+
 def test_zero_gates_is_noop(torch_cuda):
     ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
     t = empty(torch_cuda, 0)
