@@ -51,7 +51,9 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t w
     return x * w - __umulhi(x, ws) * p;
 }
 
-__device__ __forceinline__ uint32_t red_below(uint32_t a, uint32_t b) { return a >= b ? a - b : a; }
+// a - b if a >= b, else a (any a, b > 0): when a < b, a - b wraps above a, so the unsigned
+// minimum picks a; one subtraction and one min, no compare-and-select
+__device__ __forceinline__ uint32_t red_below(uint32_t a, uint32_t b) { return min(a, a - b); }
 
 // Montgomery reduction: T / 2^32 mod p in [0, 2p) for T < p 2^32
 __device__ __forceinline__ uint32_t redc32(uint64_t T, uint32_t p, uint32_t ninv) {
