@@ -30,10 +30,10 @@ namespace {
 
 // Coefficient j of X^k p over Torus64 (k in [0, 2N)).
 __device__ __forceinline__ uint64_t rot_coef64(const uint64_t *p, int N, int k, int j) {
-    int neg = 0;
-    if (k >= N) { k -= N; neg = 1; }
-    const uint64_t v = j >= k ? p[j - k] : 0ull - p[j - k + N];
-    return neg ? 0ull - v : v;
+    // s = j - k in (-2N, N): p[s mod N], negated once exactly when -N <= s < 0
+    const int s = j - k;
+    const uint64_t neg = (uint64_t)(int64_t)((s >> 31) & ~((s + N) >> 31));  // all ones or zero
+    return (p[s & (N - 1)] ^ neg) - neg;
 }
 
 // Signed gadget digits of a Torus64 value (l levels of Bgbit bits, round to nearest,

@@ -203,12 +203,11 @@ void tfhe_tc_free(tfhe_ctx *ctx);
 // Coefficient j of X^k * p (k in [0, 2N)) for a Torus32 polynomial p of degree < N:
 // X^k p has p_{j-k} at X^j for j >= k and -p_{j-k+N} below; X^k = -X^{k-N} for k >= N.
 __device__ __forceinline__ uint32_t rot_coef(const uint32_t *p, int N, int k, int j) {
-    int neg = 0;
-    if (k >= N) { k -= N; neg = 1; }
-    uint32_t v;
-    if (j >= k) v = p[j - k];
-    else v = 0u - p[j - k + N];
-    return neg ? 0u - v : v;
+    // s = j - k in (-2N, N): the source is p[s mod N], negated once exactly when
+    // -N <= s < 0 (X^N = -1; two wraps cancel).  N is a power of two.
+    const int s = j - k;
+    const uint32_t neg = (uint32_t)((s >> 31) & ~((s + N) >> 31));  // all ones or zero
+    return (p[s & (N - 1)] ^ neg) - neg;
 }
 
 // Signed gadget digits of t (l levels of Bgbit bits, rounding to nearest, digits in

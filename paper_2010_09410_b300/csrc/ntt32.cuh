@@ -61,9 +61,11 @@ __device__ __forceinline__ uint32_t redc32(uint64_t T, uint32_t p, uint32_t ninv
     return (uint32_t)((T + (uint64_t)m * p) >> 32);
 }
 
-// signed integer below 2^31 in magnitude -> residue in [0, p)
+// signed integer d, |d| < p, -> residue in [0, p): for d >= 0 the bit pattern u = d is
+// below u + p; for d < 0, u >= 2^31 exceeds u + p = p - |d|; the unsigned min picks it
 __device__ __forceinline__ uint32_t res_of_i32(int32_t d, uint32_t p) {
-    return d >= 0 ? (uint32_t)d : p - (uint32_t)(-d);
+    const uint32_t u = (uint32_t)d;
+    return min(u, u + p);
 }
 
 // CRT of canonical residues (r1 mod P1, r2 mod P2) -> the centred integer V, |V| < M/2
