@@ -221,7 +221,7 @@ __device__ __forceinline__ void extprod32(const uint32_t *d, const uint32_t *__r
 // word j of polynomial c of the product, mod 2^32
 __device__ __forceinline__ uint32_t prod32_word(const uint32_t *prod, int N, int c, int j) {
     const size_t o = (size_t)c * N + swz(j);
-    return (uint32_t)crt_centred(red_below(prod[o], NP1), red_below(prod[(size_t)2 * N + o], NP2));
+    return crt_lo32(red_below(prod[o], NP1), red_below(prod[(size_t)2 * N + o], NP2));
 }
 
 // One block per CMUX (x, y) = (blockIdx.x, blockIdx.y) of the geometry g:

@@ -68,13 +68,31 @@ __device__ __forceinline__ uint32_t res_of_i32(int32_t d, uint32_t p) {
     return min(u, u + p);
 }
 
-// CRT of canonical residues (r1 mod P1, r2 mod P2) -> the centred integer V, |V| < M/2
-__device__ __forceinline__ int64_t crt_centred(uint32_t r1, uint32_t r2) {
+// CRT of canonical residues (r1 mod P1, r2 mod P2): v = r1 + P1 h in [0, M) with
+// h = (r2 - r1) P1^{-1} mod P2.  The centred integer V is v - M when v > M/2.  As M is
+// odd and 0 <= r1 < P1, that holds exactly when h > (P2-1)/2, or h = (P2-1)/2 and
+// r1 > (P1-1)/2, so it is decided on 32-bit words.
+__device__ __forceinline__ uint32_t crt_digit(uint32_t r1, uint32_t r2) {
     const uint32_t r1m = red_below(r1, NP2);  // r1 < P1 < 2 P2
     const uint32_t dlt = red_below(r2 + NP2 - r1m, NP2);
-    const uint32_t h = red_below(shoup_mul(dlt, CRT_C, CRT_CS, NP2), NP2);
+    return red_below(shoup_mul(dlt, CRT_C, CRT_CS, NP2), NP2);
+}
+
+__device__ __forceinline__ bool crt_negative(uint32_t r1, uint32_t h) {
+    return h > (NP2 - 1) / 2 || (h == (NP2 - 1) / 2 && r1 > (NP1 - 1) / 2);
+}
+
+// -> the centred integer V, |V| < M/2
+__device__ __forceinline__ int64_t crt_centred(uint32_t r1, uint32_t r2) {
+    const uint32_t h = crt_digit(r1, r2);
     const uint64_t v = (uint64_t)r1 + (uint64_t)NP1 * h;  // in [0, M)
-    return v > CRT_M / 2 ? (int64_t)(v - CRT_M) : (int64_t)v;
+    return (int64_t)(v - (crt_negative(r1, h) ? CRT_M : 0ull));
+}
+
+// -> V mod 2^32
+__device__ __forceinline__ uint32_t crt_lo32(uint32_t r1, uint32_t r2) {
+    const uint32_t h = crt_digit(r1, r2);
+    return r1 + NP1 * h - (crt_negative(r1, h) ? (uint32_t)CRT_M : 0u);
 }
 
 // Cooley-Tukey, natural order in, bit-reversed evaluations out; values in [0, 2p).
