@@ -57,7 +57,7 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
 // level; NTT / two-prime NTT / tensor core L1 / L2): 64 gates 18.8 / 10.2 / 41.6 / 38.7;
 // 256: 34.0 / 16.7 / 44.8 / 44.8; 768: 94.6 / 44.7 / 46.6 / 49.7; 1024: 110 / 51.8 /
 // 48.8 / 52.1; 2048: 216 / 101 / 71.0 / 67.6; 4096: 428 / 200 / 137 / 120.  So the
-// two-prime per-gate form up to about 1,450 gates, Karatsuba level 1 to about 2,000,
+// two-prime per-gate form up to about 1,800 gates, Karatsuba level 1 to about 2,000,
 // level 2 beyond (the per-gate NTT form over 2^64 - 2^32 + 1 when the two-prime form
 // is not available: up to about 400 gates).
 void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
@@ -81,7 +81,7 @@ void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
         *level = best->level;
         return;
     }
-    if (width < (ctx->bsk_ntt2 ? 1440 : 384)) {
+    if (width < (ctx->bsk_ntt2 ? 1792 : 384)) {
         *form = ntt;
         return;
     }
