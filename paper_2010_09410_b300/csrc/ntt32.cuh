@@ -248,7 +248,8 @@ __device__ __forceinline__ void ntt32_fwd_pass(uint32_t *a, int np, int pst, con
                 if (k & half) continue;
                 const int j = k >> (R - q);
                 const uint32_t V = shoup_mul(v[k + half], w[2 * j], w[2 * j + 1], p);
-                const uint32_t U = red_below(v[k], p2);
+                // inputs of the first stage are below 2p already (the transform's contract)
+                const uint32_t U = (S == 0 && q == 0) ? v[k] : red_below(v[k], p2);
                 v[k] = U + V;
                 v[k + half] = U - V + p2;
             }
