@@ -7,14 +7,15 @@
 // whose residue mod 2^32 or mod 2^64 the callers take.  This replaces the 64-bit
 // arithmetic mod 2^64 - 2^32 + 1: 30-bit residues fit one 32-bit register, a twiddle
 // multiply is three 32-bit multiplies (Shoup's precomputed quotient), and butterflies
-// keep values lazily in [0, 2p) (Harvey's bounds), so there are few compare-and-subtract
-// steps.
+// keep values lazily below 2p or 4p (Harvey's bounds), so there are few conditional
+// subtractions, each an unsigned min.
 //
-// Layout: the transforms work in place on shared memory a[2 primes][np][N], prime-major;
-// the twiddle table is tw[2 primes][2][N][2]: for each prime the forward pairs
-// (psi^{brv(k)}, its Shoup quotient), then the inverse pairs (psi^{-brv(k)}, quotient),
-// psi a primitive 2N-th root of unity mod the prime.  A pair is one 8-byte load, and the
-// consecutive pairs a radix-8 group needs are one or two 16-byte loads.
+// Layout: the transforms work in place on shared memory a[2 primes][np][N], prime-major
+// (or with a given stride between the primes); the twiddle table is tw[2 primes][2][N][2]:
+// for each prime the forward pairs (psi^{brv(k)}, its Shoup quotient), then the inverse
+// pairs (psi^{-brv(k)}, quotient), psi a primitive 2N-th root of unity mod the prime.  A
+// pair is one 8-byte load, and the consecutive pairs of a group's stages are one 8-byte
+// load or one to four 16-byte loads.
 #pragma once
 
 #include "common.cuh"
