@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bg
 // with each external product computed by extprod32 against the BSK in the two-prime NTT
 // form (u32[n][2l][2][2 primes][N]).  Shared memory: digits, products, accumulator,
 // rotation difference and the twiddle table (112 KB at N = 1024, l = 3).
-__global__ void __launch_bounds__(1024) k_blind_rotate_ntt2(
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_blind_rotate_ntt2(
     int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
     uint32_t *__restrict__ acc_out, const uint32_t *__restrict__ bsk2p,
     const uint32_t *__restrict__ tw) {
@@ -412,17 +413,26 @@ int tfhe_blind_rotate_ntt2(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, in
     if (!ctx->bsk_ntt2)
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "two-prime NTT form not available here");
     const size_t smem = ((size_t)4 * p.l * p.N + (size_t)16 * p.N) * 4;
-    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt2,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
     if (!ctx->sms)
         TFHE_CUDA_TRY(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount,
                                                   ctx->device));
-    // one block per SM of 1024 threads while there are SMs to spare, else two of 512
-    const int threads = G <= ctx->sms ? 1024 : 512;
     StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_NTT, st);
-    k_blind_rotate_ntt2<<<G, threads, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar, acc,
-                                                  ctx->bsk_ntt2, ctx->tw32);
+    if (G <= ctx->sms) {
+        // one block per SM while there are SMs to spare: 512 threads with up to 128
+        // registers each
+        TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt2<512>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+        k_blind_rotate_ntt2<512><<<G, 512, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar,
+                                                       acc, ctx->bsk_ntt2, ctx->tw32);
+    } else {
+        // two blocks of 512 threads per SM (64 registers each)
+        TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_blind_rotate_ntt2<1024>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+        k_blind_rotate_ntt2<1024><<<G, 512, smem, st>>>(p.n, p.N, ctx->logN, p.l, p.Bgbit, bar,
+                                                        acc, ctx->bsk_ntt2, ctx->tw32);
+    }
     tm.stop();
     return tfhe_check_launch(ctx, "blind_rotate_ntt2");
 }
