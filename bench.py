@@ -155,33 +155,47 @@ def oracle_gates_per_s(batch, sample_gates, threads=None):
 
 
 def oracle_sample_size():
-    # 1.5-2.4 s per gate per core: eight rounds of one gate per core (10-30 s of work)
+    # cpu_baseline leg: 1.5-2.4 s per gate per core, eight rounds of one gate per core
+    # (10-30 s of work)
     cores = os.cpu_count() or 1
     return max(8, min(8 * cores, 512))
 
 
+def reference_step_gates():
+    # reference arm: one step = four rounds of one gate per core (about 6-10 s), so that
+    # the driver's --steps 20 --warmup 5 run stays within a few minutes
+    cores = os.cpu_count() or 1
+    return max(4, min(4 * cores, 256))
+
+
 def run_reference(args):
+    """The reference arm of this tier: the CPU oracle, as it stands, on the host cores.
+    One step = one bounded sample of the flat level's gates; the step time reported is
+    the sample's measured wall time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import tfhe_inputs as ti
     batch = ti.flat_level(args.gates)
-    sample = oracle_sample_size()
+    sample = reference_step_gates()
     for _ in range(args.warmup):
         oracle_gates_per_s(batch, min(sample, os.cpu_count() or 1))
-    vals, times = [], []
+    times = []
     cores = os.cpu_count() or 1
     for _ in range(args.steps):
-        v, cores, dt = oracle_gates_per_s(batch, sample)
-        vals.append(v)
+        _, cores, dt = oracle_gates_per_s(batch, sample)
         times.append(dt)
-    value = statistics.median(vals)
+    step_s = statistics.median(times)
+    value = sample / step_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * args.gates / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "gates": args.gates, "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOAD, "gates": args.gates, "sample_gates_per_step": sample,
+                   "l2": "n/a (CPU)"},
+        "ms_per_step_extrapolated_full_level": 1e3 * args.gates / value,
+        "timed_s_total": sum(times),
         "cpu_baseline": {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample} of the {args.gates} gates per step, one gate per "
                                    f"thread on {cores} host threads"},
@@ -304,7 +318,9 @@ def run_ours(args):
     h2d = h_in.nbytes + h_types.nbytes + h_idx.nbytes
     d2h = h_out.nbytes
 
-    roof = roofline(best, r, args.gates, p, ctx.tc_level() if best == "tc" else 0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = roofline(best, r, args.gates, p, ctx.tc_level() if best == "tc" else 0, sms)
+    roof_ks = roofline_keyswitch(r, args.gates, p)
     line = {
         "metric": METRIC, "value": r["gates_per_s"], "unit": "gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
@@ -321,6 +337,7 @@ def run_ours(args):
                        "decrypt_ok": v["decrypt_ok"]} if "gates_per_s" in v else v)
                   for n, v in results.items()},
         "roofline": roof,
+        "roofline_keyswitch": roof_ks,
         "e2e": {"value": e2e_val, "unit": "gates/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(r["launches"]),
@@ -375,70 +392,102 @@ def kernel_traffic(key, src):
     return rec["bytes"]
 
 
-def roofline(form, r, G, p, tc_level):
+# 2 * 128 * 128 * 16 flops in 64 cycles: one M = 128, N = 128, K = 16 bf16 MMA, the issue
+# rate measured on this B300 for the tensor-core BlindRotate's instruction shape
+TC_FLOP_PER_CLK_SM = 8192
+# 32-bit integer multiply (IMAD) lanes per SM and clock (CUDA programming guide
+# throughput table for recent architectures)
+IMAD_LANES = 64
+
+
+def roofline(form, r, G, p, tc_level, sms):
     """Roofline of the dominant kernel of the measured form.
 
-    Two-prime NTT form: k_blind_rotate_ntt2, the same transforms and products modulo two
-    30-bit primes; each 32-bit modular multiply counted as 3 32-bit multiplies (Shoup).
+    TC form: k_tc_blind_rotate, the persistent tensor-core BlindRotate (one launch per
+    level, timed alone by its own events), bound by the bf16 tensor pipe.  The external
+    product of a gate and step, as dense negacyclic N-products on the 4 byte planes of the
+    key, is 2 * (2lN) * (2N) * 4 flops (100.7 M at N = 1024, l = 3); with L Karatsuba
+    levels the kernel executes (3/4)^L of that on the tensor pipe.  achieved / frac count
+    the executed flops against the measured sustained bf16 peak (a long kernel under the
+    power cap); `per_clock` divides by SM count and the median SM clock sampled during the
+    timed region, against the 8,192 flop/clk/SM of the kernel's MMA shape;
+    `dense_equivalent_tflops` is the rate in the dense count (no fraction: it is not work
+    the kernel does).
 
-    NTT form: k_blind_rotate_ntt, bound by integer ALU throughput.  Algorithmic work per
-    gate and BlindRotate step: 2l forward and 2 inverse N-point NTTs (N/2 log2 N
-    butterflies each, one modular multiply per butterfly) and 4lN pointwise products:
-    53,248 multiplies mod P at N = 1024, l = 3.  One 64x64-bit product needs at least
-    4 32-bit multiplies and 4 more for the high halves, so it is counted as 8 32-bit
-    integer multiply instructions.  Peak = 148 SMs x 128 lanes x the max SM clock.
-
-    TC form: the persistent tensor-core BlindRotate (one launch per level), bound by the
-    bf16 tensor pipe.  Algorithmic work per gate and step: the external product as 2 x 2l
-    dense negacyclic N-products, each N^2 multiply-adds on each of the 4 byte planes of
-    the key, i.e. 2 * (2lN) * (2N) * 4 flops (100.7 M at N = 1024, l = 3); n steps per
-    launch.  With L Karatsuba levels the kernel executes (3/4)^L of that on the tensor
-    pipe, reported as `executed` beside the algorithmic figure.  The launch duration is
-    the stage's event time (accumulator init and final re-layout, tens of microseconds,
-    + the kernel).
+    Two-prime NTT form: k_blind_rotate_ntt2, transforms and products modulo two 30-bit
+    primes, each 32-bit modular multiply counted as 3 integer multiplies (Shoup).
+    NTT form: k_blind_rotate_ntt, 53,248 multiplies mod 2^64 - 2^32 + 1 per gate and step
+    at N = 1024, l = 3, each counted as 8 32-bit integer multiplies.  Both are bound by
+    integer multiply throughput: peak = SMs x 64 IMAD lanes x the max SM clock.
     """
     mp, kind = peaks()
     logN = p.N.bit_length() - 1
     steps = p.n  # every step counted (a zero rotation, probability 1/2N, is skipped)
-    if form == "ntt2":
-        ms, launches = r["stages"]["blind_rotate_ntt"]
-        per_launch_s = ms / 1e3 / max(launches, 1)
-        mulmods = 2 * ((2 * p.l + 2) * (p.N // 2) * logN + 4 * p.l * p.N)  # both primes
-        ops = G * steps * mulmods * 3
-        achieved = ops / per_launch_s / 1e12
-        peak = 148 * 128 * mp.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        return {"bound": "alu", "kernel": "k_blind_rotate_ntt2", "achieved": achieved,
-                "peak": peak, "unit": "T int32-mul-op/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": "derived from SM count, lanes and max clock",
-                "work": f"{mulmods} 32-bit mulmods/gate-step (two primes) x 3 int32 multiplies"}
-    if form == "ntt":
+    clk = (r.get("clocks") or {}).get("sm_mhz") or mp.get("sm_max_mhz", 2032.0)
+    alu_peak = sms * IMAD_LANES * mp.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    alu_kind = f"derived: {sms} SMs x {IMAD_LANES} IMAD lanes x max SM clock"
+    if form in ("ntt2", "ntt"):
         ms, launches = r["stages"]["blind_rotate_ntt"]
         per_launch_s = ms / 1e3 / max(launches, 1)
         mulmods = (2 * p.l + 2) * (p.N // 2) * logN + 4 * p.l * p.N
-        ops = G * steps * mulmods * 8
+        if form == "ntt2":
+            ops, work = G * steps * 2 * mulmods * 3, f"{2 * mulmods} 32-bit mulmods/gate-step (two primes) x 3 int32 multiplies"
+        else:
+            ops, work = G * steps * mulmods * 8, f"{mulmods} mulmods/gate-step x 8 int32 multiplies"
         achieved = ops / per_launch_s / 1e12
-        peak = 148 * 128 * mp.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        return {"bound": "alu", "kernel": "k_blind_rotate_ntt", "achieved": achieved,
-                "peak": peak, "unit": "T int32-mul-op/s", "frac": achieved / peak,
-                "traffic": kernel_traffic("k_blind_rotate_ntt", "ntt.cu"),
-                "peak_kind": "derived from SM count, lanes and max clock",
-                "work": f"{mulmods} mulmods/gate-step x 8 int32 multiplies"}
-    ms, kernels = r["stages"]["blind_rotate_tc"]
-    per_launch_s = ms / 1e3 / max(kernels // 3, 1)  # three kernels per BlindRotate
+        kern = "k_blind_rotate_ntt2" if form == "ntt2" else "k_blind_rotate_ntt"
+        return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": alu_peak,
+                "unit": "T int32-mul-op/s", "frac": achieved / alu_peak,
+                "traffic": kernel_traffic(kern, "ntt.cu"), "peak_kind": alu_kind, "work": work,
+                "launch_ms": per_launch_s * 1e3}
+    ms, launches = r["stages"]["blind_rotate_tc"]
+    per_launch_s = ms / 1e3 / max(launches, 1)
     planes = 4
-    flops = G * steps * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
-    executed = flops * 0.75 ** tc_level
-    achieved = flops / per_launch_s / 1e12
+    dense = G * steps * 2 * (2 * p.l * p.N) * (2 * p.N) * planes
+    executed = dense * 0.75 ** tc_level
+    achieved = executed / per_launch_s / 1e12
     peak = mp["bf16_tflops_sustained"]
+    per_clk = achieved * 1e12 / (sms * clk * 1e6)
     return {"bound": "tensor", "kernel": f"k_tc_blind_rotate<{tc_level}>", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": kernel_traffic(f"k_tc_blind_rotate<{tc_level}>", "tc.cu"),
-            "peak_kind": f"bf16 sustained (cuBLAS loop), of {kind}",
-            "work": f"n*2*(2lN)*(2N)*{planes} flops per gate per launch (dense negacyclic "
-                    f"products on 4 key byte planes)",
-            "executed": {"karatsuba_levels": tc_level,
-                         "achieved": executed / per_launch_s / 1e12,
-                         "frac": executed / per_launch_s / 1e12 / peak}}
+            "peak_kind": f"bf16 sustained (cuBLAS loop under the power cap), of {kind}",
+            "work": f"executed on the tensor pipe: (3/4)^{tc_level} x n*2*(2lN)*(2N)*{planes} "
+                    f"flops per gate per launch (Karatsuba level {tc_level} of the dense "
+                    f"negacyclic products on 4 key byte planes)",
+            "launch_ms": per_launch_s * 1e3,
+            "per_clock": {"sm_mhz": clk, "sms": sms, "flop_per_clk_per_sm": per_clk,
+                          "frac_of_mma_rate": per_clk / TC_FLOP_PER_CLK_SM,
+                          "mma_rate": f"{TC_FLOP_PER_CLK_SM} flop/clk/SM (M128 N128 K16 bf16 in 64 cycles)"},
+            "dense_equivalent_tflops": dense / per_launch_s / 1e12}
+
+
+def roofline_keyswitch(r, G, p):
+    """SampleExtract + identity key switch (k_extract_keyswitch_staged), one launch per
+    level.  Algorithmic DRAM bytes per launch: the re-laid-out KSK once (N t (base-1)
+    rows of n_pad words), the extracted accumulator words of every gate ((N + 1) words)
+    and the output TLWEs ((n + 1) words); achieved = those bytes / the launch time, against
+    the measured HBM copy bandwidth.  The kernel stages each KSK row in shared memory once
+    per 16 gates and every gate adds it from there, so in practice it is bound by those
+    shared-memory reads (`smem_gathered`)."""
+    mp, kind = peaks()
+    ms, launches = r["stages"].get("keyswitch", (0.0, 0))
+    if not launches:
+        return None
+    per_launch_s = ms / 1e3 / launches
+    n_pad = (p.n + 1 + 3) // 4 * 4
+    base = 1 << p.ks_basebit
+    ksk = p.N * p.ks_t * (base - 1) * n_pad * 4
+    io = G * ((p.N + 1) + (p.n + 1)) * 4
+    gathered = G * p.N * p.ks_t * n_pad * 4
+    achieved = (ksk + io) / per_launch_s / 1e9
+    return {"bound": "hbm", "kernel": "k_extract_keyswitch_staged", "achieved": achieved,
+            "peak": mp["hbm_gbs"], "unit": "GB/s", "frac": achieved / mp["hbm_gbs"],
+            "traffic": kernel_traffic("k_extract_keyswitch_staged", "gate.cu"),
+            "peak_kind": f"HBM copy bandwidth, of {kind}", "launch_ms": per_launch_s * 1e3,
+            "algorithmic_bytes": ksk + io,
+            "smem_gathered": {"bytes": gathered, "tb_per_s": gathered / per_launch_s / 1e12,
+                              "what": "KSK rows added from shared memory, N*t per gate"}}
 
 
 # ---------------------------------------------------------------------------

@@ -103,6 +103,13 @@ void tfhe_ctx_destroy(tfhe_ctx *ctx);
  * Valid until the next call on the context. */
 const char *tfhe_last_error(const tfhe_ctx *ctx);
 
+/* The same text copied into a caller buffer: writes at most len - 1 bytes of it and a
+ * terminating NUL into buf (nothing if buf is NULL or len <= 0) and returns the text's
+ * full length in bytes, so a return value >= len means it was truncated.  Safe to keep
+ * after later calls on the context.  TFHE_EINVAL for a NULL context (buf, if usable,
+ * receives ""). */
+int tfhe_last_error_string(const tfhe_ctx *ctx, char *buf, int len);
+
 /* Load the bootstrapping and key-switching keys (device pointers, layouts above).
  * The context copies and re-lays them out on `stream` (NTT-domain BSK for the NTT
  * form, raw BSK for the TC form, KSK rows without the v = 0 entries and padded to
@@ -180,9 +187,9 @@ int tfhe_ctx_set_tc_pass_limit(tfhe_ctx *ctx, int limit);
 enum {
     TFHE_STAGE_COMBINE = 0,          /* gate linear combination + ModSwitch (one launch) */
     TFHE_STAGE_BLIND_ROTATE_NTT = 1, /* whole BlindRotate, NTT form (one launch) */
-    TFHE_STAGE_RESERVED_2 = 2,       /* unused */
-    TFHE_STAGE_BLIND_ROTATE_TC = 3,  /* whole BlindRotate, TC form: accumulator init +
-                                        one persistent launch */
+    TFHE_STAGE_TC_AUX = 2,           /* TC form: accumulator initialisation and the final
+                                        re-layout of the accumulators (two launches) */
+    TFHE_STAGE_BLIND_ROTATE_TC = 3,  /* TC form: the persistent BlindRotate launch alone */
     TFHE_STAGE_KEYSWITCH = 4,        /* SampleExtract + identity key switch (one launch) */
     TFHE_STAGE_CMUX = 5,             /* CMUX batches, tree levels, RAM write */
     TFHE_STAGE_CB_BLIND_ROTATE = 6,  /* circuit bootstrapping: lvl2 BlindRotates (one launch) */
@@ -245,11 +252,14 @@ int tfhe_gate_batch_host(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
  * 2 MiB scratch array compiled into the library, which every GPU that loads the
  * library holds until the process exits.  It therefore accepts at most
  * G * ((n+1) + 2N) * 4 bytes (rounded) of scratch: 195 gates at n = 630, N = 1024;
- * larger batches return TFHE_EINVAL without enqueueing anything.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls on a device share the one array: calls
- * whose work overlaps on the GPU (other streams, other contexts) race and must be
- * serialised by the caller.  Calls no cudaMalloc, cudaFree or allocating routine. */
+ * larger batches return TFHE_EINVAL without enqueueing anything.  tfhe_ctx_create
+ * looks up the array's device address (cudaGetSymbolAddress, which under lazy module
+ * loading loads the array's module and so allocates it) and loads the kernels this
+ * entry point launches; a call then only reads the stored address.  The address belongs
+ * to the CUDA context current at tfhe_ctx_create: after a device reset, create new
+ * contexts.  All calls on a device share the one array: calls whose work overlaps on
+ * the GPU (other streams, other contexts) race and must be serialised by the caller.
+ * Calls no cudaMalloc, cudaFree or allocating routine. */
 int tfhe_gate_batch_noalloc(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in,
                             const uint8_t *types, const int32_t *in_idx, uint32_t *out, int G,
                             void *stream);

@@ -31,6 +31,7 @@ GATES = ["NAND", "AND", "OR", "NOR", "XOR", "XNOR", "ANDNY", "ANDYN", "ORNY", "O
 # every symbol the public header declares
 EXPORTS = [
     "tfhe_version", "tfhe_ctx_create", "tfhe_ctx_destroy", "tfhe_last_error",
+    "tfhe_last_error_string",
     "tfhe_ctx_set_keys", "tfhe_ctx_reserve", "tfhe_ctx_sync", "tfhe_gate_batch",
     "tfhe_gate_batch_host", "tfhe_blind_rotate", "tfhe_extract_keyswitch", "tfhe_cmux_batch",
     "tfhe_cmux_tree_read", "tfhe_ram_write", "tfhe_circuit_plan", "tfhe_plan_num_levels",
@@ -53,7 +54,7 @@ EXPORTS = [
     "tfhe_private_keyswitch",
     "tfhe_ctx_probe_wait",
 ]
-STAGES = ["combine", "blind_rotate_ntt", "reserved_2", "blind_rotate_tc", "keyswitch", "cmux",
+STAGES = ["combine", "blind_rotate_ntt", "tc_aux", "blind_rotate_tc", "keyswitch", "cmux",
           "cb_blind_rotate", "cb_keyswitch"]
 NUM_STAGES = 8
 
@@ -92,6 +93,7 @@ def lib():
         "tfhe_ctx_create": (i32, [ctypes.POINTER(CParams), i32, ctypes.POINTER(vp)]),
         "tfhe_ctx_destroy": (None, [vp]),
         "tfhe_last_error": (ctypes.c_char_p, [vp]),
+        "tfhe_last_error_string": (i32, [vp, ctypes.c_char_p, i32]),
         "tfhe_ctx_set_keys": (i32, [vp, vp, vp, vp]),
         "tfhe_ctx_reserve": (i32, [vp, i32]),
         "tfhe_ctx_sync": (i32, [vp, vp]),

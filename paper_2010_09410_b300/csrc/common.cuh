@@ -86,6 +86,11 @@ struct tfhe_ctx {
 
     int *d_err = nullptr;  // device error word (0 = ok, else a TFHE_E* code)
 
+    // device address of the no-allocation entry point's fixed scratch array (noalloc.cu),
+    // resolved at context creation; null (with the cause) if that failed
+    uint32_t *noalloc_scratch = nullptr;
+    std::string noalloc_err;
+
     // per-kernel timing (tfhe_ctx_enable_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -125,6 +130,9 @@ int tfhe_set_error(tfhe_ctx *ctx, int code, const std::string &msg);
 int tfhe_check_launch(tfhe_ctx *ctx, const char *what);
 int tfhe_ensure_workspace(tfhe_ctx *ctx, int gates);
 int tfhe_ensure_trgsw_ws(tfhe_ctx *ctx, size_t count);
+
+// noalloc.cu: resolve the fixed scratch array and load the kernels of its entry point
+int tfhe_noalloc_prepare(tfhe_ctx *ctx);
 
 // ntt.cu
 int tfhe_ntt_setup(tfhe_ctx *ctx);

@@ -26,6 +26,20 @@ extern "C" const char *tfhe_last_error(const tfhe_ctx *ctx) {
     return ctx ? ctx->err.c_str() : "null context";
 }
 
+extern "C" int tfhe_last_error_string(const tfhe_ctx *ctx, char *buf, int len) {
+    if (!ctx) {
+        if (buf && len > 0) buf[0] = 0;
+        return TFHE_EINVAL;
+    }
+    const std::string &m = ctx->err;
+    if (buf && len > 0) {
+        const size_t k = m.size() < (size_t)(len - 1) ? m.size() : (size_t)(len - 1);
+        memcpy(buf, m.data(), k);
+        buf[k] = 0;
+    }
+    return (int)(m.size() < 0x7FFFFFFF ? m.size() : 0x7FFFFFFF);
+}
+
 static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 extern "C" int tfhe_ctx_create(const tfhe_params *params, int device, tfhe_ctx **out) {
@@ -58,6 +72,10 @@ extern "C" int tfhe_ctx_create(const tfhe_params *params, int device, tfhe_ctx *
         tfhe_ctx_destroy(ctx);
         return rc;
     }
+    // Loads the module of the no-allocation entry point's scratch array now, while the
+    // caller may allocate (failure only disables that entry point).
+    tfhe_noalloc_prepare(ctx);
+    ctx->err.clear();
     *out = ctx;
     return TFHE_OK;
 }

@@ -656,6 +656,17 @@ int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *
     return launch_extract_keyswitch(ctx, acc, out, G, types, idx, num_in, st);
 }
 
+// Load the combination and key-switch kernels now (lazy module loading would otherwise
+// load their code, allocating device memory, at their first launch).
+int tfhe_preload_gate_kernels(tfhe_ctx *ctx) {
+    cudaFuncAttributes fa;
+    TFHE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_combine_modswitch));
+    TFHE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_extract_keyswitch_staged));
+    TFHE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_extract_keyswitch_b2));
+    TFHE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_extract_keyswitch<KS_GT>));
+    return TFHE_OK;
+}
+
 // ---- HomMUX batches ----------------------------------------------------------------
 
 static int mux_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const int32_t *idx3,

@@ -1,6 +1,14 @@
 // noalloc.cu -- tfhe_gate_batch_noalloc: the NTT-form gate batch with its scratch in a
-// fixed device array that the library owns from load time, for callers that must not
-// allocate device memory while they run.
+// fixed device array compiled into the library, for callers that must not allocate
+// device memory while they run.
+//
+// Under lazy module loading (the CUDA default) the array's module is loaded, and its
+// memory allocated, the first time host code touches one of its symbols.  So
+// tfhe_ctx_create calls tfhe_noalloc_prepare, which looks the array's device address up
+// (loading the module) and loads the kernels the entry point launches, while the caller
+// may still allocate; the address is kept in the context.  A call of the entry point
+// then only reads it.  A context lives inside one CUDA context: after a device reset
+// the caller creates new contexts, which resolve the address again.
 //
 // The scratch is one file-scope __device__ array shared by every call on a device:
 // the ModSwitched combinations u32[G][n+1] followed (at a 256-byte boundary) by the
@@ -9,8 +17,6 @@
 // acc), so nothing needs clearing between calls; but two calls whose kernels overlap
 // on the GPU (different streams, or different contexts on the same device) share the
 // array and race.
-#include <mutex>
-
 #include "common.cuh"
 
 int tfhe_launch_combine(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,
@@ -23,28 +29,30 @@ int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *
 static constexpr size_t kScratchWords = (size_t)1 << 19;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
-// Device address of g_noalloc_scratch per device.  In host code the array's name is
-// only a host-side stand-in, so the address is looked up once per device (with that
-// device current) and cached.
-static constexpr int kMaxDevices = 128;
-static std::mutex g_scratch_mu;
-static uint32_t *g_scratch_addr[kMaxDevices];
+int tfhe_preload_gate_kernels(tfhe_ctx *ctx);
+int tfhe_preload_ntt_kernels(tfhe_ctx *ctx);
 
-static int scratch_address(tfhe_ctx *ctx, uint32_t **out) {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    const int dev = ctx->device;
-    if (dev < 0 || dev >= kMaxDevices)
-        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "gate_batch_noalloc: device id too large");
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return tfhe_set_error(ctx, TFHE_ECUDA,
-                                  std::string("gate_batch_noalloc: scratch address lookup: ") +
-                                      cudaGetErrorString(e));
-        g_scratch_addr[dev] = (uint32_t *)p;
+// Device address of g_noalloc_scratch for the context's device (current when called).
+// In host code the array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress.  Also loads the kernels the entry point launches.  Not fatal for
+// the context: on failure the entry point reports the recorded cause.
+int tfhe_noalloc_prepare(tfhe_ctx *ctx) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        ctx->noalloc_scratch = nullptr;
+        ctx->noalloc_err = std::string("scratch address lookup: ") + cudaGetErrorString(e);
+        return TFHE_ECUDA;
     }
-    *out = g_scratch_addr[dev];
+    int rc = tfhe_preload_gate_kernels(ctx);
+    if (rc == TFHE_OK) rc = tfhe_preload_ntt_kernels(ctx);
+    if (rc != TFHE_OK) {
+        ctx->noalloc_scratch = nullptr;
+        ctx->noalloc_err = "kernel preload: " + ctx->err;
+        return rc;
+    }
+    ctx->noalloc_scratch = (uint32_t *)p;
     return TFHE_OK;
 }
 
@@ -71,14 +79,15 @@ extern "C" int tfhe_gate_batch_noalloc(tfhe_ctx *ctx, const uint32_t *in, int64_
                 " bytes; use at most about " + std::to_string(kScratchWords / per) +
                 " gates per call with these parameters");
     }
+    uint32_t *scratch = ctx->noalloc_scratch;  // resolved by tfhe_ctx_create
+    if (!scratch)
+        return tfhe_set_error(ctx, TFHE_ECUDA, "gate_batch_noalloc: scratch unavailable (" +
+                                                   ctx->noalloc_err + ")");
     TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    uint32_t *scratch = nullptr;
-    int rc = scratch_address(ctx, &scratch);
-    if (rc != TFHE_OK) return rc;
     uint32_t *bar = scratch;
     uint32_t *acc = scratch + bar_words;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = tfhe_launch_combine(ctx, in, num_in, types, in_idx, bar, G, st);
+    int rc = tfhe_launch_combine(ctx, in, num_in, types, in_idx, bar, G, st);
     if (rc != TFHE_OK) return rc;
     rc = tfhe_blind_rotate_ntt(ctx, bar, acc, G, st);
     if (rc != TFHE_OK) return rc;

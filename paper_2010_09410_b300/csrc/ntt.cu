@@ -384,6 +384,13 @@ int tfhe_trgsw_to_ntt(tfhe_ctx *ctx, const uint32_t *trgsw, uint64_t *out, size_
     return tfhe_check_launch(ctx, "polys_to_ntt");
 }
 
+// Load the per-gate NTT BlindRotate kernel now (see tfhe_preload_gate_kernels).
+int tfhe_preload_ntt_kernels(tfhe_ctx *ctx) {
+    cudaFuncAttributes fa;
+    TFHE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_blind_rotate_ntt));
+    return TFHE_OK;
+}
+
 int tfhe_blind_rotate_ntt(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
                           cudaStream_t st) {
     const tfhe_params &p = ctx->p;

@@ -1509,20 +1509,26 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     } else {
         cfg.gridDim = dim3((unsigned)(args.total_e < w->sms ? args.total_e : w->sms));
     }
-    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
     {
+        StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
         const size_t total = (size_t)tiles_pad * 2 * p.N * TILE_M;
         k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, tiles_pad, bar,
                                                                       w->acc_t);
+        ta.stop();
         rc = tfhe_check_launch(ctx, "tc_init_acc");
         if (rc != TFHE_OK) return rc;
     }
-    TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
-    rc = tfhe_check_launch(ctx, "tc blind rotate");
-    if (rc != TFHE_OK) return rc;
+    {
+        StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
+        TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
+        tm.stop();
+        rc = tfhe_check_launch(ctx, "tc blind rotate");
+        if (rc != TFHE_OK) return rc;
+    }
+    StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
     k_tc_untile_acc<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * tiles), 2), dim3(32, 8), 0, st>>>(
         p.N, G, w->acc_t, acc);
-    tm.stop(3);
+    ta.stop();
     return tfhe_check_launch(ctx, "tc untile accumulators");
 }
 

@@ -43,10 +43,27 @@ def test_cmux_tree_read_toy_every_address(torch_cuda, form):
         assert np.array_equal(orc.trlwe_decrypt(k.s1, got[r]), rom.table_bits[rom.addrs[r]])
 
 
+_TREE_WANT = {}
+
+
+def tree_read_sample(rom):
+    """Eight of the 64 reads (the first, the last and six seeded others) with the oracle's
+    words, computed once (in threads: the C oracle releases the interpreter lock)."""
+    if not _TREE_WANT:
+        from concurrent.futures import ThreadPoolExecutor
+        reads = sorted({0, 63} | set(int(r) for r in
+                                     np.random.default_rng(11).choice(np.arange(1, 63), 6, replace=False)))
+        with ThreadPoolExecutor(len(reads)) as ex:
+            want = list(ex.map(lambda r: orc.cmux_tree_read(ti.STD, rom.addr_trgsw[r], rom.table, 9),
+                               reads))
+        _TREE_WANT.update(zip(reads, want))
+    return _TREE_WANT
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_cmux_tree_read_512_rows_64_reads(torch_cuda, form):
     """512-row table, 9 address bits, 64 reads: all reads decrypt to the addressed row,
-    sampled reads match the oracle word for word."""
+    eight reads match the oracle word for word."""
     p = ti.STD
     rom = ti.cmux_rom()
     ctx, k = gpu_context(p, ti.SEED_CMUX)
@@ -56,8 +73,10 @@ def test_cmux_tree_read_512_rows_64_reads(torch_cuda, form):
     got = from_dev(out)
     for r in range(64):
         assert np.array_equal(orc.trlwe_decrypt(k.s1, got[r])[:32], rom.table_bits[rom.addrs[r], :32])
-    for r in (0, 63):
-        assert np.array_equal(got[r], orc.cmux_tree_read(p, rom.addr_trgsw[r], rom.table, 9)), r
+    want = tree_read_sample(rom)
+    assert len(want) == 8
+    for r, w in want.items():
+        assert np.array_equal(got[r], w), r
 
 
 @pytest.mark.parametrize("form", FORMS)

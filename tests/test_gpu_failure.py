@@ -47,3 +47,24 @@ def test_wait_arguments_checked_on_host(torch_cuda):
             ctx.probe_wait(flag, 1, bad)
         assert e.value.code == -1
     ctx.sync()
+
+
+def test_last_error_string_copies_and_truncates(torch_cuda):
+    """tfhe_last_error_string copies the context's last error text (the same text
+    tfhe_last_error returns), NUL-terminated, truncated to the buffer, and returns the
+    text's full length."""
+    import ctypes
+    import paper_2010_09410_b300 as tb
+    ctx, _ = gpu_context(ti.STD, ti.SEED_FLAT)
+    with pytest.raises(tb.TfheError):
+        ctx.set_tc_pass_limit((1 << 17) + 1)
+    L = tb.lib()
+    text = L.tfhe_last_error(ctx.h)
+    assert text
+    big = ctypes.create_string_buffer(len(text) + 16)
+    assert L.tfhe_last_error_string(ctx.h, big, len(big)) == len(text)
+    assert big.value == text
+    small = ctypes.create_string_buffer(b"#" * 8)
+    assert L.tfhe_last_error_string(ctx.h, small, 8) == len(text)
+    assert small.value == text[:7]
+    assert L.tfhe_last_error_string(ctx.h, None, 0) == len(text)

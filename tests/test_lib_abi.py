@@ -45,6 +45,9 @@ def test_null_arguments_rejected_without_device(L):
     assert L.tfhe_cmux_tree_read(None, None, None, 9, None, 1, 0, None) == -1
     assert L.tfhe_plan_run(None, None, None, 0, None, None) == -1
     assert L.tfhe_plan_num_levels(None) == -1
+    buf = ctypes.create_string_buffer(b"x" * 8)
+    assert L.tfhe_last_error_string(None, buf, 8) == -1 and buf.value == b""
+    assert L.tfhe_last_error_string(None, None, 0) == -1
     L.tfhe_ctx_destroy(None)
     L.tfhe_plan_destroy(None)
 

@@ -27,6 +27,32 @@ def call_noalloc(ctx, inp, types, idx, out, torch):
                                             types.numel(), stream)
 
 
+def test_noalloc_call_leaves_free_device_memory_unchanged(torch_cuda):
+    """The context resolves the scratch array (and loads the entry point's kernels) when it
+    is created, so not even the first call of the process allocates: free device memory
+    (cudaMemGetInfo) is the same before and after it."""
+    torch = torch_cuda
+    params = ti.STD
+    ctx, k = gpu_context(params, ti.SEED_FLAT)
+    G = 64
+    bits = ti.random_bits(ti.SEED_FLAT, 490, 2 * G)
+    inp = to_dev(ti.encrypt_tlwe0_bits(params, ti.SEED_FLAT, 490, k.s0, bits))
+    types = to_dev(ti.random_below(ti.SEED_FLAT, 491, G, 10).astype(np.uint8))
+    idx = to_dev(np.arange(2 * G, dtype=np.int32).reshape(G, 2))
+    got = torch.zeros((G, params.n + 1), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert call_noalloc(ctx, inp, types, idx, got, torch) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    ctx.sync()
+    assert free1 == free0, (free0, free1)
+    ref = torch.zeros_like(got)
+    ctx.gate_batch(inp, types, idx, ref)
+    ctx.sync()
+    assert np.array_equal(from_dev(got), from_dev(ref))
+
+
 @pytest.mark.parametrize("params,seed,sizes", [
     (ti.TOY, ti.SEED_TOY, (40, 23)),
     (ti.STD, ti.SEED_FLAT, (37, 195)),
