@@ -229,6 +229,30 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// A-operand collector buffer: the MMAs of one K-step multiply the same digit block A by
+// the four key planes, so the first of them reads A from shared memory into the
+// collector (fill), the next two reuse it (use) and the last reuses and releases it
+// (lastuse).  COLL: 0 fill, 1 use, 2 lastuse.  Cuts the A reads from shared memory 4x.
+template <int COLL>
+__device__ __forceinline__ void mma_bf16_coll(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc) {
+    if constexpr (COLL == 0)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, 1, 1;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc));
+    else if constexpr (COLL == 1)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, 1, 1;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, 1, 1;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc));
+}
+
 // Pair form: one thread of the even CTA issues an M = 256 MMA whose A rows 0-127 and
 // B columns 0 .. N/2-1 come from its own shared memory and A rows 128-255 and B columns
 // N/2 .. N-1 from the odd CTA's (same offsets); rows 0-127 of D go to the even CTA's
@@ -762,13 +786,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 #pragma unroll
                         for (int kk = 0; kk < KS / 16; kk++) {
                             const uint64_t ad = a_desc + (uint64_t)(kk * 256 / 16);
+                            if constexpr (PAIR) {
 #pragma unroll
-                            for (int p = 0; p < PLANES; p++) {
-                                const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
-                                if constexpr (PAIR)
+                                for (int p = 0; p < PLANES; p++) {
+                                    const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
                                     mma_bf16_pair(tmem + p * NB, ad, bd, idesc, 1u);
-                                else
-                                    mma_bf16(tmem + p * NB, ad, bd, idesc, 1u);
+                                }
+                            } else {
+                                static_assert(PLANES == 4, "collector sequence assumes 4 planes");
+                                const uint64_t bd = b_desc + (uint64_t)(kk * 256 / 16);
+                                mma_bf16_coll<0>(tmem, ad, bd, idesc);
+                                mma_bf16_coll<1>(tmem + NB, ad, bd + BPL / 16, idesc);
+                                mma_bf16_coll<1>(tmem + 2 * NB, ad, bd + 2 * BPL / 16, idesc);
+                                mma_bf16_coll<2>(tmem + 3 * NB, ad, bd + 3 * BPL / 16, idesc);
                             }
                         }
                     }
