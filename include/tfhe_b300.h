@@ -144,7 +144,7 @@ int tfhe_ctx_sync(tfhe_ctx *ctx, void *stream);
 int tfhe_ctx_probe_wait(tfhe_ctx *ctx, const uint32_t *flag, uint32_t target, int64_t max_cycles,
                         void *stream);
 
-/* Karatsuba levels of the tensor-core form (0, 1 or 2; -1 selects the default: 2 for
+/* Karatsuba levels of the tensor-core form (0 .. 3; -1 selects the default: 2 for
  * N >= 1024, 1 for N = 512, else 0).  Level L computes each negacyclic product as 3^L Toeplitz products of
  * size N / 2^L (3/4 of the multiply-adds per level); results are identical for every
  * level.  Needs N / 2^L >= 128.  If keys are loaded, re-expands the key windows on the

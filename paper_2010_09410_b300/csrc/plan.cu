@@ -353,7 +353,7 @@ extern "C" int tfhe_ctx_autotune(tfhe_ctx *ctx, int max_gates, void *stream) {
     std::vector<std::pair<int, int>> cand = {{TFHE_FORM_NTT, -1}};
     if (ctx->bsk_ntt2) cand.push_back({TFHE_FORM_NTT2, -1});
     if (tfhe_tc_supported(ctx))
-        for (int L = 0; L <= 2; L++)
+        for (int L = 0; L <= 3; L++)
             if (tfhe_tc_ensure_level(ctx, L, st) == TFHE_OK) cand.push_back({TFHE_FORM_TC, L});
     ctx->err.clear();
     std::vector<int> widths;

@@ -4,8 +4,8 @@
 // digits D (|d| <= Bg/2 <= 32) by the negacyclic Toeplitz matrices of the key
 // polynomials q = BSK_i[r][c] (T[n][k] = q[n-k] for n >= k, -q[n-k+N] otherwise):
 //   Y[g][c][n] = sum_{r < 2l} sum_{k < N} D_g[r][k] * T_{r,c}[n][k]   (mod 2^32).
-// It runs on the sm_103a tensor cores (tcgen05.mma kind::f16, bf16 operands, fp32
-// accumulators in TMEM).  bf16 holds small integers exactly: the (combined) digits and
+// It runs on the sm_103a tensor cores (tcgen05.mma kind::f16, fp16 operands, fp32
+// accumulators in TMEM).  fp16 holds small integers exactly: the (combined) digits and
 // the signed byte planes of the key, q = sum_p 2^{8p} q_p with q_p in [-128, 128).  Each
 // accumulation covers the l rows of one polynomial of the TRLWE and is read out of TMEM,
 // rounded to int32 and recombined mod 2^32 as sum_p 2^{8p} Y_p.
@@ -23,7 +23,7 @@
 // The Toeplitz operand is never materialised.  Row n' of a size-s Toeplitz matrix with
 // generator t (T[n'][k'] = t[n'-k']) is the window r_vec[s-1-n'+k'] of
 // r_vec[x] = t[s-1-x] (x < 2s-1, zero beyond).  Shared memory holds "units": unit u is
-// the 16 bytes r_vec[u .. u+7] of one byte plane (bf16).  For an output block n' in
+// the 16 bytes r_vec[u .. u+7] of one byte plane (fp16).  For an output block n' in
 // [c0-NB+1, c0] (column idx = c0 - n') and digits k' in [k0, k0+KS), element (idx, k')
 // is r_vec[P0 + idx + k'] with P0 = s-1-c0, i.e. element t of unit (P0 + k0) + idx +
 // (k' - k0 - t).  A K-major, no-swizzle UMMA descriptor reads row idx's 8-element
@@ -34,7 +34,7 @@
 //
 // Digits of term j are written per 128-gate tile in the A-operand layout:
 // [tile][term j][row r < 2l][stage < s/KS] blocks of 32 KB, each [mg < 16][kb < 16]
-// [m8 < 8][8 bf16] for gate m = 8 mg + m8 and digit index k' = stage*KS + 8 kb + e.
+// [m8 < 8][8 fp16] for gate m = 8 mg + m8 and digit index k' = stage*KS + 8 kb + e.
 // The accumulators live gate-fastest within tiles ([tile][c][word][128 gates]) while the
 // BlindRotate runs, so the read-out warps' read-modify-writes and the digit jobs' loads
 // are whole 128-byte lines; the caller's [G][2][N] layout is written at the end.
@@ -49,7 +49,10 @@
 // barriers.
 #include <algorithm>
 #include <map>
+#include <type_traits>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 
@@ -215,10 +218,9 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, layout SWIZZLE_NONE
 }
 
-// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N.
+// Instruction descriptor, kind::f16: D f32, A and B f16 (format 0), both K-major, M x N.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -302,10 +304,9 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// bf16 bit pattern of a small integer |x| <= 256: its fp32 pattern has at most 8
-// significant bits, so the upper half is the exact bf16 value.
-__device__ __forceinline__ uint32_t bf16_bits(int x) {
-    return __float_as_uint((float)x) >> 16;
+// fp16 bit pattern of a small integer |x| <= 2048 (exact).
+__device__ __forceinline__ uint32_t f16_bits(int x) {
+    return __half_as_ushort(__int2half_rn(x));
 }
 
 // signed byte planes: q = sum_p 2^{8p} q_p (mod 2^32), q_p in [-128, 128)
@@ -322,35 +323,160 @@ __device__ __forceinline__ void byte_planes(uint32_t q, int (&pl)[PLANES]) {
 // Karatsuba term plan
 // ---------------------------------------------------------------------------
 
-constexpr int MAX_TERMS = 9;  // 3^L, L <= 2
+constexpr int MAX_TERMS = 27;  // 3^L, L <= 3
+constexpr int MAX_BLK = 8;     // 2^L blocks of size s per polynomial
 
-// Digit combination of each term (weight of input block b), per level, in build_plan's
-// term order; the host checks its plan against this table.  Compile-time weights let the
-// digit jobs add only the blocks a term uses.
+// Digit combination of each term (weight of input block b) and the sign with which its
+// product enters output block b, per level, in build_plan's term order; the host checks
+// its plan against these tables.  Compile-time weights let the digit jobs add only the
+// blocks a term uses and recombine the term products without a table lookup.
 __host__ __device__ constexpr int in_coef_tab(int L, int j, int b) {
-    constexpr int t0[1][4] = {{1, 0, 0, 0}};
-    constexpr int t1[3][4] = {{1, 0, 0, 0}, {-1, 1, 0, 0}, {1, 1, 0, 0}};
+    constexpr int t0[1][1] = {{1}};
+    constexpr int t1[3][2] = {{1, 0}, {-1, 1}, {1, 1}};
     constexpr int t2[9][4] = {{1, 1, 0, 0},   {0, 1, 0, 0},  {1, 0, 0, 0},
                               {-1, -1, 1, 1}, {0, -1, 0, 1}, {-1, 0, 1, 0},
                               {1, 1, 1, 1},   {0, 1, 0, 1},  {1, 0, 1, 0}};
-    return L == 0 ? t0[j][b] : (L == 1 ? t1[j][b] : t2[j][b]);
+    constexpr int t3[27][8] = {
+        {1, 1, 1, 1, 0, 0, 0, 0},     {0, 1, 0, 1, 0, 0, 0, 0},     {1, 0, 1, 0, 0, 0, 0, 0},
+        {0, 0, 1, 1, 0, 0, 0, 0},     {0, 0, 0, 1, 0, 0, 0, 0},     {0, 0, 1, 0, 0, 0, 0, 0},
+        {1, 1, 0, 0, 0, 0, 0, 0},     {0, 1, 0, 0, 0, 0, 0, 0},     {1, 0, 0, 0, 0, 0, 0, 0},
+        {-1, -1, -1, -1, 1, 1, 1, 1}, {0, -1, 0, -1, 0, 1, 0, 1},   {-1, 0, -1, 0, 1, 0, 1, 0},
+        {0, 0, -1, -1, 0, 0, 1, 1},   {0, 0, 0, -1, 0, 0, 0, 1},    {0, 0, -1, 0, 0, 0, 1, 0},
+        {-1, -1, 0, 0, 1, 1, 0, 0},   {0, -1, 0, 0, 0, 1, 0, 0},    {-1, 0, 0, 0, 1, 0, 0, 0},
+        {1, 1, 1, 1, 1, 1, 1, 1},     {0, 1, 0, 1, 0, 1, 0, 1},     {1, 0, 1, 0, 1, 0, 1, 0},
+        {0, 0, 1, 1, 0, 0, 1, 1},     {0, 0, 0, 1, 0, 0, 0, 1},     {0, 0, 1, 0, 0, 0, 1, 0},
+        {1, 1, 0, 0, 1, 1, 0, 0},     {0, 1, 0, 0, 0, 1, 0, 0},     {1, 0, 0, 0, 1, 0, 0, 0}};
+    return L == 0 ? t0[j][b] : (L == 1 ? t1[j][b] : (L == 2 ? t2[j][b] : t3[j][b]));
+}
+__host__ __device__ constexpr int out_coef_tab(int L, int j, int b) {
+    constexpr int t0[1][1] = {{1}};
+    constexpr int t1[3][2] = {{1, 1}, {0, 1}, {-1, 0}};
+    constexpr int t2[9][4] = {{1, 1, 1, 1},   {1, 0, 1, 0},  {0, 1, 0, 1},
+                              {0, 0, 1, 1},   {0, 0, 1, 0},  {0, 0, 0, 1},
+                              {-1, -1, 0, 0}, {-1, 0, 0, 0}, {0, -1, 0, 0}};
+    constexpr int t3[27][8] = {
+        {1, 1, 1, 1, 1, 1, 1, 1},     {1, 0, 1, 0, 1, 0, 1, 0},     {0, 1, 0, 1, 0, 1, 0, 1},
+        {1, 1, 0, 0, 1, 1, 0, 0},     {1, 0, 0, 0, 1, 0, 0, 0},     {0, 1, 0, 0, 0, 1, 0, 0},
+        {0, 0, 1, 1, 0, 0, 1, 1},     {0, 0, 1, 0, 0, 0, 1, 0},     {0, 0, 0, 1, 0, 0, 0, 1},
+        {0, 0, 0, 0, 1, 1, 1, 1},     {0, 0, 0, 0, 1, 0, 1, 0},     {0, 0, 0, 0, 0, 1, 0, 1},
+        {0, 0, 0, 0, 1, 1, 0, 0},     {0, 0, 0, 0, 1, 0, 0, 0},     {0, 0, 0, 0, 0, 1, 0, 0},
+        {0, 0, 0, 0, 0, 0, 1, 1},     {0, 0, 0, 0, 0, 0, 1, 0},     {0, 0, 0, 0, 0, 0, 0, 1},
+        {-1, -1, -1, -1, 0, 0, 0, 0}, {-1, 0, -1, 0, 0, 0, 0, 0},   {0, -1, 0, -1, 0, 0, 0, 0},
+        {-1, -1, 0, 0, 0, 0, 0, 0},   {-1, 0, 0, 0, 0, 0, 0, 0},    {0, -1, 0, 0, 0, 0, 0, 0},
+        {0, 0, -1, -1, 0, 0, 0, 0},   {0, 0, -1, 0, 0, 0, 0, 0},    {0, 0, 0, -1, 0, 0, 0, 0}};
+    return L == 0 ? t0[j][b] : (L == 1 ? t1[j][b] : (L == 2 ? t2[j][b] : t3[j][b]));
 }
 
-// Two small integers (|x| < 2^22) as packed bf16: x + 1.5 * 2^23 is exact in fp32, so its
-// bit pattern is 0x4B400000 + x and subtracting 1.5 * 2^23 back gives float(x); the high
-// halves of the two floats are the bf16 values (exact for |x| <= 256).
-__device__ __forceinline__ uint32_t pack_bf16x2(int x0, int x1) {
-    const float f0 = __int_as_float(0x4B400000 + x0) - 12582912.0f;
-    const float f1 = __int_as_float(0x4B400000 + x1) - 12582912.0f;
-    return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+// Two small integers (|x| < 512) as packed fp16: the 16-bit field x + 0x6600 is the fp16
+// pattern of 1536 + x (exponent 10: unit spacing on [1024, 2048)), and both fields stay in
+// [0, 2^16), so one integer sum builds the pair and one packed subtraction of 1536
+// leaves x0 and x1 exactly.
+__device__ __forceinline__ uint32_t pack_f16x2(int x0, int x1) {
+    const uint32_t v = (uint32_t)x0 + ((uint32_t)x1 << 16) + 0x66006600u;
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0x66006600u));
+    return r;
 }
+
+// The 3^L Karatsuba digit combinations of a set of E positions, v[b][e] the digit of
+// position e in size-s block b of the polynomial, built as the plan's tree (negacyclic
+// split: x0, x1 - x0, x0 + x1; then per Toeplitz split: x0 + x1, x1, x0) instead of one
+// dense sum per term: 23 additions per position at L = 3 instead of 80.  emit(j, x)
+// receives term j (a std::integral_constant, build_plan's order) and its E values.
+__host__ __device__ constexpr int pow3(int k) { return k == 0 ? 1 : 3 * pow3(k - 1); }
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+template <int M, int J0, int E, typename F>
+__device__ __forceinline__ void kara_split(const int (&v)[M][E], F &emit) {
+    if constexpr (M == 1) {
+        emit(std::integral_constant<int, J0>(), v[0]);
+    } else {
+        constexpr int H = M / 2, SUB = pow3(ilog2c(H));
+        int sa[H][E], s1[H][E], s0[H][E];
+#pragma unroll
+        for (int h = 0; h < H; h++)
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                sa[h][e] = v[h][e] + v[H + h][e];
+                s1[h][e] = v[H + h][e];
+                s0[h][e] = v[h][e];
+            }
+        kara_split<H, J0, E>(sa, emit);
+        kara_split<H, J0 + SUB, E>(s1, emit);
+        kara_split<H, J0 + 2 * SUB, E>(s0, emit);
+    }
+}
+
+template <int M, int E, typename F>
+__device__ __forceinline__ void kara_terms(const int (&v)[M][E], F &emit) {
+    if constexpr (M == 1) {
+        emit(std::integral_constant<int, 0>(), v[0]);
+    } else {
+        constexpr int H = M / 2, SUB = pow3(ilog2c(H));
+        int p1[H][E], p2[H][E], p3[H][E];
+#pragma unroll
+        for (int h = 0; h < H; h++)
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                p1[h][e] = v[h][e];
+                p2[h][e] = v[H + h][e] - v[h][e];
+                p3[h][e] = v[h][e] + v[H + h][e];
+            }
+        kara_split<H, 0, E>(p1, emit);
+        kara_split<H, SUB, E>(p2, emit);
+        kara_split<H, 2 * SUB, E>(p3, emit);
+    }
+}
+
+// Stores term j's E digit combinations of one thread as packed fp16 into the A-operand
+// layout: unit u = base + j * term_stride (16 bytes, 8 positions; E = 4 fills half eh).
+template <int E>
+struct DigitStore {
+    uint4 *digits;
+    size_t base, term_stride;
+    int eh;
+    template <int j>
+    __device__ __forceinline__ void operator()(std::integral_constant<int, j>, const int (&x)[E]) const {
+        uint32_t wv[E / 2];
+#pragma unroll
+        for (int e = 0; e < E; e += 2) wv[e / 2] = pack_f16x2(x[e], x[e + 1]);
+        const size_t u = base + (size_t)j * term_stride;
+        if constexpr (E == 8)
+            digits[u] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        else
+            reinterpret_cast<uint2 *>(digits)[2 * u + eh] = make_uint2(wv[0], wv[1]);
+    }
+};
+
+// The same tree as coefficients (weight of input block b in term j), checked against
+// in_coef_tab at compile time.
+__host__ __device__ constexpr int tree_split_coef(int M, int j, int b) {
+    if (M == 1) return b == 0 ? 1 : 0;
+    const int H = M / 2, SUB = pow3(ilog2c(H));
+    const int child = j / SUB, c = tree_split_coef(H, j % SUB, b % H), hi = b / H;
+    return child == 0 ? c : (child == 1 ? (hi ? c : 0) : (hi ? 0 : c));
+}
+__host__ __device__ constexpr int tree_coef(int L, int j, int b) {
+    if (L == 0) return b == 0 ? 1 : 0;
+    const int M = 1 << L, H = M / 2, SUB = pow3(L - 1);
+    const int child = j / SUB, c = tree_split_coef(H, j % SUB, b % H), hi = b / H;
+    return child == 0 ? (hi ? 0 : c) : (child == 1 ? (hi ? c : -c) : c);
+}
+__host__ __device__ constexpr bool tree_matches_tables() {
+    for (int L = 0; L <= 3; L++)
+        for (int j = 0; j < pow3(L); j++)
+            for (int b = 0; b < (1 << L); b++)
+                if (tree_coef(L, j, b) != in_coef_tab(L, j, b)) return false;
+    return true;
+}
+static_assert(tree_matches_tables(), "Karatsuba tree and term table disagree");
 
 struct KTerm {
-    int n_in, in_blk[4], in_sgn[4];      // digit combination: sum sgn * block (size s)
-    int n_out, out_blk[4], out_sgn[4];   // output blocks (size s) receiving sgn * P
-    int n_key, key_off[4], key_coef[4];  // generator t_j[d] = sum coef * t[d + off]
-    int phase;                           // terms of one phase write disjoint blocks
-    int in_coef[4];                      // the digit combination as dense block weights
+    int n_in, in_blk[MAX_BLK], in_sgn[MAX_BLK];      // digit combination: sum sgn * block (size s)
+    int n_out, out_blk[MAX_BLK], out_sgn[MAX_BLK];   // output blocks (size s) receiving sgn * P
+    int n_key, key_off[MAX_BLK], key_coef[MAX_BLK];  // generator t_j[d] = sum coef * t[d + off]
+    int in_coef[MAX_BLK];                            // the digit combination as block weights
+    int out_coef[MAX_BLK];                           // the output signs as block weights
 };
 
 // Negacyclic generator of the key polynomial q: t[e] = q[e] (e >= 0), -q[e+N] (e < 0).
@@ -387,7 +513,7 @@ __global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, int s, i
             byte_planes(val[0], pl0);
             byte_planes(val[1], pl1);
 #pragma unroll
-            for (int p = 0; p < PLANES; p++) w[p][e / 2] = bf16_bits(pl0[p]) | (bf16_bits(pl1[p]) << 16);
+            for (int p = 0; p < PLANES; p++) w[p][e / 2] = f16_bits(pl0[p]) | (f16_bits(pl1[p]) << 16);
         }
 #pragma unroll
         for (int p = 0; p < PLANES; p++)
@@ -443,27 +569,27 @@ __global__ void k_tc_untile_acc(int N, int G, const uint32_t *__restrict__ acc_t
 // Persistent BlindRotate: all n steps in one launch, one block per SM.
 //
 // Jobs: D(i, gt, part) writes the digits (all terms) of gates 8*part .. 8*part+7 of gate
-// tile gt for step i (16 parts per tile); E(i, gt, j, c, b) is the tensor-core product of
-// term j for column block b of output polynomial c, added (with signs) into ACC.
-// Two job streams, each taken in order from its own global counter: digit jobs (step,
-// tile, part) by the digit warps of any block, product jobs (step, then a per-step table:
-// each tile's phases in order, later phases of a tile staggered about one wave of SMs
-// behind its earlier ones) by the loaders.  With D(i) < E(i) < D(i+1) a job
-// only waits for jobs earlier in that order, each stream is handed out in order, and no
-// role holds anything a later job needs, so the schedule cannot deadlock:
-//   stages of E(i, gt, ...) wait for done_D[gt] >= 16 (i+1);
-//   the accumulator update of a phase-p product waits for the products of gt in earlier
-//   phases (done_E[gt] >= E_per_tile * i + dep);
-//   D(i, gt, .) waits for done_E[gt] >= E_per_tile * i.
+// tile gt for step i (16 parts per tile) from ACC(i), the accumulator before step i;
+// E(i, gt, j, c, b) is the tensor-core product P_j of term j for column block b of output
+// polynomial c, added with its signs into every output block of ACC that it enters (the
+// Karatsuba recombination) by reductions at L2, so the products of one tile and step run
+// in any order (integer addition mod 2^32 commutes).  Two job streams, each taken in
+// order from its own global counter: digit jobs (step, tile, part) by the digit warps of
+// any block, product jobs (step, tile, term, polynomial, block) by the loaders.  With
+// D(i) < E(i) < D(i+1) a job only waits for jobs earlier in that order, each stream is
+// handed out in order, and no role holds anything a later job needs, so the schedule
+// cannot deadlock:
+//   stages of E(i, gt, ...), and its additions into ACC, wait for done_D[gt] >= 16 (i+1)
+//   (every digit job of the step has read ACC(i));
+//   D(i, gt, .) waits for done_E[gt] >= E_per_tile * i (ACC(i) is complete).
 // Every wait is bounded.
 //
 // Warp roles (448 threads): warps 0-7 read TMEM out (warp w owns lanes 32(w%4)..+31 and
 // columns 64(w/4)..+63 of the block), warp 8 owns TMEM and one lane issues the MMAs,
 // warp 12 fetches jobs and streams stages with cp.async.bulk, warps 9-11 and 13 compute
-// digits.  The four planes of TMEM are handed
-// back one by one after each K-half's read-out, so the next half's MMAs on plane p start
-// as soon as plane p has been read; both halves of a job accumulate in registers and the
-// accumulator rows are updated once per job.
+// digits.  The four planes of TMEM are handed back one by one after each K-pass's
+// read-out, so the next pass's MMAs on plane p start as soon as plane p has been read;
+// the passes of a job accumulate in registers and the product is added once.
 // ---------------------------------------------------------------------------
 constexpr int P_THREADS = 448;
 constexpr int EPI_WARPS = 8;                 // read-out warps: 2 per TMEM lane quarter
@@ -481,29 +607,29 @@ constexpr float RO_MAGIC = 12582912.0f;
 constexpr uint32_t RO_MAGIC_BITS = 0x4B400000u;
 constexpr float RO_FAST_LIMIT = 4194304.0f;  // 2^22
 constexpr int RO_COLS = 32;                   // columns per TMEM load slice
-constexpr int RMW_BATCH = 32;                 // accumulator loads in flight per thread
 // bit-pattern offset that one K-pass adds over the four planes (mod 2^32)
 constexpr uint32_t RO_MAGIC_PER_PASS =
     RO_MAGIC_BITS + (RO_MAGIC_BITS << 8) + (RO_MAGIC_BITS << 16) + (RO_MAGIC_BITS << 24);
 // A product job accumulates its whole K (2l rows of s digits) in one TMEM pass when every
 // gate g of the tile has sum_k |x_gk| <= 2^17 for the job's term: each partial sum is then
 // at most 128 * 2^17 = 2^24 in magnitude (|key byte| <= 128), so fp32 stays exact.  The
-// digit jobs check this; a (tile, step) that fails it is marked and its products take
-// two passes of l rows each, for which the worst case l * s * (32 * 2^L) * 128 <= 2^24.
+// digit jobs check a bound of it (the sum over the term's input blocks of sum |digit|);
+// a (tile, step) where the bound fails is marked and its products take two passes of l
+// rows each, for which the worst case l * s * (32 * 2^L) * 128 <= 2^24.
 constexpr int ONE_PASS_LIMIT = 1 << 17;  // default and largest allowed limit
 constexpr int JQ = 8;       // job ring depth
 constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
 
 enum { JOB_STOP = 0, JOB_D = 1, JOB_E = 2, JOB_NOP = 3 };
 
-// packed job-table entry: kind (2 bits) | gt (12) | term (4) | c (1) | sub (5) | dep (8)
-__host__ __device__ constexpr uint32_t pack_job(int kind, int gt, int j, int c, int sub, int dep) {
-    return (uint32_t)kind | ((uint32_t)gt << 2) | ((uint32_t)j << 14) | ((uint32_t)c << 18) |
-           ((uint32_t)sub << 19) | ((uint32_t)dep << 24);
+// packed job-table entry: kind (2 bits) | gt (12) | term (5) | c (1) | sub (4)
+__host__ __device__ constexpr uint32_t pack_job(int kind, int gt, int j, int c, int sub) {
+    return (uint32_t)kind | ((uint32_t)gt << 2) | ((uint32_t)j << 14) | ((uint32_t)c << 19) |
+           ((uint32_t)sub << 20);
 }
 
 struct Job {
-    int kind, i, gt, j, c, sub, dep;
+    int kind, i, gt, j, c, sub;
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
@@ -515,6 +641,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 // gpu-scope release increment of a progress counter (pairs with ld_acquire)
 __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// relaxed reduction at L2: the read-out adds term products into the accumulators
+__device__ __forceinline__ void red_add_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ bool wait_count(const uint32_t *p, uint32_t target, volatile int *abort,
@@ -554,16 +685,15 @@ struct BrArgs {
 };
 
 __device__ __forceinline__ Job decode_e(const BrArgs &a, int job) {
-    Job J{JOB_STOP, 0, 0, 0, 0, 0, 0};
+    Job J{JOB_STOP, 0, 0, 0, 0, 0};
     if (job < 0) return J;
     const uint32_t e = __ldg(a.table + job % a.step_len);
     J.kind = JOB_E;
     J.i = job / a.step_len;
     J.gt = (int)((e >> 2) & 0xFFF);
-    J.j = (int)((e >> 14) & 0xF);
-    J.c = (int)((e >> 18) & 1);
-    J.sub = (int)((e >> 19) & 0x1F);
-    J.dep = (int)(e >> 24);
+    J.j = (int)((e >> 14) & 0x1F);
+    J.c = (int)((e >> 19) & 1);
+    J.sub = (int)((e >> 20) & 0xF);
     return J;
 }
 
@@ -587,7 +717,7 @@ __device__ __forceinline__ int passes_for(const BrArgs &a, const Job &J, const u
 template <int L, bool PAIR>
 __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     constexpr int NBLK = 1 << L;                      // size-s blocks per polynomial
-    constexpr int NT = L == 0 ? 1 : (L == 1 ? 3 : 9);  // terms
+    constexpr int NT = L == 0 ? 1 : (L == 1 ? 3 : (L == 2 ? 9 : 27));  // terms
     constexpr int BPL = b_plane_bytes(PAIR), BST = b_stage_bytes(PAIR);
     extern __shared__ __align__(128) uint8_t smem[];  // no swizzle: 16-byte alignment suffices
     uint8_t *a_st = smem;
@@ -600,8 +730,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     __shared__ int job_passes[JQ];  // set by the loader before the job's first stage is full
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ KTerm terms[NT];
-    if (threadIdx.x < NT) terms[threadIdx.x] = a.terms[threadIdx.x];
+    __shared__ int8_t out_tab[NT][NBLK];  // out_coef_tab of this level
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // pair form: CTA 0 of the cluster fetches the product jobs and issues the MMAs
@@ -634,6 +763,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             mbar_init(&job_empty[q], PAIR ? 5 : 2);
         }
         abort_flag = 0;
+#pragma unroll
+        for (int j = 0; j < NT; j++)
+#pragma unroll
+            for (int b = 0; b < NBLK; b++) out_tab[j][b] = (int8_t)out_coef_tab(L, j, b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -906,33 +1039,30 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 }
             }
             if (!ok) break;
-            // accumulator update: column idx of the term output is word n' = c0 - idx of
-            // each of the term's output blocks.  The leader's acquires order these accesses
-            // after the digit job of this step and after this tile's earlier phases.
-            if (tid == 0 && gt < a.tiles) {
+            // accumulator update: column idx of the block is word n' = c0 - idx of P_j,
+            // added with sign out_tab[j][b] into output block b.  The leader's acquire
+            // orders these additions after this step's digit jobs of the tile (the
+            // readers of ACC(i)).
+            if (tid == 0 && gt < a.tiles)
                 wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
-                if (J.dep) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * J.i + J.dep), abort, err);
-            }
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             if (*abort) break;
-            const KTerm &T = terms[J.j];
-            const int g = gt * TILE_M + gl;
-            if (g < a.G) {
+            if (gt * TILE_M + gl < a.G) {
                 // this warp's columns idx = 64 colh + e map to words c0 - idx, i.e. the
                 // 64 words starting at bcol*NB + 64 (1 - colh), in reverse order; in the
                 // tiled accumulator each word of the warp's 32 gates is one 128-byte line
                 const int w0 = bcol * NB + EPI_COLS * (1 - colh);
-                for (int o = 0; o < T.n_out; o++) {
-                    const uint32_t sg = (uint32_t)T.out_sgn[o];
-                    uint32_t *col = a.acc + ((size_t)(gt * 2 + J.c) * N + (size_t)T.out_blk[o] * s + w0) * TILE_M + gl;
+#pragma unroll 1
+                for (int b = 0; b < NBLK; b++) {
+                    const int sg = out_tab[J.j][b];
+                    if (!sg) continue;
+                    uint32_t *col = a.acc + ((size_t)(gt * 2 + J.c) * N + (size_t)b * s + w0) * TILE_M + gl;
+                    if (sg > 0) {
 #pragma unroll
-                    for (int j0 = 0; j0 < EPI_COLS; j0 += RMW_BATCH) {
-                        uint32_t v[RMW_BATCH];
+                        for (int q = 0; q < EPI_COLS; q++) red_add_u32(col + (size_t)q * TILE_M, sum[EPI_COLS - 1 - q]);
+                    } else {
 #pragma unroll
-                        for (int k = 0; k < RMW_BATCH; k++) v[k] = __ldcg(col + (size_t)(j0 + k) * TILE_M);
-#pragma unroll
-                        for (int k = 0; k < RMW_BATCH; k++)
-                            __stcg(col + (size_t)(j0 + k) * TILE_M, v[k] + sg * sum[EPI_COLS - 1 - (j0 + k)]);
+                        for (int q = 0; q < EPI_COLS; q++) red_add_u32(col + (size_t)q * TILE_M, 0u - sum[EPI_COLS - 1 - q]);
                     }
                 }
             }
@@ -942,11 +1072,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             if (tid == 0 && gt < a.tiles) red_release_add(&done_E[gt], 1u);
         }
     } else {
-        // ---- warps 10-13: digit jobs ----
+        // ---- warps 9-11 and 13: digit jobs ----
         const int tid = digit_warp_index(warp) * 32 + lane;
         const uint32_t off = gadget_offset(l, a.Bgbit);
+        // One-pass check (see ONE_PASS_LIMIT): sum |x| over a term's K is bounded by the
+        // sum, over the term's input blocks, of sum |digit| per block (triangle
+        // inequality), so the digit jobs keep one counter per block.  Level 3 digitises 4
+        // positions per pass (registers), the others 8.
+        constexpr int E = L == 3 ? 4 : 8;
         __shared__ int d_job;
-        __shared__ int d_abs[8 * NT];  // sum of |x| per (gate of the part, term)
+        __shared__ int d_abs[8 * NBLK];  // per gate of the part and input block
         for (;;) {
             if (tid == 0) {
                 const unsigned jn = atomicAdd(d_counter, 1u);
@@ -973,10 +1108,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (*abort) break;
             // One accumulator polynomial of the part's 8 gates at a time: the rows are copied
-            // into shared memory (16-byte asynchronous copies), then thread (m8 = tid & 7,
-            // kb = tid >> 3) digitises positions kp = kc*KS + 8 kb .. + 7 of every size-s block
-            // of gate m8, so 8 consecutive threads write 128 contiguous bytes of the A-operand
-            // layout (stage kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
+            // into shared memory, then thread (m8 = tid & 7, kb = tid >> 3) digitises
+            // positions kp = kc*KS + 8 kb .. + 7 of every size-s block of gate m8, so 8
+            // consecutive threads write 128 contiguous bytes of the A-operand layout (stage
+            // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
             const int pitch = N + 4;
             int rot8[8];
 #pragma unroll
@@ -985,10 +1120,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 rot8[m8] = g < a.G ? (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
             }
             const int m8 = tid & 7, kb = tid >> 3;
-            for (int v = tid; v < 8 * NT; v += 128) d_abs[v] = 0;
-            int asum[NT];
+            for (int v = tid; v < 8 * NBLK; v += 128) d_abs[v] = 0;
+            int asum[NBLK];
 #pragma unroll
-            for (int j = 0; j < NT; j++) asum[j] = 0;
+            for (int b = 0; b < NBLK; b++) asum[b] = 0;
             const int rot = rot8[m8];
             const int rk = rot >= N ? rot - N : rot;      // X^rot = (-1)^{rot >= N} X^rk
             const uint32_t rneg = rot >= N ? 0xFFFFFFFFu : 0u;
@@ -996,93 +1131,89 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             for (int c = 0; c < 2; c++) {
                 asm volatile("bar.sync 2, 128;" ::: "memory");  // previous polynomial consumed
                 {
-                    // word k of the part's 8 gates: 32 contiguous bytes of the tiled
-                    // accumulator; thread tid takes words tid, tid + 128, ... (two per batch)
-                    const uint4 *src = (const uint4 *)(a.acc + (size_t)(gt * 2 + c) * N * TILE_M) + mg * 2;
-                    for (int k0 = tid; k0 < N; k0 += 256) {
-                        uint4 v[4];
-#pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            v[2 * h] = __ldcg(src + (size_t)(k0 + 128 * h) * (TILE_M / 4));
-                            v[2 * h + 1] = __ldcg(src + (size_t)(k0 + 128 * h) * (TILE_M / 4) + 1);
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            const int k = k0 + 128 * h;
-                            d_rows[0 * pitch + k] = v[2 * h].x;
-                            d_rows[1 * pitch + k] = v[2 * h].y;
-                            d_rows[2 * pitch + k] = v[2 * h].z;
-                            d_rows[3 * pitch + k] = v[2 * h].w;
-                            d_rows[4 * pitch + k] = v[2 * h + 1].x;
-                            d_rows[5 * pitch + k] = v[2 * h + 1].y;
-                            d_rows[6 * pitch + k] = v[2 * h + 1].z;
-                            d_rows[7 * pitch + k] = v[2 * h + 1].w;
-                        }
+                    // item (k, h): word k for gates 4h .. 4h+3 of the part, 16 bytes of the
+                    // tiled accumulator; the rows of two gate halves land on disjoint banks
+                    const uint32_t *accp = a.acc + (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
+#pragma unroll 4
+                    for (int it = tid; it < 2 * N; it += 128) {
+                        const int k = it >> 1, h = it & 1;
+                        const uint4 o = __ldcg((const uint4 *)(accp + (size_t)k * TILE_M) + h);
+                        uint32_t *rr = d_rows + 4 * h * pitch + k;
+                        rr[0] = o.x;
+                        rr[pitch] = o.y;
+                        rr[2 * pitch] = o.z;
+                        rr[3 * pitch] = o.w;
                     }
                 }
                 asm volatile("bar.sync 2, 128;" ::: "memory");
                 for (int kc = 0; kc < kstages; kc++) {
-                    const int kp = kc * KS + kb * 8;
-                    uint32_t xv[NBLK][8];
 #pragma unroll
-                    for (int b = 0; b < NBLK; b++) {
-                        const int k0 = b * s + kp;
-                        const uint4 o0 = *(const uint4 *)(row + k0);
-                        const uint4 o1 = *(const uint4 *)(row + k0 + 4);
-                        const uint32_t own[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                    for (int eh = 0; eh < 8 / E; eh++) {
+                        const int kp = kc * KS + kb * 8 + eh * E;
+                        uint32_t xv[NBLK][E];
 #pragma unroll
-                        for (int e = 0; e < 8; e++) {
-                            const int k = k0 + e;
-                            const int src = k - rk;
-                            uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
-                            v = (v ^ rneg) - rneg;  // negate when rot >= N
-                            xv[b][e] = v - own[e];
-                        }
-                    }
-                    for (int jd = 0; jd < l; jd++) {
-                        int dg[NBLK][8];
+                        for (int b = 0; b < NBLK; b++) {
+                            const int k0 = b * s + kp;
+                            uint32_t own[E];
 #pragma unroll
-                        for (int b = 0; b < NBLK; b++)
-#pragma unroll
-                            for (int e = 0; e < 8; e++) dg[b][e] = gadget_digit(xv[b][e] + off, jd + 1, a.Bgbit);
-                        const int r = c * l + jd;
-#pragma unroll
-                        for (int j = 0; j < NT; j++) {
-                            int x[8];
-#pragma unroll
-                            for (int e = 0; e < 8; e++) x[e] = 0;
-#pragma unroll
-                            for (int b = 0; b < NBLK; b++) {
-                                const int cf = in_coef_tab(L, j, b);
-#pragma unroll
-                                for (int e = 0; e < 8; e++) {
-                                    if (cf == 1) x[e] += dg[b][e];
-                                    else if (cf == -1) x[e] -= dg[b][e];
-                                }
+                            for (int q = 0; q < E; q += 4) {
+                                const uint4 o4 = *(const uint4 *)(row + k0 + q);
+                                own[q] = o4.x;
+                                own[q + 1] = o4.y;
+                                own[q + 2] = o4.z;
+                                own[q + 3] = o4.w;
                             }
 #pragma unroll
-                            for (int e = 0; e < 8; e++) asum[j] += abs(x[e]);
-                            uint32_t w[4];
+                            for (int e = 0; e < E; e++) {
+                                const int k = k0 + e;
+                                const int src = k - rk;
+                                uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
+                                v = (v ^ rneg) - rneg;  // negate when rot >= N
+                                xv[b][e] = v - own[e];
+                            }
+                        }
+                        for (int jd = 0; jd < l; jd++) {
+                            int dg[NBLK][E];
 #pragma unroll
-                            for (int e = 0; e < 8; e += 2) w[e / 2] = pack_bf16x2(x[e], x[e + 1]);
-                            const size_t blk = (((size_t)gt * NT + j) * 2 * l + r) * kstages + kc;
-                            a.digits[blk * (A_STAGE_BYTES / 16) + ((size_t)mg * 16 + kb) * 8 + m8] =
-                                make_uint4(w[0], w[1], w[2], w[3]);
+                            for (int b = 0; b < NBLK; b++)
+#pragma unroll
+                                for (int e = 0; e < E; e++) {
+                                    dg[b][e] = gadget_digit(xv[b][e] + off, jd + 1, a.Bgbit);
+                                    asum[b] += abs(dg[b][e]);
+                                }
+                            const int r = c * l + jd;
+                            const size_t u0 = ((size_t)mg * 16 + kb) * 8 + m8;
+                            const size_t blk0 = ((size_t)gt * NT * 2 * l + r) * kstages + kc;
+                            DigitStore<E> emit{a.digits, blk0 * (A_STAGE_BYTES / 16) + u0,
+                                               (size_t)2 * l * kstages * (A_STAGE_BYTES / 16), eh};
+                            kara_terms<NBLK, E>(dg, emit);
                         }
                     }
                 }
             }
-            // one-pass check: sum |x| over the 16 threads of each gate, mark the step if
-            // some gate exceeds the bound for some term (read by the product jobs)
+            // one-pass check: reduce the block sums over the 16 threads of each gate, then
+            // mark the step if some gate exceeds the bound for some term (read by the
+            // product jobs)
 #pragma unroll
-            for (int j = 0; j < NT; j++) {
-                int v = asum[j];
+            for (int b = 0; b < NBLK; b++) {
+                int v = asum[b];
                 v += __shfl_xor_sync(0xffffffffu, v, 8);
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (lane < 8) atomicAdd(&d_abs[lane * NT + j], v);
+                if (lane < 8) atomicAdd(&d_abs[lane * NBLK + b], v);
             }
             asm volatile("bar.sync 2, 128;" ::: "memory");
-            if (tid < 8 * NT && d_abs[tid] > a.one_pass_limit) atomicMax(&two_pass[gt], (uint32_t)(i + 1));
+            if (tid < 8 * NT) {
+                const int gq = tid / NT, jt = tid % NT;
+                int v = 0;
+#pragma unroll
+                for (int j = 0; j < NT; j++) {  // compile-time coefficients, selected by jt
+                    if (j != jt) continue;
+#pragma unroll
+                    for (int b = 0; b < NBLK; b++)
+                        if (in_coef_tab(L, j, b) != 0) v += d_abs[gq * NBLK + b];
+                }
+                if (v > a.one_pass_limit) atomicMax(&two_pass[gt], (uint32_t)(i + 1));
+            }
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (tid == 0) red_release_add(&done_D[gt], 1u);
         }
@@ -1177,26 +1308,20 @@ static void build_plan(int N, int L, std::vector<KTerm> &terms) {
         terms.swap(next);
     }
     for (KTerm &t : terms) {
-        for (int b = 0; b < 4; b++) t.in_coef[b] = 0;
+        for (int b = 0; b < MAX_BLK; b++) t.in_coef[b] = t.out_coef[b] = 0;
         for (int m = 0; m < t.n_in; m++) t.in_coef[t.in_blk[m]] += t.in_sgn[m];
+        for (int m = 0; m < t.n_out; m++) t.out_coef[t.out_blk[m]] += t.out_sgn[m];
     }
-    for (size_t j = 0; j < terms.size(); j++)  // the kernels' compile-time table must agree
-        for (int b = 0; b < 4; b++)
-            if (terms[j].in_coef[b] != (b < (1 << L) ? in_coef_tab(L, (int)j, b) : 0)) terms.clear();
-    // phases: greedy, terms of one phase write disjoint output blocks
-    std::vector<std::vector<int>> used;  // per phase, blocks written
-    for (KTerm &t : terms) {
-        int ph = 0;
-        for (;; ph++) {
-            if (ph == (int)used.size()) used.emplace_back();
-            bool clash = false;
-            for (int m = 0; m < t.n_out && !clash; m++)
-                for (int b : used[ph]) if (b == t.out_blk[m]) clash = true;
-            if (!clash) break;
+    // the kernels' compile-time tables must agree (a term enters each output block once)
+    for (size_t j = 0; j < terms.size(); j++)
+        for (int b = 0; b < MAX_BLK; b++) {
+            const bool in_range = b < (1 << L);
+            if (terms[j].in_coef[b] != (in_range ? in_coef_tab(L, (int)j, b) : 0) ||
+                terms[j].out_coef[b] != (in_range ? out_coef_tab(L, (int)j, b) : 0)) {
+                terms.clear();
+                return;
+            }
         }
-        t.phase = ph;
-        for (int m = 0; m < t.n_out; m++) used[ph].push_back(t.out_blk[m]);
-    }
 }
 
 struct TcWorkspace {
@@ -1209,7 +1334,7 @@ struct TcWorkspace {
         size_t win_cap = 0;        // bytes
         bool ready = false;        // windows expanded for the current keys
     };
-    Level lv[3];
+    Level lv[4];
     uint4 *digits = nullptr;
     size_t digits_cap = 0;     // bytes
     uint32_t *sync = nullptr;  // job counter and per-tile progress counters
@@ -1223,7 +1348,7 @@ struct TcWorkspace {
     std::map<int, JobTable> tables;  // by (level, pair form, gate tiles); kept: captured
                                      // graphs use them
     int sms = 0;
-    int max_pairs[3] = {-1, -1, -1};  // co-resident SM pairs of the pair kernel, per level
+    int max_pairs[4] = {-1, -1, -1, -1};  // co-resident SM pairs of the pair kernel, per level
     int want_level = -1;       // requested Karatsuba levels (-1: default)
     int want_variant = -1;     // TFHE_TC_SINGLE_SM, TFHE_TC_SM_PAIR, -1: default
     int one_pass_limit = ONE_PASS_LIMIT;
@@ -1246,7 +1371,7 @@ static bool use_pair(tfhe_ctx *ctx) {
 }
 
 static bool level_ok(const tfhe_params &p, int L) {
-    if (L < 0 || L > 2) return false;
+    if (L < 0 || L > 3) return false;
     const int s = p.N >> L;
     return s >= NB && s % NB == 0 && s % KS == 0;
 }
@@ -1318,7 +1443,7 @@ int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *, cudaStream_t st) {
     if (!tfhe_tc_supported(ctx)) return TFHE_OK;
     if (!ctx->tc) ctx->tc = new TcWorkspace();
     const int L0 = resolve_level(ctx, -1);
-    for (int L = 0; L < 3; L++) {
+    for (int L = 0; L < 4; L++) {
         TcWorkspace::Level &V = ctx->tc->lv[L];
         if (V.ready || L == L0) {
             V.ready = false;
@@ -1334,7 +1459,7 @@ int tfhe_tc_prepare_keys(tfhe_ctx *ctx, const uint32_t *, cudaStream_t st) {
 void tfhe_tc_keep_levels(tfhe_ctx *ctx, unsigned mask) {
     if (!ctx->tc) return;
     const int L0 = resolve_level(ctx, -1);
-    for (int L = 0; L < 3; L++) {
+    for (int L = 0; L < 4; L++) {
         TcWorkspace::Level &V = ctx->tc->lv[L];
         if (L == L0 || (mask >> L) & 1 || !V.win) continue;
         cudaFree(V.win);
@@ -1375,35 +1500,14 @@ static int prepare_table(tfhe_ctx *ctx, int level, int tiles, bool pair,
         return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core job table missing while recording a graph");
     const int s = ctx->p.N >> level;
     const int bpp = s / NB;
-    int nphase = 0;
-    for (const KTerm &t : terms) nphase = t.phase + 1 > nphase ? t.phase + 1 : nphase;
-    // entries name the gate tile, or in the pair form the tile pair (tiles 2u, 2u+1)
+    // entries name the gate tile, or in the pair form the tile pair (tiles 2u, 2u+1); the
+    // terms write disjoint buffers, so a tile's products of one step are independent
     const int units = pair ? (tiles + 1) / 2 : tiles;
-    // Phase ph of unit u is emitted at slot u + ph * lag: a unit's later phases come about
-    // one wave of the SMs (or pairs) after its earlier ones, so the read-modify-writes they
-    // wait for are done, and the unit's last product of a step sits well before its first
-    // product of the next step, leaving time for that step's digit jobs.  Every job still
-    // follows all jobs it waits for.
-    const int per_unit = (int)terms.size() * 2 * bpp;
-    int sms = w->sms;
-    if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    const int lanes = pair ? sms / 2 : sms;  // product jobs running at once
-    const int lag = nphase > 1 ? std::max(1, std::min(units, (6 * lanes / 5 + per_unit - 1) / per_unit)) : 0;
     std::vector<uint32_t> tab;
-    for (int slot = 0; slot < units + (nphase - 1) * lag; slot++) {
-        for (int ph = 0; ph < nphase; ph++) {
-            const int gt = slot - ph * lag;
-            if (gt < 0 || gt >= units) continue;
-            int dep = 0;  // product jobs of this tile in earlier phases
-            for (const KTerm &t : terms)
-                if (t.phase < ph) dep += 2 * bpp;
-            for (int j = 0; j < (int)terms.size(); j++) {
-                if (terms[j].phase != ph) continue;
-                for (int c = 0; c < 2; c++)
-                    for (int b = 0; b < bpp; b++) tab.push_back(pack_job(JOB_E, gt, j, c, b, dep));
-            }
-        }
-    }
+    for (int gt = 0; gt < units; gt++)
+        for (int j = 0; j < (int)terms.size(); j++)
+            for (int c = 0; c < 2; c++)
+                for (int b = 0; b < bpp; b++) tab.push_back(pack_job(JOB_E, gt, j, c, b));
     TcWorkspace::JobTable t;
     if (cudaMalloc(&t.d, tab.size() * 4) != cudaSuccess)
         return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core job table");
@@ -1480,10 +1584,12 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     void (*kern)(BrArgs);
     if (pair)
         kern = level == 0 ? k_tc_blind_rotate<0, true>
-             : (level == 1 ? k_tc_blind_rotate<1, true> : k_tc_blind_rotate<2, true>);
+             : (level == 1 ? k_tc_blind_rotate<1, true>
+                           : (level == 2 ? k_tc_blind_rotate<2, true> : k_tc_blind_rotate<3, true>));
     else
         kern = level == 0 ? k_tc_blind_rotate<0, false>
-             : (level == 1 ? k_tc_blind_rotate<1, false> : k_tc_blind_rotate<2, false>);
+             : (level == 1 ? k_tc_blind_rotate<1, false>
+                           : (level == 2 ? k_tc_blind_rotate<2, false> : k_tc_blind_rotate<3, false>));
     const int smem = smem_bytes(p.N, pair);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 3 * (size_t)tiles_pad) * 4, st));

@@ -176,7 +176,7 @@ def test_host_buffer_entry_point_matches_device(torch_cuda):
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("params,seed,levels,G", [
     (ti.TOY, ti.SEED_TOY, (0, 1), 40),
-    (ti.STD, ti.SEED_FLAT, (0, 1, 2), 37),
+    (ti.STD, ti.SEED_FLAT, (0, 1, 2, 3), 37),
 ])
 def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G, variant):
     """Every Karatsuba level of the tensor-core form, on one SM per tile and on SM pairs,
@@ -199,14 +199,18 @@ def test_tc_karatsuba_levels_bit_exact(torch_cuda, params, seed, levels, G, vari
 
 
 @pytest.mark.parametrize("limit", [0, 60000])
-@pytest.mark.parametrize("params,seed,G", [(ti.TOY, ti.SEED_TOY, 40), (ti.STD, ti.SEED_FLAT, 300)])
-def test_tc_one_and_two_pass_accumulation(torch_cuda, params, seed, G, limit):
+@pytest.mark.parametrize("params,seed,G,level", [(ti.TOY, ti.SEED_TOY, 40, -1),
+                                                 (ti.STD, ti.SEED_FLAT, 300, -1),
+                                                 (ti.STD, ti.SEED_FLAT, 300, 3)])
+def test_tc_one_and_two_pass_accumulation(torch_cuda, params, seed, G, level, limit):
     """Steps accumulated in two TMEM passes (forced everywhere with limit 0, mixed with
     one-pass steps at 60000) give the same words as the default; sampled gates match the
-    oracle."""
+    oracle.  Level 3 bounds the one-pass sum through per-block digit sums."""
     ctx, k = gpu_context(params, seed)
     b = ti.toy_gates() if params is ti.TOY else ti.flat_level(G)
     outs = []
+    if level >= 0:
+        ctx.set_tc_level(level)
     try:
         for lim in (-1, limit):
             ctx.set_tc_pass_limit(lim)
@@ -216,6 +220,7 @@ def test_tc_one_and_two_pass_accumulation(torch_cuda, params, seed, G, limit):
             outs.append(from_dev(out))
     finally:
         ctx.set_tc_pass_limit(-1)
+        ctx.set_tc_level(-1)
     assert np.array_equal(outs[0], outs[1])
     samples = [0, b.types.size // 2, b.types.size - 1]
     want = orc.gate_batch(params, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=samples)
