@@ -325,7 +325,7 @@ def run_ours(args):
         "metric": METRIC, "value": r["gates_per_s"], "unit": "gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16 (exact integer planes) -> u32" if best == "tc" else "u32",
+        "dtype": "fp16 (exact integer planes) -> u32" if best == "tc" else "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "gates": args.gates, "form": best,
                    **({"tc_level": ctx.tc_level(),

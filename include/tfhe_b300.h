@@ -187,9 +187,12 @@ int tfhe_ctx_set_tc_pass_limit(tfhe_ctx *ctx, int limit);
 enum {
     TFHE_STAGE_COMBINE = 0,          /* gate linear combination + ModSwitch (one launch) */
     TFHE_STAGE_BLIND_ROTATE_NTT = 1, /* whole BlindRotate, NTT form (one launch) */
-    TFHE_STAGE_TC_AUX = 2,           /* TC form: accumulator initialisation and the final
-                                        re-layout of the accumulators (two launches) */
-    TFHE_STAGE_BLIND_ROTATE_TC = 3,  /* TC form: the persistent BlindRotate launch alone */
+    TFHE_STAGE_TC_AUX = 2,           /* TC form: re-layout of the accumulators to [G][2][N]
+                                        (one launch; not on the gate path, whose key
+                                        switch reads the tensor-core layout directly) */
+    TFHE_STAGE_BLIND_ROTATE_TC = 3,  /* TC form: the persistent BlindRotate launch (on the
+                                        gate path it also forms the gate combinations, and
+                                        no combine launch is made) */
     TFHE_STAGE_KEYSWITCH = 4,        /* SampleExtract + identity key switch (one launch) */
     TFHE_STAGE_CMUX = 5,             /* CMUX batches, tree levels, RAM write */
     TFHE_STAGE_CB_BLIND_ROTATE = 6,  /* circuit bootstrapping: lvl2 BlindRotates (one launch) */

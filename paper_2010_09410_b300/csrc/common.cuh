@@ -170,8 +170,24 @@ int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level);
 int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant);
 int tfhe_tc_variant(tfhe_ctx *ctx);
 int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);
+// Gate inputs for the tensor-core BlindRotate's fused combination: its step-0 digit jobs
+// compute bar = ModSwitch(gate combination) from these (into the `bar` buffer) and
+// initialise the accumulators.
+struct TcGateInputs {
+    const uint32_t *in;
+    int64_t num_in;
+    const uint8_t *types;
+    const int32_t *idx;
+};
+// Accumulators of the tensor-core form stay gate-fastest within tiles of this many gates:
+// word k of polynomial c of gate g at [((g / TFHE_TC_TILE) * 2 + c) * N + k][g % TFHE_TC_TILE].
+constexpr int TFHE_TC_TILE = 128;
+// gates: NULL (bar given) or the inputs of a fused combination (bar receives it).
+// tiled_acc: NULL (acc receives [G][2][N]) or receives the context's tiled accumulators
+// (valid until the next tensor-core call; acc unused).
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                         cudaStream_t st, int level);
+                         cudaStream_t st, int level, const TcGateInputs *gates = nullptr,
+                         const uint32_t **tiled_acc = nullptr);
 int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st);
 // Reallocate a context-owned device buffer to at least `need` bytes (no copy); refused
 // while a plan graph is being recorded; bumps mem_gen.
@@ -182,6 +198,8 @@ int tfhe_mux_batch_impl(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const
 int tfhe_launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
                                   const uint8_t *types, const int32_t *idx, int64_t num_in,
                                   cudaStream_t st);
+// true when the key switch can read the tensor-core form's tiled accumulators directly
+bool tfhe_ks_reads_tiled(const tfhe_ctx *ctx);
 int tfhe_launch_modswitch_rows(tfhe_ctx *ctx, const uint32_t *in, uint32_t *bar, int64_t G,
                                cudaStream_t st);
 int tfhe_blind_rotate_form(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G, int form,
@@ -216,6 +234,24 @@ __device__ __forceinline__ uint32_t rot_coef(const uint32_t *p, int N, int k, in
     const int s = j - k;
     const uint32_t neg = (uint32_t)((s >> 31) & ~((s + N) >> 31));  // all ones or zero
     return (p[s & (N - 1)] ^ neg) - neg;
+}
+
+// Gate constants (Section 2.1.2 "Homomorphic Gates"): c = (0, kappa) + s1 c1 + s2 c2, in
+// Torus32 with 1/8 = 2^29 and 1/4 = 2^30; enum order NAND, AND, OR, NOR, XOR, XNOR,
+// ANDNY, ANDYN, ORNY, ORYN (NY negates the first input, YN the second).  t < 10.
+__device__ __forceinline__ void gate_coeffs(int t, uint32_t &kappa, uint32_t &s1, uint32_t &s2) {
+    const int8_t k8[10] = {1, -1, 1, -1, 2, -2, -1, -1, 1, 1};  // kappa in units of 2^29
+    const int8_t a1[10] = {-1, 1, 1, -1, 2, -2, -1, 1, -1, 1};
+    const int8_t a2[10] = {-1, 1, 1, -1, 2, -2, 1, -1, 1, -1};
+    kappa = (uint32_t)(int32_t)k8[t] << 29;
+    s1 = (uint32_t)(int32_t)a1[t];
+    s2 = (uint32_t)(int32_t)a2[t];
+}
+
+__device__ __forceinline__ bool gate_ok(const uint8_t *types, const int32_t *idx, int64_t num_in,
+                                        int64_t g) {
+    const int32_t a = idx[2 * g], b = idx[2 * g + 1];
+    return types[g] < 10 && a >= 0 && b >= 0 && a < num_in && b < num_in;
 }
 
 // Signed gadget digits of t (l levels of Bgbit bits, rounding to nearest, digits in

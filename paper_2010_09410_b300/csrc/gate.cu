@@ -4,21 +4,6 @@
 // entry points.
 #include "common.cuh"
 
-// Gate constants (Section 2.1.2 "Homomorphic Gates"): c = (0, kappa) + s1 c1 + s2 c2,
-// in Torus32 with 1/8 = 2^29 and 1/4 = 2^30; enum order NAND, AND, OR, NOR, XOR, XNOR,
-// ANDNY, ANDYN, ORNY, ORYN (NY negates the first input, YN the second).
-__constant__ uint32_t c_kappa[10] = {
-    1u << 29, 0u - (1u << 29), 1u << 29, 0u - (1u << 29), 1u << 30,
-    0u - (1u << 30), 0u - (1u << 29), 0u - (1u << 29), 1u << 29, 1u << 29};
-__constant__ int32_t c_s1[10] = {-1, 1, 1, -1, 2, -2, -1, 1, -1, 1};
-__constant__ int32_t c_s2[10] = {-1, 1, 1, -1, 2, -2, 1, -1, 1, -1};
-
-__device__ __forceinline__ bool gate_ok(const uint8_t *types, const int32_t *idx, int64_t num_in,
-                                        int64_t g) {
-    const int32_t a = idx[2 * g], b = idx[2 * g + 1];
-    return types[g] < 10 && a >= 0 && b >= 0 && a < num_in && b < num_in;
-}
-
 // One block per gate: bar[g][k] = ModSwitch(combination_k), k <= n.  ModSwitch rounds
 // x * 2N / 2^32 half up with 32-bit wrap (shift s = 32 - log2(2N)).
 __global__ void k_combine_modswitch(int n, int shift, const uint32_t *__restrict__ in,
@@ -35,11 +20,12 @@ __global__ void k_combine_modswitch(int n, int shift, const uint32_t *__restrict
     const int t = types[g];
     const uint32_t *c1 = in + (int64_t)idx[2 * g] * (n + 1);
     const uint32_t *c2 = in + (int64_t)idx[2 * g + 1] * (n + 1);
-    const uint32_t s1 = (uint32_t)c_s1[t], s2 = (uint32_t)c_s2[t];
+    uint32_t kappa, s1, s2;
+    gate_coeffs(t, kappa, s1, s2);
     const uint32_t half = 1u << (shift - 1);
     for (int k = threadIdx.x; k <= n; k += blockDim.x) {
         uint32_t x = s1 * c1[k] + s2 * c2[k];
-        if (k == n) x += c_kappa[t];
+        if (k == n) x += kappa;
         o[k] = (x + half) >> shift;
     }
 }
@@ -302,10 +288,17 @@ __device__ __forceinline__ bool ks_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
+// Word k of polynomial c of gate g in the accumulators: [G][2][N], or (tiled) the
+// tensor-core form's gate-fastest tiles of TFHE_TC_TILE gates.
+__device__ __forceinline__ size_t acc_at(bool tiled, int N, int g, int c, int k) {
+    return tiled ? (((size_t)(g / TFHE_TC_TILE) * 2 + c) * N + k) * TFHE_TC_TILE + (g % TFHE_TC_TILE)
+                 : ((size_t)g * 2 + c) * N + k;
+}
+
 __global__ void __launch_bounds__(KST_THREADS, 2) k_extract_keyswitch_staged(
     int n, int N, int t, int n_pad, const uint32_t *__restrict__ acc, const uint4 *__restrict__ ksk,
     uint32_t *__restrict__ out, int G, const uint8_t *__restrict__ types,
-    const int32_t *__restrict__ idx, int64_t num_in, int *err) {
+    const int32_t *__restrict__ idx, int64_t num_in, int *err, int tiled) {
     extern __shared__ __align__(128) uint8_t ks_smem[];
     const int ncol = n_pad >> 2;                // 16-byte columns of a key row
     const int pair_u4 = 3 * ncol;               // the three rows of one (i, j) pair
@@ -352,11 +345,28 @@ __global__ void __launch_bounds__(KST_THREADS, 2) k_extract_keyswitch_staged(
     const uint32_t prec = 1u << (32 - (1 + 2 * t));
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // t <= 8 (checked by the host)
+        // a'_i of the block's 16 gates: tiled, they are 64 contiguous bytes (g0 is a
+        // multiple of 16, so of 4 words); otherwise one word per gate
+        uint32_t av[KST_GT];
+        if (tiled) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(acc + acc_at(true, N, g0, 0, i == 0 ? 0 : N - i));
+#pragma unroll
+            for (int q = 0; q < KST_GT / 4; q++) {
+                const uint4 v = src[q];
+                av[4 * q] = v.x;
+                av[4 * q + 1] = v.y;
+                av[4 * q + 2] = v.z;
+                av[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < KST_GT; g++)
+                av[g] = live_s[g] ? acc[acc_at(false, N, g0 + g, 0, i == 0 ? 0 : N - i)] : 0u;
+        }
 #pragma unroll
         for (int g = 0; g < KST_GT; g++) {
             if (!live_s[g]) continue;
-            const uint32_t *A = acc + (size_t)(g0 + g) * 2 * N;
-            const uint32_t ab = ((i == 0) ? A[0] : 0u - A[N - i]) + prec;
+            const uint32_t ab = ((i == 0) ? av[g] : 0u - av[g]) + prec;
 #pragma unroll
             for (int j = 0; j < 8; j++)
                 if (j < t) w[j] |= ((ab >> (32 - (j + 1) * 2)) & 3u) << (2 * g);
@@ -423,7 +433,7 @@ __global__ void __launch_bounds__(KST_THREADS, 2) k_extract_keyswitch_staged(
         const int gg = g0 + gb;
         if (gg >= G) break;
         const bool live = live_s[gb];
-        const uint32_t bprime = live ? acc[(size_t)gg * 2 * N + N] : 0u;
+        const uint32_t bprime = live ? acc[acc_at(tiled, N, gg, 1, 0)] : 0u;
         uint32_t *o = out + (size_t)gg * (n + 1);
         const uint32_t v[4] = {res[g].x, res[g].y, res[g].z, res[g].w};
 #pragma unroll
@@ -434,9 +444,24 @@ __global__ void __launch_bounds__(KST_THREADS, 2) k_extract_keyswitch_staged(
     }
 }
 
+// The staged key switch (basebit 2, t <= 8, shared memory within 110 KB) reads either
+// accumulator layout; the others read [G][2][N] only.
+static size_t ks_staged_smem(const tfhe_ctx *ctx) {
+    const tfhe_params &p = ctx->p;
+    return (size_t)KST_STAGES * KST_IJ * 3 * ctx->n_pad * 4 + (size_t)ctx->n_pad * 4 +
+           (size_t)p.N * p.ks_t * 4;
+}
+
+bool tfhe_ks_reads_tiled(const tfhe_ctx *ctx) {
+    return ctx->p.ks_basebit == 2 && ctx->p.ks_t <= 8 && ctx->n_pad / 4 <= KST_COLS &&
+           ks_staged_smem(ctx) <= 110 * 1024;
+}
+
 static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, int G,
                                     const uint8_t *types, const int32_t *idx, int64_t num_in,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, bool tiled = false) {
+    if (tiled && !tfhe_ks_reads_tiled(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "key switch: tiled accumulators need the staged kernel");
     const tfhe_params &p = ctx->p;
     if (G == 0) return TFHE_OK;
     const size_t smem = (size_t)p.N * p.ks_t * KS_GT;
@@ -446,8 +471,7 @@ static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t
     if (ctx->n_pad / 4 > 160)
         return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "key switch: n + 1 > 640");
     if (p.ks_basebit == 2 && p.ks_t <= 8) {
-        const size_t smem_st = (size_t)KST_STAGES * KST_IJ * 3 * ctx->n_pad * 4 +
-                               (size_t)ctx->n_pad * 4 + (size_t)p.N * p.ks_t * 4;
+        const size_t smem_st = ks_staged_smem(ctx);
         if (smem_st <= 110 * 1024) {
             TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_extract_keyswitch_staged,
                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -455,7 +479,7 @@ static int launch_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t
             StageTimer tm(ctx, TFHE_STAGE_KEYSWITCH, st);
             k_extract_keyswitch_staged<<<(G + KST_GT - 1) / KST_GT, KST_THREADS, smem_st, st>>>(
                 p.n, p.N, p.ks_t, ctx->n_pad, acc, (const uint4 *)ctx->ksk, out, G, types, idx,
-                num_in, ctx->d_err);
+                num_in, ctx->d_err, tiled ? 1 : 0);
             tm.stop();
             return tfhe_check_launch(ctx, "extract_keyswitch");
         }
@@ -532,6 +556,16 @@ int tfhe_gate_batch_cfg(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const
     rc = tfhe_ensure_workspace(ctx, G);
     if (rc != TFHE_OK) return rc;
     const tfhe_params &p = ctx->p;
+    if (form == TFHE_FORM_TC && tfhe_ks_reads_tiled(ctx)) {
+        // two launches: the persistent BlindRotate (its step-0 digit jobs form the gate
+        // combinations and the accumulators), then the key switch reading the tiled
+        // accumulators
+        const TcGateInputs gin{in, num_in, types, in_idx};
+        const uint32_t *acc_t = nullptr;
+        rc = tfhe_blind_rotate_tc(ctx, ctx->ws_bar, nullptr, G, st, tc_level, &gin, &acc_t);
+        if (rc != TFHE_OK) return rc;
+        return launch_extract_keyswitch(ctx, acc_t, out, G, types, in_idx, num_in, st, true);
+    }
     const int shift = 32 - (ctx->logN + 1);
     StageTimer tm(ctx, TFHE_STAGE_COMBINE, st);
     k_combine_modswitch<<<G, 256, 0, st>>>(p.n, shift, in, num_in, types, in_idx, ctx->ws_bar,

@@ -524,27 +524,10 @@ __global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, int s, i
 
 // The tensor-core path keeps its accumulators gate-fastest within 128-gate tiles:
 // word k of polynomial c of gate g = 128 t + m sits at acc_t[((t * 2 + c) * N + k) * 128 + m],
-// so a warp's 32 gates touch one 128-byte line per word.
-//
-// ACC = X^{-b~} (0, v), v_j = mu: coefficient j of X^{-b~} v is +mu when (j + b~) mod 2N < N.
-// Gates >= G (padding of the last tile) start at zero.
-__global__ void k_tc_init_acc(int N, int n1, int G, int tiles, const uint32_t *__restrict__ bar,
-                              uint32_t *__restrict__ acc_t) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)tiles * 2 * N * TILE_M) return;
-    const int m = (int)(e % TILE_M);
-    const size_t r = e / TILE_M;
-    const int k = (int)(r % N);
-    const int c = (int)((r / N) % 2);
-    const size_t g = (r / (2 * (size_t)N)) * TILE_M + m;
-    const uint32_t mu = 1u << 29;
-    if (c == 0 || g >= (size_t)G) {
-        acc_t[e] = 0;
-    } else {
-        const int bb = (int)(bar[g * n1 + n1 - 1] % (uint32_t)(2 * N));
-        acc_t[e] = ((k + bb) % (2 * N)) < N ? mu : 0u - mu;
-    }
-}
+// so a warp's 32 gates touch one 128-byte line per word.  The step-0 digit jobs write
+// ACC(0) = X^{-b~} (0, v), v_j = mu: coefficient j of X^{-b~} v is +mu when
+// (j + b~) mod 2N < N; gates >= G (padding of the last tile) start at zero.
+static_assert(TILE_M == TFHE_TC_TILE, "tile size shared with the key switch");
 
 // acc[g][c][k] = acc_t word (g, c, k): 32 x 32 blocks through shared memory.
 // grid (N / 32, 4 * tiles, 2), block (32, 8).
@@ -674,7 +657,16 @@ struct BrArgs {
     long long total_e, total_d;
     const uint32_t *table;      // per-step job table
     const KTerm *terms;
-    const uint32_t *bar;        // [G][n+1]
+    const uint32_t *bar;        // [G][n+1] ModSwitched combinations (written at step 0 when fused)
+    // fused gate combination: when `in` is set, the step-0 digit jobs form bar[g] =
+    // ModSwitch(combination of in[idx[g][0]], in[idx[g][1]] for gate type types[g]) into
+    // bar_w (which `bar` aliases); a bad type or index gives a zero row and TFHE_EINVAL
+    const uint32_t *in;
+    int64_t num_in;
+    const uint8_t *types;
+    const int32_t *idx;
+    uint32_t *bar_w;
+    int ms_shift;               // ModSwitch shift 32 - log2(2N)
     uint32_t *acc;              // [tiles_pad][2][N][128] (gate-fastest within a tile)
     uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
     const uint4 *win;           // [n][2l][2][nterms][4][2s] units
@@ -1113,11 +1105,41 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // consecutive threads write 128 contiguous bytes of the A-operand layout (stage
             // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
             const int pitch = N + 4;
-            int rot8[8];
+            __shared__ uint32_t bbar_s[8];  // b~ of the part's gates (step 0)
+            if (i == 0) {
+                // step 0: the part's ModSwitched combinations (fused form) and b~
+                const int n1 = a.n1;
+                if (a.in) {
+                    for (int e = tid; e < 8 * n1; e += 128) {
+                        const int m = e / n1, k = e - m * n1;
+                        const int64_t g = (int64_t)gt * TILE_M + mg * 8 + m;
+                        if (g >= a.G) continue;
+                        uint32_t v = 0;
+                        if (gate_ok(a.types, a.idx, a.num_in, g)) {
+                            uint32_t kappa, s1, s2;
+                            gate_coeffs(a.types[g], kappa, s1, s2);
+                            uint32_t x = s1 * __ldg(a.in + (int64_t)a.idx[2 * g] * n1 + k) +
+                                         s2 * __ldg(a.in + (int64_t)a.idx[2 * g + 1] * n1 + k);
+                            if (k == n1 - 1) x += kappa;
+                            v = (x + (1u << (a.ms_shift - 1))) >> a.ms_shift;
+                        } else if (k == 0) {
+                            atomicCAS(err, 0, TFHE_EINVAL);
+                        }
+                        a.bar_w[g * n1 + k] = v;
+                    }
+                    asm volatile("bar.sync 2, 128;" ::: "memory");
+                }
+                if (tid < 8) {
+                    const int g = gt * TILE_M + mg * 8 + tid;
+                    bbar_s[tid] = g < a.G ? __ldcg(a.bar + (size_t)g * n1 + n1 - 1) % (uint32_t)(2 * N) : 0u;
+                }
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+            }
+            int rot8[8];  // written at step 0 of this launch when fused: coherent loads
 #pragma unroll
             for (int m8 = 0; m8 < 8; m8++) {
                 const int g = gt * TILE_M + mg * 8 + m8;
-                rot8[m8] = g < a.G ? (int)(__ldg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
+                rot8[m8] = g < a.G ? (int)(__ldcg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
             }
             const int m8 = tid & 7, kb = tid >> 3;
             for (int v = tid; v < 8 * NBLK; v += 128) d_abs[v] = 0;
@@ -1132,12 +1154,28 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 asm volatile("bar.sync 2, 128;" ::: "memory");  // previous polynomial consumed
                 {
                     // item (k, h): word k for gates 4h .. 4h+3 of the part, 16 bytes of the
-                    // tiled accumulator; the rows of two gate halves land on disjoint banks
-                    const uint32_t *accp = a.acc + (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
+                    // tiled accumulator; the rows of two gate halves land on disjoint banks.
+                    // Step 0 writes ACC(0) instead of reading it.
+                    uint32_t *accp = a.acc + (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
 #pragma unroll 4
                     for (int it = tid; it < 2 * N; it += 128) {
                         const int k = it >> 1, h = it & 1;
-                        const uint4 o = __ldcg((const uint4 *)(accp + (size_t)k * TILE_M) + h);
+                        uint4 o;
+                        if (i > 0) {
+                            o = __ldcg((const uint4 *)(accp + (size_t)k * TILE_M) + h);
+                        } else {
+                            uint32_t v[4] = {0u, 0u, 0u, 0u};
+                            if (c == 1) {
+#pragma unroll
+                                for (int q = 0; q < 4; q++) {
+                                    const int g = gt * TILE_M + mg * 8 + 4 * h + q;
+                                    const uint32_t mu = 1u << 29;
+                                    if (g < a.G) v[q] = ((uint32_t)k + bbar_s[4 * h + q]) % (uint32_t)(2 * N) < (uint32_t)N ? mu : 0u - mu;
+                                }
+                            }
+                            o = make_uint4(v[0], v[1], v[2], v[3]);
+                            __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, o);
+                        }
                         uint32_t *rr = d_rows + 4 * h * pitch + k;
                         rr[0] = o.x;
                         rr[pitch] = o.y;
@@ -1556,7 +1594,8 @@ int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level) {
 }
 
 int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                         cudaStream_t st, int level) {
+                         cudaStream_t st, int level, const TcGateInputs *gates,
+                         const uint32_t **tiled_acc) {
     const tfhe_params &p = ctx->p;
     if (G == 0) return TFHE_OK;
     if (!tfhe_tc_supported(ctx))
@@ -1613,6 +1652,12 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     args.table = table->d;
     args.terms = V.d_terms;
     args.bar = bar;
+    args.in = gates ? gates->in : nullptr;
+    args.num_in = gates ? gates->num_in : 0;
+    args.types = gates ? gates->types : nullptr;
+    args.idx = gates ? gates->idx : nullptr;
+    args.bar_w = gates ? const_cast<uint32_t *>(bar) : nullptr;
+    args.ms_shift = 32 - (ctx->logN + 1);
     args.acc = w->acc_t;
     args.digits = w->digits;
     args.win = V.win;
@@ -1646,20 +1691,15 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         cfg.gridDim = dim3((unsigned)(args.total_e < w->sms ? args.total_e : w->sms));
     }
     {
-        StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
-        const size_t total = (size_t)tiles_pad * 2 * p.N * TILE_M;
-        k_tc_init_acc<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.N, n1, G, tiles_pad, bar,
-                                                                      w->acc_t);
-        ta.stop();
-        rc = tfhe_check_launch(ctx, "tc_init_acc");
-        if (rc != TFHE_OK) return rc;
-    }
-    {
         StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
         TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
         tm.stop();
         rc = tfhe_check_launch(ctx, "tc blind rotate");
         if (rc != TFHE_OK) return rc;
+    }
+    if (tiled_acc) {  // the caller reads the tiled accumulators (the gate path's key switch)
+        *tiled_acc = w->acc_t;
+        return TFHE_OK;
     }
     StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
     k_tc_untile_acc<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * tiles), 2), dim3(32, 8), 0, st>>>(

@@ -143,7 +143,12 @@ def test_zero_gates_is_noop(torch_cuda):
     ctx.sync()
 
 
-def test_bad_type_and_index_reported_on_device(torch_cuda):
+@pytest.mark.parametrize("form", [0, 1])
+def test_bad_type_and_index_reported_on_device(torch_cuda, form):
+    """A bad gate type and an out-of-range input index are caught on the device: those
+    gates give all-zero outputs, TFHE_EINVAL comes back at the next sync, and every other
+    gate is still bit-exact (form 1: the tensor-core BlindRotate forms the combinations
+    itself)."""
     b = ti.toy_gates()
     ctx, k = gpu_context(ti.TOY, ti.SEED_TOY)
     types = b.types.copy()
@@ -151,7 +156,7 @@ def test_bad_type_and_index_reported_on_device(torch_cuda):
     types[2] = 10
     idx[5, 1] = 1000
     out = empty(torch_cuda, types.size, ti.TOY.n + 1)
-    ctx.gate_batch(to_dev(b.inp), to_dev(types), to_dev(idx), out)
+    ctx.gate_batch(to_dev(b.inp), to_dev(types), to_dev(idx), out, form=form)
     import paper_2010_09410_b300 as tb
     with pytest.raises(tb.TfheError) as e:
         ctx.sync()
