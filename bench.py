@@ -690,11 +690,43 @@ def run_other(args):
         cells = cells0.clone()
         ctx.reserve(256)
 
+        # best: the two-prime NTT form and the tensor-core form (tree levels with >= 128
+        # CMUXes per selector on the tensor cores, the rest and the write bars in NTT)
+        cm_forms = {"ntt2": tb.FORM_NTT2, "tc": tb.FORM_TC}
+        if args.form in cm_forms:
+            cm_forms = {args.form: cm_forms[args.form]}
+        cm_form = [next(iter(cm_forms.values()))]
+
         def step():
-            ctx.cmux_tree_read(addr, table, 9, rout)
+            ctx.cmux_tree_read(addr, table, 9, rout, form=cm_form[0])
             cells.copy_(cells0)
-            ctx.ram_write(raddr, 8, rnew, cells)
+            ctx.ram_write(raddr, 8, rnew, cells, form=cm_form[0])
         units, unit = 64 * 511 + 256 * 8, "CMUX external products/s"
+        if len(cm_forms) > 1:
+            per_form = {}
+            for name, f in cm_forms.items():
+                cm_form[0] = f
+                step()
+                ctx.sync()
+                for _ in range(args.warmup):
+                    flush.fill_(1)
+                    step()
+                torch.cuda.synchronize()
+                ms_f = []
+                for _ in range(args.steps):
+                    flush.fill_(1)
+                    a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    step()
+                    b0.record(stream)
+                    torch.cuda.synchronize()
+                    ms_f.append(a0.elapsed_time(b0))
+                per_form[name] = {"ext_products_per_s": units / (statistics.median(ms_f) / 1e3),
+                                  "ms_per_step": statistics.median(ms_f)}
+            best = max(per_form, key=lambda n: per_form[n]["ext_products_per_s"])
+            cm_form[0] = cm_forms[best]
+            extra["forms"] = per_form
+            extra["form"] = best
         metric = "CMUX external products/s (64 reads of a 512-row TRLWE table + 256-cell RAM write)"
         workload = "ROM 512 rows x 64 reads (9 address bits) + RAM write 256 cells (8 bits), N=1024 l=3 Bgbit=6"
         step()

@@ -286,10 +286,11 @@ int tfhe_extract_keyswitch(tfhe_ctx *ctx, const uint32_t *acc, uint32_t *out, in
  * C_k = trgsw + (k / group) * (2l * 2 * N) -- consecutive runs of `group` CMUXes
  * share one TRGSW selector.  d1, d0, out: device u32[B][2][N]; out may alias d0 or
  * d1 (same k only).  trgsw: device u32[ceil(B / group)][2l][2][N].
- * CMUX batches, trees and RAM writes run in the NTT form (the two-prime arithmetic of
- * TFHE_FORM_NTT2): form TFHE_FORM_NTT or TFHE_FORM_NTT2; TFHE_FORM_TC returns
- * TFHE_EUNSUPPORTED (the tensor-core form covers the BlindRotate of gate batches, whose
- * key is shared by the whole batch). */
+ * form TFHE_FORM_NTT or TFHE_FORM_NTT2: the two-prime NTT arithmetic of TFHE_FORM_NTT2.
+ * TFHE_FORM_TC: groups of at least 128 CMUXes sharing a selector run on the tensor cores
+ * (the selector takes the place of BSK_i in one BlindRotate step; its key windows are
+ * expanded on each call, 3.5 MB per selector at N = 1024), smaller groups in the
+ * two-prime NTT form.  Results are identical in every form. */
 int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint32_t *d1,
                     const uint32_t *d0, uint32_t *out, int B, int form, void *stream);
 
@@ -297,7 +298,8 @@ int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group, const uint3
  * 2^v TRLWE rows.  Address bit j (least significant first) selects at tree level j:
  *   node_j[k] = CMUX(C_{r,j}, node_{j-1}[2k+1], node_{j-1}[2k]),  node_{-1} = table.
  * addr_trgsw: device u32[R][v][2l][2][N]; table: device u32[2^v][2][N];
- * out: device u32[R][2][N].  1 <= v <= 16.  form: TFHE_FORM_NTT (see tfhe_cmux_batch). */
+ * out: device u32[R][2][N].  1 <= v <= 16.  form as for tfhe_cmux_batch: with
+ * TFHE_FORM_TC the levels with at least 128 CMUXes per read run on the tensor cores. */
 int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_t *table, int v,
                         uint32_t *out, int R, int form, void *stream);
 
@@ -305,8 +307,9 @@ int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw, const uint32_
  * cell c of the 2^v cells, r <- new_cell; for j = 0..v-1: r <- CMUX(S_j, r, cell_c)
  * with S_j = C_j if bit j of c is 1 else G - C_j (G the gadget TRGSW of 1); then
  * cell_c <- r.  addr_trgsw: device u32[v][2l][2][N]; new_cell: device u32[2][N];
- * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16.  form: TFHE_FORM_NTT
- * (see tfhe_cmux_batch). */
+ * cells: device u32[2^v][2][N], updated in place.  1 <= v <= 16.  Every form runs the
+ * write bars in the two-prime NTT arithmetic: at step j a cell takes C_j or G - C_j by
+ * bit j of its index, so the cells that share a selector are not contiguous tiles. */
 int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v, const uint32_t *new_cell,
                    uint32_t *cells, int form, void *stream);
 

@@ -55,14 +55,14 @@ extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
     const int M0 = 1 << (v - 1);
     rc = tfhe_ensure_workspace(ctx, R * M0);
     if (rc != TFHE_OK) return rc;
-    const uint64_t *sel_ntt = nullptr;
-    if (form != TFHE_FORM_TC) {
-        rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
-        if (rc != TFHE_OK) return rc;
-        rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
-        if (rc != TFHE_OK) return rc;
-        sel_ntt = ctx->ws_trgsw_ntt;
-    }
+    // tensor-core form: tree levels with at least one 128-CMUX tile per selector run on
+    // the tensor cores, narrower levels (always the last ones) in the two-prime NTT form
+    const bool tc = form == TFHE_FORM_TC;
+    rc = tfhe_ensure_trgsw_ws(ctx, (size_t)R * v);
+    if (rc != TFHE_OK) return rc;
+    rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)R * v, st);
+    if (rc != TFHE_OK) return rc;
+    const uint64_t *sel_ntt = ctx->ws_trgsw_ntt;
     uint32_t *buf[2] = {ctx->ws_acc, ctx->ws_tmp};
     const uint32_t *in = table;
     int64_t in_ystride = 0;  // level 0 reads the shared table
@@ -71,19 +71,16 @@ extern "C" int tfhe_cmux_tree_read(tfhe_ctx *ctx, const uint32_t *addr_trgsw,
         uint32_t *o = (j == v - 1) ? out : buf[j & 1];
         CmuxGeom g{in + N2, in, o, 2 * N2, in_ystride, N2, (int64_t)M * N2, (int64_t)v,
                    M, R, (int64_t)R * M};
-        if (form != TFHE_FORM_TC)
-            rc = tfhe_cmux_ntt(ctx, sel_ntt + (size_t)j * per, g, st);
-        else
+        if (tc && M >= TFHE_TC_TILE)
             rc = tfhe_cmux_tc(ctx, addr_trgsw + (size_t)j * per, g, st);
+        else
+            rc = tfhe_cmux_ntt(ctx, sel_ntt + (size_t)j * per, g, st);
         if (rc != TFHE_OK) return rc;
         in = o;
         in_ystride = (int64_t)M * N2;
     }
     return TFHE_OK;
 }
-
-int tfhe_ram_write_tc(tfhe_ctx *ctx, const uint32_t *c, const uint32_t *gmc, int v,
-                      const uint32_t *new_cell, uint32_t *cells, cudaStream_t st);
 
 extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
                               const uint32_t *new_cell, uint32_t *cells, int form,
@@ -110,8 +107,8 @@ extern "C" int tfhe_ram_write(tfhe_ctx *ctx, const uint32_t *addr_trgsw, int v,
     k_gadget_minus<<<256, 256, 0, st>>>(addr_trgsw, ctx->ws_gmc, v, p.l, p.N, p.Bgbit);
     rc = tfhe_check_launch(ctx, "gadget_minus");
     if (rc != TFHE_OK) return rc;
-    if (form == TFHE_FORM_TC) return tfhe_ram_write_tc(ctx, addr_trgsw, ctx->ws_gmc, v, new_cell,
-                                                       cells, st);
+    // every form runs the write bars in the two-prime NTT form: at step j a cell takes
+    // C_j or G - C_j by bit j of its index, so cells sharing a selector are not contiguous
     rc = tfhe_ensure_trgsw_ws(ctx, (size_t)2 * v);
     if (rc != TFHE_OK) return rc;
     rc = tfhe_sel_to_ntt(ctx, addr_trgsw, ctx->ws_trgsw_ntt, (size_t)v, st);

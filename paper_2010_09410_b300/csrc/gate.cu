@@ -620,7 +620,8 @@ extern "C" int tfhe_cmux_batch(tfhe_ctx *ctx, const uint32_t *trgsw, int group,
     const int gx = group < B ? group : B;
     const int ny = (B + group - 1) / group;
     CmuxGeom g{d1, d0, out, N2, (int64_t)group * N2, N2, (int64_t)group * N2, 1, gx, ny, B};
-    if (form == TFHE_FORM_TC) return tfhe_cmux_tc(ctx, trgsw, g, st);
+    // tensor-core form for groups of at least one 128-CMUX tile, else the NTT form
+    if (form == TFHE_FORM_TC && gx >= TFHE_TC_TILE) return tfhe_cmux_tc(ctx, trgsw, g, st);
     rc = tfhe_ensure_trgsw_ws(ctx, (size_t)ny);
     if (rc != TFHE_OK) return rc;
     rc = tfhe_sel_to_ntt(ctx, trgsw, ctx->ws_trgsw_ntt, (size_t)ny, st);

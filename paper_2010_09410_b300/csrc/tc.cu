@@ -484,14 +484,16 @@ __device__ __forceinline__ uint32_t neg_gen(const uint32_t *__restrict__ q, int 
     return e >= 0 ? __ldg(q + e) : 0u - __ldg(q + e + N);
 }
 
-// Window units of term T for every (step, row, column) key polynomial:
+// Window units of term T for every (key, row, column) polynomial:
 // win[((poly * nterms + j) * 4 + p) * 2s + u] holds byte plane p of r_vec_j[u .. u+7].
-// blockIdx.x = key polynomial (BSK order), blockIdx.y = term.
+// blockIdx.x = key polynomial (keys of ppk polynomials: BSK_i, or CMUX selectors that lie
+// key_stride polynomials apart), blockIdx.y = term.
 __global__ void k_tc_windows(const uint32_t *__restrict__ polys, int N, int s, int nterms,
-                             const KTerm *__restrict__ terms, uint4 *__restrict__ win) {
+                             const KTerm *__restrict__ terms, uint4 *__restrict__ win, int ppk,
+                             int64_t key_stride) {
     const size_t poly = blockIdx.x;
     const int j = blockIdx.y;
-    const uint32_t *q = polys + poly * N;
+    const uint32_t *q = polys + ((int64_t)(poly / ppk) * key_stride + poly % ppk) * N;
     const KTerm T = terms[j];
     for (int u = threadIdx.x; u < 2 * s; u += blockDim.x) {
         uint32_t w[PLANES][4];
@@ -545,6 +547,27 @@ __global__ void k_tc_untile_acc(int N, int G, const uint32_t *__restrict__ acc_t
     for (int i = 0; i < 32; i += 8) {
         const int g = g0 + threadIdx.y + i;
         if (g < G) acc[((size_t)g * 2 + c) * N + k0 + threadIdx.x] = t[threadIdx.x][threadIdx.y + i];
+    }
+}
+
+// CMUX mode: out + x ox + y oy (+ c N + k) = acc_t word (tile, c, k, m) for the tile's
+// CMUX x = (tile % tpg) * 128 + m of group y = tile / tpg.  grid (N / 32, 4 * tiles, 2).
+__global__ void k_tc_untile_cmux(int N, int tpg, int nx, int64_t count, int64_t ox, int64_t oy,
+                                 const uint32_t *__restrict__ acc_t, uint32_t *__restrict__ out) {
+    __shared__ uint32_t t[32][33];
+    const int k0 = blockIdx.x * 32, g0 = blockIdx.y * 32, c = blockIdx.z;
+    const int tile = g0 / TILE_M, m0 = g0 % TILE_M;
+    const uint32_t *src = acc_t + ((size_t)(tile * 2 + c) * N + k0) * TILE_M + m0;
+#pragma unroll
+    for (int i = 0; i < 32; i += 8)
+        t[threadIdx.y + i][threadIdx.x] = src[(size_t)(threadIdx.y + i) * TILE_M + threadIdx.x];
+    __syncthreads();
+    const int y = tile / tpg;
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+        const int x = (tile % tpg) * TILE_M + m0 + threadIdx.y + i;
+        if (x < nx && (int64_t)y * nx + x < count)
+            out[x * ox + y * oy + (int64_t)c * N + k0 + threadIdx.x] = t[threadIdx.x][threadIdx.y + i];
     }
 }
 
@@ -667,6 +690,14 @@ struct BrArgs {
     const int32_t *idx;
     uint32_t *bar_w;
     int ms_shift;               // ModSwitch shift 32 - log2(2N)
+    // CMUX mode (one step): tile gt holds CMUXes x = (gt % tpg) * 128 + lane of group
+    // y = gt / tpg, whose selector's windows are key y; ACC(0) = d0 and the digits are
+    // those of d1 - d0 (no rotation); CMUX (x, y) reads d1/d0 + x dx + y dy (words)
+    int cmux, tpg;
+    const uint32_t *cm_d1, *cm_d0;
+    int64_t cm_dx, cm_dy;
+    int cm_nx;
+    int64_t cm_count;
     uint32_t *acc;              // [tiles_pad][2][N][128] (gate-fastest within a tile)
     uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
     const uint4 *win;           // [n][2l][2][nterms][4][2s] units
@@ -841,7 +872,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     mbar_arrive_tx(&full[st], A_STAGE_BYTES + BST);
                     bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
                              A_STAGE_BYTES, &full[st]);
-                    const size_t poly = ((size_t)J.i * 2 * l + r) * 2 + J.c;
+                    const size_t poly = ((size_t)(a.cmux ? gt / a.tpg : J.i) * 2 * l + r) * 2 + J.c;
                     const uint4 *wsrc = a.win + ((poly * a.nterms + J.j) * PLANES) * 2 * s +
                                         (P0 + ks * KS);
 #pragma unroll
@@ -1106,7 +1137,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
             const int pitch = N + 4;
             __shared__ uint32_t bbar_s[8];  // b~ of the part's gates (step 0)
-            if (i == 0) {
+            if (i == 0 && !a.cmux) {
                 // step 0: the part's ModSwitched combinations (fused form) and b~
                 const int n1 = a.n1;
                 if (a.in) {
@@ -1139,7 +1170,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 #pragma unroll
             for (int m8 = 0; m8 < 8; m8++) {
                 const int g = gt * TILE_M + mg * 8 + m8;
-                rot8[m8] = g < a.G ? (int)(__ldcg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
+                rot8[m8] = g < a.G && !a.cmux ? (int)(__ldcg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
             }
             const int m8 = tid & 7, kb = tid >> 3;
             for (int v = tid; v < 8 * NBLK; v += 128) d_abs[v] = 0;
@@ -1161,7 +1192,20 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     for (int it = tid; it < 2 * N; it += 128) {
                         const int k = it >> 1, h = it & 1;
                         uint4 o;
-                        if (i > 0) {
+                        if (a.cmux) {
+                            // ACC(0) = d0; the shared rows take d1 - d0
+                            uint32_t v0[4], v1[4];
+#pragma unroll
+                            for (int q = 0; q < 4; q++) {
+                                const int x = (gt % a.tpg) * TILE_M + mg * 8 + 4 * h + q, y = gt / a.tpg;
+                                const bool ok = x < a.cm_nx && (int64_t)y * a.cm_nx + x < a.cm_count;
+                                const int64_t o_ = (int64_t)x * a.cm_dx + (int64_t)y * a.cm_dy + (int64_t)c * N + k;
+                                v0[q] = ok ? __ldg(a.cm_d0 + o_) : 0u;
+                                v1[q] = ok ? __ldg(a.cm_d1 + o_) - v0[q] : 0u;
+                            }
+                            __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, make_uint4(v0[0], v0[1], v0[2], v0[3]));
+                            o = make_uint4(v1[0], v1[1], v1[2], v1[3]);
+                        } else if (i > 0) {
                             o = __ldcg((const uint4 *)(accp + (size_t)k * TILE_M) + h);
                         } else {
                             uint32_t v[4] = {0u, 0u, 0u, 0u};
@@ -1201,13 +1245,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                 own[q + 2] = o4.z;
                                 own[q + 3] = o4.w;
                             }
+                            if (a.cmux) {  // the rows hold d1 - d0
 #pragma unroll
-                            for (int e = 0; e < E; e++) {
-                                const int k = k0 + e;
-                                const int src = k - rk;
-                                uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
-                                v = (v ^ rneg) - rneg;  // negate when rot >= N
-                                xv[b][e] = v - own[e];
+                                for (int e = 0; e < E; e++) xv[b][e] = own[e];
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < E; e++) {
+                                    const int k = k0 + e;
+                                    const int src = k - rk;
+                                    uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
+                                    v = (v ^ rneg) - rneg;  // negate when rot >= N
+                                    xv[b][e] = v - own[e];
+                                }
                             }
                         }
                         for (int jd = 0; jd < l; jd++) {
@@ -1379,6 +1428,8 @@ struct TcWorkspace {
     size_t sync_cap = 0;       // words
     uint32_t *acc_t = nullptr; // accumulators, gate-fastest within 128-gate tiles
     size_t acc_t_cap = 0;      // bytes
+    uint4 *cm_win = nullptr;   // windows of the CMUX selectors of one call
+    size_t cm_win_cap = 0;     // bytes
     struct JobTable {
         uint32_t *d = nullptr;  // per-step product-job table
         int len = 0;            // entries
@@ -1424,6 +1475,7 @@ void tfhe_tc_free(tfhe_ctx *ctx) {
     if (w->digits) cudaFree(w->digits);
     if (w->sync) cudaFree(w->sync);
     if (w->acc_t) cudaFree(w->acc_t);
+    if (w->cm_win) cudaFree(w->cm_win);
     for (auto &t : w->tables) cudaFree(t.second.d);
     delete w;
     ctx->tc = nullptr;
@@ -1433,27 +1485,38 @@ static int grow_dev(tfhe_ctx *ctx, void **ptr, size_t *cap, size_t need, const c
     return tfhe_grow(ctx, ptr, cap, need, what);
 }
 
+// The term plan of `level` on the device (built once; the CMUX form needs it without keys).
+static int ensure_plan(tfhe_ctx *ctx, int level, cudaStream_t st) {
+    TcWorkspace::Level &V = ctx->tc->lv[level];
+    if (!V.terms.empty() && V.d_terms) return TFHE_OK;
+    if (ctx->capturing)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core plan: cannot build while recording");
+    build_plan(ctx->p.N, level, V.terms);
+    if (V.terms.empty())
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba plan differs from the kernels' table");
+    if (!V.d_terms && cudaMalloc(&V.d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
+        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core term plan");
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(V.d_terms, V.terms.data(), sizeof(KTerm) * V.terms.size(),
+                                       cudaMemcpyHostToDevice, st));
+    return TFHE_OK;
+}
+
 // (Re)build the term plan of `level` and expand the windows of the whole BSK for it.
 static int prepare_windows(tfhe_ctx *ctx, int level, cudaStream_t st) {
     const tfhe_params &p = ctx->p;
     TcWorkspace::Level &V = ctx->tc->lv[level];
     if (ctx->capturing)
         return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core windows: cannot rebuild while recording");
-    build_plan(p.N, level, V.terms);
-    if (V.terms.empty())
-        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba plan differs from the kernels' table");
+    int rc = ensure_plan(ctx, level, st);
+    if (rc != TFHE_OK) return rc;
     const int T = (int)V.terms.size();
     const int s = p.N >> level;
-    if (!V.d_terms && cudaMalloc(&V.d_terms, sizeof(KTerm) * MAX_TERMS) != cudaSuccess)
-        return tfhe_set_error(ctx, TFHE_ENOMEM, "tensor-core term plan");
-    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(V.d_terms, V.terms.data(), sizeof(KTerm) * T,
-                                       cudaMemcpyHostToDevice, st));
     const size_t npoly = (size_t)p.n * 2 * p.l * 2;
     const size_t bytes = npoly * T * PLANES * 2 * (size_t)s * sizeof(uint4);
-    int rc = grow_dev(ctx, (void **)&V.win, &V.win_cap, bytes, "tensor-core key windows");
+    rc = grow_dev(ctx, (void **)&V.win, &V.win_cap, bytes, "tensor-core key windows");
     if (rc != TFHE_OK) return rc;
     k_tc_windows<<<dim3((unsigned)npoly, T), 256, 0, st>>>(ctx->bsk_raw, p.N, s, T, V.d_terms,
-                                                          V.win);
+                                                          V.win, 1, 1);
     rc = tfhe_check_launch(ctx, "tc_windows");
     if (rc != TFHE_OK) return rc;
     V.ready = true;
@@ -1593,24 +1656,18 @@ int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level) {
     return reserve_tc(ctx, gates, resolve_level(ctx, level), nullptr);
 }
 
-int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
-                         cudaStream_t st, int level, const TcGateInputs *gates,
-                         const uint32_t **tiled_acc) {
+// Arguments of a `steps`-step persistent launch over the tiles of G rows (gates or
+// CMUXes), with the buffers and job table sized for it; the caller sets the mode fields.
+static int persistent_args(tfhe_ctx *ctx, int G, int steps, int level, const uint4 *win,
+                           BrArgs &args) {
     const tfhe_params &p = ctx->p;
-    if (G == 0) return TFHE_OK;
-    if (!tfhe_tc_supported(ctx))
-        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
-    int rc = tfhe_tc_ensure_level(ctx, level, st);
-    if (rc != TFHE_OK) return rc;
-    level = resolve_level(ctx, level);
     TcWorkspace *w = ctx->tc;
     const TcWorkspace::Level &V = w->lv[level];
-    if (!V.ready) return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
     const int tiles = (G + TILE_M - 1) / TILE_M;
     const int T = (int)V.terms.size();
     const int s = p.N >> level;
     const TcWorkspace::JobTable *table = nullptr;
-    rc = reserve_tc(ctx, G, level, &table);
+    int rc = reserve_tc(ctx, G, level, &table);
     if (rc != TFHE_OK) return rc;
     if (!w->sms) {
         int sms = 0;
@@ -1618,8 +1675,38 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         w->sms = sms;
     }
     const bool pair = use_pair(ctx);
-    const int tiles_pad = pair ? (tiles + 1) / 2 * 2 : tiles;
-    const int n1 = p.n + 1;
+    args = BrArgs{};
+    args.N = p.N;
+    args.l = p.l;
+    args.Bgbit = p.Bgbit;
+    args.G = G;
+    args.n = steps;
+    args.n1 = p.n + 1;
+    args.s = s;
+    args.nterms = T;
+    args.tiles = tiles;
+    args.tiles_pad = pair ? (tiles + 1) / 2 * 2 : tiles;
+    args.one_pass_limit = w->one_pass_limit;
+    args.cbs = 2 * (s / NB);
+    args.e_per_tile = T * 2 * (s / NB);
+    args.step_len = table->len;
+    args.total_e = (long long)steps * table->len;
+    args.total_d = (long long)steps * tiles * DPARTS;
+    args.table = table->d;
+    args.terms = V.d_terms;
+    args.ms_shift = 32 - (ctx->logN + 1);
+    args.acc = w->acc_t;
+    args.digits = w->digits;
+    args.win = win;
+    args.sync = w->sync;
+    args.err = ctx->d_err;
+    return TFHE_OK;
+}
+
+// Launch the persistent kernel of `level` with `args` (one block per SM, or SM pairs).
+static int launch_persistent(tfhe_ctx *ctx, const BrArgs &args, int level, cudaStream_t st) {
+    TcWorkspace *w = ctx->tc;
+    const bool pair = use_pair(ctx);
     void (*kern)(BrArgs);
     if (pair)
         kern = level == 0 ? k_tc_blind_rotate<0, true>
@@ -1629,41 +1716,9 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
         kern = level == 0 ? k_tc_blind_rotate<0, false>
              : (level == 1 ? k_tc_blind_rotate<1, false>
                            : (level == 2 ? k_tc_blind_rotate<2, false> : k_tc_blind_rotate<3, false>));
-    const int smem = smem_bytes(p.N, pair);
+    const int smem = smem_bytes(ctx->p.N, pair);
     TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 3 * (size_t)tiles_pad) * 4, st));
-    BrArgs args;
-    args.N = p.N;
-    args.l = p.l;
-    args.Bgbit = p.Bgbit;
-    args.G = G;
-    args.n = p.n;
-    args.n1 = n1;
-    args.s = s;
-    args.nterms = T;
-    args.tiles = tiles;
-    args.tiles_pad = tiles_pad;
-    args.one_pass_limit = w->one_pass_limit;
-    args.cbs = 2 * (s / NB);
-    args.e_per_tile = T * 2 * (s / NB);
-    args.step_len = table->len;
-    args.total_e = (long long)p.n * table->len;
-    args.total_d = (long long)p.n * tiles * DPARTS;
-    args.table = table->d;
-    args.terms = V.d_terms;
-    args.bar = bar;
-    args.in = gates ? gates->in : nullptr;
-    args.num_in = gates ? gates->num_in : 0;
-    args.types = gates ? gates->types : nullptr;
-    args.idx = gates ? gates->idx : nullptr;
-    args.bar_w = gates ? const_cast<uint32_t *>(bar) : nullptr;
-    args.ms_shift = 32 - (ctx->logN + 1);
-    args.acc = w->acc_t;
-    args.digits = w->digits;
-    args.win = V.win;
-    args.sync = w->sync;
-    args.err = ctx->d_err;
-
+    TFHE_CUDA_TRY(ctx, cudaMemsetAsync(w->sync, 0, (2 + 3 * (size_t)args.tiles_pad) * 4, st));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(P_THREADS);
@@ -1690,22 +1745,101 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     } else {
         cfg.gridDim = dim3((unsigned)(args.total_e < w->sms ? args.total_e : w->sms));
     }
-    {
-        StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
-        TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
-        tm.stop();
-        rc = tfhe_check_launch(ctx, "tc blind rotate");
-        if (rc != TFHE_OK) return rc;
-    }
+    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_TC, st);
+    TFHE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, args));
+    tm.stop();
+    return tfhe_check_launch(ctx, "tc blind rotate");
+}
+
+int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int G,
+                         cudaStream_t st, int level, const TcGateInputs *gates,
+                         const uint32_t **tiled_acc) {
+    const tfhe_params &p = ctx->p;
+    if (G == 0) return TFHE_OK;
+    if (!tfhe_tc_supported(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
+    int rc = tfhe_tc_ensure_level(ctx, level, st);
+    if (rc != TFHE_OK) return rc;
+    level = resolve_level(ctx, level);
+    TcWorkspace *w = ctx->tc;
+    const TcWorkspace::Level &V = w->lv[level];
+    if (!V.ready) return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
+    BrArgs args;
+    rc = persistent_args(ctx, G, p.n, level, V.win, args);
+    if (rc != TFHE_OK) return rc;
+    args.bar = bar;
+    args.in = gates ? gates->in : nullptr;
+    args.num_in = gates ? gates->num_in : 0;
+    args.types = gates ? gates->types : nullptr;
+    args.idx = gates ? gates->idx : nullptr;
+    args.bar_w = gates ? const_cast<uint32_t *>(bar) : nullptr;
+    rc = launch_persistent(ctx, args, level, st);
+    if (rc != TFHE_OK) return rc;
     if (tiled_acc) {  // the caller reads the tiled accumulators (the gate path's key switch)
         *tiled_acc = w->acc_t;
         return TFHE_OK;
     }
     StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
-    k_tc_untile_acc<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * tiles), 2), dim3(32, 8), 0, st>>>(
+    k_tc_untile_acc<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * args.tiles), 2), dim3(32, 8), 0, st>>>(
         p.N, G, w->acc_t, acc);
     ta.stop();
     return tfhe_check_launch(ctx, "tc untile accumulators");
+}
+
+// Batched CMUX on the tensor cores: out(x, y) = d0 + C_y (.) (d1 - d0) for the geometry g
+// (groups of g.nx CMUXes sharing selector C_y = sel + y * g.sy TRGSWs).  One step of the
+// persistent kernel in CMUX mode over ceil(nx / 128) tiles per group; the selectors'
+// windows are expanded for this call.  No keys are needed.
+int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (g.count <= 0 || g.nx <= 0 || g.ny <= 0) return TFHE_OK;
+    if (!tfhe_tc_supported(ctx))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core form: unsupported parameters");
+    if (!ctx->tc) ctx->tc = new TcWorkspace();
+    const int level = resolve_level(ctx, -1);
+    if (!level_ok(p, level))
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "Karatsuba level not supported for this N");
+    int rc = ensure_plan(ctx, level, st);
+    if (rc != TFHE_OK) return rc;
+    TcWorkspace *w = ctx->tc;
+    const TcWorkspace::Level &V = w->lv[level];
+    const int T = (int)V.terms.size();
+    const int s = p.N >> level;
+    const int tpg = (g.nx + TILE_M - 1) / TILE_M;
+    const int64_t tiles = (int64_t)tpg * g.ny;
+    if (tiles * TILE_M > (int64_t)1 << 30)
+        return tfhe_set_error(ctx, TFHE_EINVAL, "tensor-core CMUX: batch too large");
+    const int ppk = 2 * p.l * 2;  // polynomials per selector
+    const size_t npoly = (size_t)g.ny * ppk;
+    rc = grow_dev(ctx, (void **)&w->cm_win, &w->cm_win_cap,
+                  npoly * T * PLANES * 2 * (size_t)s * sizeof(uint4), "tensor-core CMUX windows");
+    if (rc != TFHE_OK) return rc;
+    {
+        StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
+        k_tc_windows<<<dim3((unsigned)npoly, T), 256, 0, st>>>(sel, p.N, s, T, V.d_terms, w->cm_win,
+                                                              ppk, g.sy * ppk);
+        ta.stop();
+        rc = tfhe_check_launch(ctx, "tc cmux windows");
+        if (rc != TFHE_OK) return rc;
+    }
+    BrArgs args;
+    rc = persistent_args(ctx, (int)(tiles * TILE_M), 1, level, w->cm_win, args);
+    if (rc != TFHE_OK) return rc;
+    args.cmux = 1;
+    args.tpg = tpg;
+    args.cm_d1 = g.d1;
+    args.cm_d0 = g.d0;
+    args.cm_dx = g.dx;
+    args.cm_dy = g.dy;
+    args.cm_nx = g.nx;
+    args.cm_count = g.count;
+    rc = launch_persistent(ctx, args, level, st);
+    if (rc != TFHE_OK) return rc;
+    StageTimer ta(ctx, TFHE_STAGE_TC_AUX, st);
+    k_tc_untile_cmux<<<dim3((unsigned)(p.N / 32), (unsigned)(4 * tiles), 2), dim3(32, 8), 0, st>>>(
+        p.N, tpg, g.nx, g.count, g.ox, g.oy, w->acc_t, g.out);
+    ta.stop();
+    return tfhe_check_launch(ctx, "tc cmux outputs");
 }
 
 int tfhe_tc_set_variant(tfhe_ctx *ctx, int variant) {
@@ -1736,11 +1870,4 @@ int tfhe_tc_variant(tfhe_ctx *ctx) {
     return use_pair(ctx) ? TFHE_TC_SM_PAIR : TFHE_TC_SINGLE_SM;
 }
 
-int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *, const CmuxGeom &, cudaStream_t) {
-    return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core CMUX not built yet");
-}
 
-int tfhe_ram_write_tc(tfhe_ctx *ctx, const uint32_t *, const uint32_t *, int, const uint32_t *,
-                      uint32_t *, cudaStream_t) {
-    return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "tensor-core RAM write not built yet");
-}

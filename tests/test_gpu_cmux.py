@@ -8,7 +8,7 @@ from conftest import from_dev, gpu_context, to_dev
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [0, 2]
+FORMS = [0, 2, 1]  # form 1 (tensor cores) covers groups of >= 128 CMUXes per selector
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -77,6 +77,44 @@ def test_cmux_tree_read_512_rows_64_reads(torch_cuda, form):
     assert len(want) == 8
     for r, w in want.items():
         assert np.array_equal(got[r], w), r
+
+
+@pytest.mark.parametrize("B,group", [(256, 128), (300, 150), (700, 700)])
+def test_cmux_batch_tensor_cores_toy(torch_cuda, B, group):
+    """Tensor-core CMUX batches: one or several 128-CMUX tiles per selector, with ragged
+    groups (150 = 128 + 22 padding rows; 700 over six tiles), every CMUX word for word
+    against the oracle and the NTT form."""
+    p = ti.TOY
+    ctx, k = gpu_context(p, ti.SEED_TOY)
+    rng = np.random.default_rng(B + group)
+    ny = (B + group - 1) // group
+    sel = ti.encrypt_trgsw_bits(p, 7, 3, k.s1, rng.integers(0, 2, ny).astype(np.uint8))
+    d1 = rng.integers(0, 2**32, (B, 2, p.N), dtype=np.uint64).astype(np.uint32)
+    d0 = rng.integers(0, 2**32, (B, 2, p.N), dtype=np.uint64).astype(np.uint32)
+    outs = {}
+    for form in (1, 2):
+        out = to_dev(np.zeros_like(d0))
+        ctx.cmux_batch(to_dev(sel), group, to_dev(d1), to_dev(d0), out, form=form)
+        ctx.sync()
+        outs[form] = from_dev(out)
+    assert np.array_equal(outs[1], outs[2])
+    for q in range(B):
+        assert np.array_equal(outs[1][q], orc.cmux(p, sel[q // group], d1[q], d0[q])), q
+
+
+def test_cmux_tree_read_tensor_cores_toy(torch_cuda):
+    """A 256-row toy table (8 address bits): tree level 0 has 128 CMUXes per read and runs
+    on the tensor cores, the other levels in the NTT form; both reads word for word."""
+    p = ti.TOY
+    rom = ti.cmux_rom(p, ti.SEED_TOY, v=8, R=2, packed=32)
+    ctx, k = gpu_context(p, ti.SEED_TOY)
+    out = to_dev(np.zeros((2, 2, p.N), np.uint32))
+    ctx.cmux_tree_read(to_dev(rom.addr_trgsw), to_dev(rom.table), 8, out, form=1)
+    ctx.sync()
+    got = from_dev(out)
+    for r in range(2):
+        assert np.array_equal(got[r], orc.cmux_tree_read(p, rom.addr_trgsw[r], rom.table, 8)), r
+        assert np.array_equal(orc.trlwe_decrypt(k.s1, got[r])[:32], rom.table_bits[rom.addrs[r], :32])
 
 
 @pytest.mark.parametrize("form", FORMS)
