@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;
     uint32_t *d_rows = (uint32_t *)(b_st + STAGES * BST);  // [8][N + 4]
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], pfull[STAGES];
-    __shared__ __align__(8) uint64_t acc_full, acc_empty[PLANES], drain;
+    __shared__ __align__(8) uint64_t acc_full[PLANES], acc_empty[PLANES], drain;
     __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
     __shared__ int jobs[JQ];
     __shared__ int job_passes[JQ];  // set by the loader before the job's first stage is full
@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             mbar_init(&empty[q], 1);
             mbar_init(&pfull[q], 1);  // pair form: the odd CTA's stage q is full
         }
-        mbar_init(&acc_full, 1);
+        for (int p = 0; p < PLANES; p++) mbar_init(&acc_full[p], 1);
         // one arrival per read-out warp (of both CTAs in the pair form)
         for (int p = 0; p < PLANES; p++) mbar_init(&acc_empty[p], (PAIR ? 2 : 1) * EPI_WARPS);
         mbar_init(&drain, 1);
@@ -916,25 +916,33 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     // to the start-address field (shared addresses < 256 KB: no carry)
                     const uint64_t a_desc = make_desc(smem_u32(a_st + st * A_STAGE_BYTES), 128, 2048);
                     const uint64_t b_desc = make_desc(smem_u32(b_st + st * BST), 128, 128);
-                    if (ts % pass_stages == 0) {
-                        // first stage of a pass: plane p starts once its previous contents
-                        // have been read out
+                    const bool first = ts % pass_stages == 0, last = (ts + 1) % pass_stages == 0;
+                    if (first || last) {
+                        // first and last stage of a pass go plane by plane: in the first,
+                        // plane p starts once its previous contents have been read out; in the
+                        // last, plane p is committed on its own (acc_full[p]), so its read-out
+                        // (and the next job's MMAs on it) overlap the later planes' MMAs
 #pragma unroll
                         for (int p = 0; p < PLANES; p++) {
-                            if (khalf > 0 &&
+                            if (first && khalf > 0 &&
                                 !mbar_wait<PAIR>(&acc_empty[p], (khalf - 1) & 1, abort, err)) {
                                 ok = false;
                                 break;
                             }
-                            tc_fence_after();
+                            if (first) tc_fence_after();
 #pragma unroll
                             for (int kk = 0; kk < KS / 16; kk++) {
                                 const uint64_t ad = a_desc + (uint64_t)(kk * 256 / 16);
                                 const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
+                                const uint32_t accum = (first && kk == 0) ? 0u : 1u;
                                 if constexpr (PAIR)
-                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, kk == 0 ? 0u : 1u);
+                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, accum);
                                 else
-                                    mma_bf16(tmem + p * NB, ad, bd, idesc, kk == 0 ? 0u : 1u);
+                                    mma_bf16(tmem + p * NB, ad, bd, idesc, accum);
+                            }
+                            if (last) {
+                                if constexpr (PAIR) mma_commit_pair_both(&acc_full[p]);
+                                else mma_commit(&acc_full[p]);
                             }
                         }
                         if (!ok) break;
@@ -960,11 +968,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     }
                     if constexpr (PAIR) mma_commit_pair_both(&empty[st]);
                     else mma_commit(&empty[st]);
-                    if ((ts + 1) % pass_stages == 0) {
-                        if constexpr (PAIR) mma_commit_pair_both(&acc_full);
-                        else mma_commit(&acc_full);
-                        khalf++;
-                    }
+                    if (last) khalf++;
                 }
             }
             if constexpr (PAIR) mma_commit_pair_own(&drain);
@@ -1020,13 +1024,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             for (int e = 0; e < EPI_COLS; e++) sum[e] = sum_init;
             bool ok = true;
             for (int h = 0; h < passes && ok; h++, khalf++) {
-                if (!mbar_wait_warp<PAIR>(&acc_full, khalf & 1, abort, err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
 #pragma unroll
                 for (int p = 0; p < PLANES; p++) {
+                    // plane p of this pass is complete once its own commit has arrived
+                    if (!mbar_wait_warp<PAIR>(&acc_full[p], khalf & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     // exact fp32 -> int: for |x| < 2^22 the sum x + 1.5*2^23 is exact and its
                     // bit pattern is RO_MAGIC_BITS + x; the constant is removed once through
                     // the initial value of sum.  A slice holding a larger |x| (possible, never
