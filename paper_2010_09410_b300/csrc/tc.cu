@@ -624,6 +624,10 @@ constexpr uint32_t RO_MAGIC_PER_PASS =
 // rows each, for which the worst case l * s * (32 * 2^L) * 128 <= 2^24.
 constexpr int ONE_PASS_LIMIT = 1 << 17;  // default and largest allowed limit
 constexpr int JQ = 8;       // job ring depth
+// Fewest product jobs per step of a tile chunk, in waves of the SMs: 32 tiles at
+// Karatsuba level 2 (36 jobs per tile and step) make two chunks of 16 on 148 SMs.  Smaller
+// chunks were slower on B300 (3.2 waves: +17 %), as were uneven ones.
+constexpr double CHUNK_WAVES = 3.8;
 constexpr int DPARTS = 16;  // digit parts per gate tile (8 gates each)
 
 enum { JOB_STOP = 0, JOB_D = 1, JOB_E = 2, JOB_NOP = 3 };
@@ -678,6 +682,11 @@ struct BrArgs {
     int e_per_tile;             // product jobs per tile and step
     int step_len;               // entries of the per-step product-job table
     long long total_e, total_d;
+    // Tiles are processed in nchunks chunks of job-table units (tiles, or tile pairs) of
+    // nearly equal size (the first units % nchunks chunks hold one unit more): both job
+    // streams run all steps of one chunk before the next, so a step's digit blocks and
+    // accumulators of the chunk stay in L2.  units: table units in all.
+    int units, nchunks;
     const uint32_t *table;      // per-step job table
     const KTerm *terms;
     const uint32_t *bar;        // [G][n+1] ModSwitched combinations (written at step 0 when fused)
@@ -707,12 +716,37 @@ struct BrArgs {
     int *err;
 };
 
+// Chunk of stream entry `job` when `units` units are split into `nchunks` chunks of
+// nearly equal size (the first units % nchunks one larger) and each unit contributes
+// per_unit entries per chunk pass: the chunk's first unit u0, its size uc, and the
+// entry's offset rem within the chunk.
+__device__ __forceinline__ void chunk_of(long long job, int units, int nchunks, long long per_unit,
+                                         int *u0, int *uc, long long *rem) {
+    const int base = units / nchunks, extra = units % nchunks;
+    const long long big = (long long)extra * (base + 1) * per_unit;  // entries of the larger chunks
+    int c;
+    if (job < big) {
+        c = (int)(job / ((base + 1) * per_unit));
+        *rem = job - (long long)c * (base + 1) * per_unit;
+    } else {
+        c = extra + (int)((job - big) / (base * per_unit));
+        *rem = job - big - (long long)(c - extra) * base * per_unit;
+    }
+    *u0 = c * base + min(c, extra);
+    *uc = base + (c < extra ? 1 : 0);
+}
+
 __device__ __forceinline__ Job decode_e(const BrArgs &a, int job) {
     Job J{JOB_STOP, 0, 0, 0, 0, 0};
     if (job < 0) return J;
-    const uint32_t e = __ldg(a.table + job % a.step_len);
+    // the table lists every unit's e_per_tile entries in unit order
+    int u0, uc;
+    long long rem;
+    chunk_of(job, a.units, a.nchunks, (long long)a.n * a.e_per_tile, &u0, &uc, &rem);
+    const int len_c = uc * a.e_per_tile;
+    const uint32_t e = __ldg(a.table + (long long)u0 * a.e_per_tile + rem % len_c);
     J.kind = JOB_E;
-    J.i = job / a.step_len;
+    J.i = (int)(rem / len_c);
     J.gt = (int)((e >> 2) & 0xFFF);
     J.j = (int)((e >> 14) & 0x1F);
     J.c = (int)((e >> 19) & 1);
@@ -1119,16 +1153,21 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             const int job = d_job;
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (job < 0 || *abort) break;
-            const int i = job / (a.tiles * DPARTS);
-            int gt, mg;
+            int i, gt, mg;
             {
-                const int r = job % (a.tiles * DPARTS);
+                // chunks of the digit stream follow those of the product stream (the pair
+                // form runs one chunk: all tiles)
+                int t0, tiles_c;
+                long long rem;
+                chunk_of(job, a.tiles, PAIR ? 1 : a.nchunks, (long long)a.n * DPARTS, &t0, &tiles_c, &rem);
+                i = (int)(rem / (tiles_c * DPARTS));
+                const int r = (int)(rem % (tiles_c * DPARTS));
                 const int paired = PAIR ? (a.tiles / 2) * 2 * DPARTS : 0;
                 if (r < paired) {  // pair form: the two tiles of a pair alternate parts
                     gt = 2 * (r / (2 * DPARTS)) + (r & 1);
                     mg = (r % (2 * DPARTS)) >> 1;
                 } else {
-                    gt = (paired / DPARTS) + (r - paired) / DPARTS;
+                    gt = t0 + (paired / DPARTS) + (r - paired) / DPARTS;
                     mg = (r - paired) % DPARTS;
                 }
             }
@@ -1697,6 +1736,13 @@ static int persistent_args(tfhe_ctx *ctx, int G, int steps, int level, const uin
     args.step_len = table->len;
     args.total_e = (long long)steps * table->len;
     args.total_d = (long long)steps * tiles * DPARTS;
+    // as many equal chunks as keep at least CHUNK_WAVES waves of product jobs per step in
+    // each (one SM per tile); the pair form keeps all tiles in one chunk
+    args.units = pair ? (tiles + 1) / 2 : tiles;
+    {
+        const int min_units = (int)ceil(CHUNK_WAVES * w->sms / args.e_per_tile);
+        args.nchunks = pair ? 1 : std::max(1, args.units / std::max(1, min_units));
+    }
     args.table = table->d;
     args.terms = V.d_terms;
     args.ms_shift = 32 - (ctx->logN + 1);
