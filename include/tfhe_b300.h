@@ -213,7 +213,7 @@ int tfhe_ctx_stage_times(tfhe_ctx *ctx, double *ms, int64_t *launches);
  * out:     device u32[G][n+1]; must not overlap rows of `in` read by this call
  * form:    TFHE_FORM_NTT, TFHE_FORM_TC, TFHE_FORM_NTT2, or -1 for the form (and Karatsuba
  *          level) chosen for the batch width: tfhe_ctx_autotune's table when present, else
- *          the level scheduler's fixed rule (the two-prime form below about 1,800 gates)
+ *          the level scheduler's fixed rule (the two-prime form below about 1,280 gates)
  * Each gate: linear combination, ModSwitch to Z_2N, BlindRotate of the test vector
  * (n CMUXes against BSK), SampleExtract, identity key switch. */
 int tfhe_gate_batch(tfhe_ctx *ctx, const uint32_t *in, int64_t num_in, const uint8_t *types,

@@ -54,12 +54,11 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
 // Form and Karatsuba level for a level of `width` gates when the caller lets the plan
 // choose (form = -1).  After tfhe_ctx_autotune: the measured winner at the nearest tuned
 // width (log scale).  Before: a rule from a B300 sweep at N = 1024, n = 630 (ms per
-// level; NTT / two-prime NTT / tensor core L1 / L2): 64 gates 18.8 / 10.2 / 41.6 / 38.7;
-// 256: 34.0 / 16.7 / 44.8 / 44.8; 768: 94.6 / 44.7 / 46.6 / 49.7; 1024: 110 / 51.8 /
-// 48.8 / 52.1; 2048: 216 / 101 / 71.0 / 67.6; 4096: 428 / 200 / 137 / 120.  So the
-// two-prime per-gate form up to about 1,800 gates, Karatsuba level 1 to about 2,000,
-// level 2 beyond (the per-gate NTT form over 2^64 - 2^32 + 1 when the two-prime form
-// is not available: up to about 400 gates).
+// level; two-prime per-gate NTT / tensor core L1 / L2): 512 gates 21.1 / 43.9 / 37.1;
+// 1024: 35.0 / 45.9 / 39.9; 1280: 44.2 / 47.0 / 43.7; 1536: 53.5 / 50.1 / 46.2;
+// 2048: 67.4 / 63.2 / 56.3.  So the two-prime per-gate form below 1,280 gates and the
+// tensor cores at the context's Karatsuba level from there (the per-gate NTT form over
+// 2^64 - 2^32 + 1 when the two-prime form is not available: up to about 400 gates).
 void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
     *level = -1;
     const int ntt = ctx->bsk_ntt2 ? TFHE_FORM_NTT2 : TFHE_FORM_NTT;  // the faster per-gate form
@@ -81,13 +80,12 @@ void tfhe_pick_form(tfhe_ctx *ctx, int64_t width, int *form, int *level) {
         *level = best->level;
         return;
     }
-    if (width < (ctx->bsk_ntt2 ? 1792 : 384)) {
+    if (width < (ctx->bsk_ntt2 ? 1280 : 384)) {
         *form = ntt;
         return;
     }
     *form = TFHE_FORM_TC;
-    const int L = tfhe_tc_level(ctx);
-    *level = (width < 2048 && L > 1) ? 1 : L;
+    *level = tfhe_tc_level(ctx);
 }
 
 // Size the context's workspaces for every level of the plan (a later call of another
