@@ -375,9 +375,10 @@ def peaks():
 # kernel source is byte-identical to the one captured (else reported as null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-    #   --clock-control none -k regex:k_tc_blind_rotate -s 2 -c 1
-    #   python bench.py --steps 1 --warmup 3 --no-cpu-baseline --form tc
-    "k_tc_blind_rotate<2>": {"bytes": 99.14e9 + 102.56e9, "source_sha256": "6f3986cf9f300142e068be80bdd04c5b9713f948d378bb8a8877deb7ae890f6c"},
+    #   --clock-control none -k regex:"k_tc_blind_rotate|k_extract_keyswitch_staged" -s 2 -c 2
+    #   python bench.py --form tc --steps 1 --warmup 3 --no-cpu-baseline
+    "k_tc_blind_rotate<2>": {"bytes": 11.617e9 + 42.776e9, "source_sha256": "34205e12f1e5a9df10acacf33a8eafdef4cc79c625da4887286eab6ee7e16c2c"},
+    "k_extract_keyswitch_staged": {"bytes": 79.324e6 + 1.273e6, "source_sha256": "72c94a6c879ea426c95cac355d8881772d54492a707151e3b2374c521ecb4774"},
 }
 
 

@@ -1174,6 +1174,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * i), abort, err);
             asm volatile("bar.sync 2, 128;" ::: "memory");
             if (*abort) break;
+            if (i > 0 && !a.cmux) {
+                // Every product job of the tile's step i-1 has copied its digit stages, so
+                // the part's digit lines of that step are dead until this job rewrites
+                // them: drop them from L2 without writing them back (2 KB per block: the
+                // part's 8 gates of each 32 KB stage block, 16 lines of 128 bytes).
+                const int nblk = NT * 2 * l * kstages;
+                for (int q = tid; q < nblk * 16; q += 128) {
+                    const uint4 *ln = a.digits + (size_t)(gt * nblk + q / 16) * (A_STAGE_BYTES / 16) +
+                                      (size_t)mg * 128 + (q % 16) * 8;
+                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(ln) : "memory");
+                }
+            }
             // One accumulator polynomial of the part's 8 gates at a time: the rows are copied
             // into shared memory, then thread (m8 = tid & 7, kb = tid >> 3) digitises
             // positions kp = kc*KS + 8 kb .. + 7 of every size-s block of gate m8, so 8
