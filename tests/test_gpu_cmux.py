@@ -79,11 +79,11 @@ def test_cmux_tree_read_512_rows_64_reads(torch_cuda, form):
         assert np.array_equal(got[r], w), r
 
 
-@pytest.mark.parametrize("B,group", [(256, 128), (300, 150), (700, 700)])
+@pytest.mark.parametrize("B,group", [(256, 128), (300, 150), (700, 700), (350, 150)])
 def test_cmux_batch_tensor_cores_toy(torch_cuda, B, group):
     """Tensor-core CMUX batches: one or several 128-CMUX tiles per selector, with ragged
-    groups (150 = 128 + 22 padding rows; 700 over six tiles), every CMUX word for word
-    against the oracle and the NTT form."""
+    groups (150 = 128 + 22 padding rows; 700 over six tiles; 350 = two groups of 150 and
+    a last group of 50), every CMUX word for word against the oracle and the NTT form."""
     p = ti.TOY
     ctx, k = gpu_context(p, ti.SEED_TOY)
     rng = np.random.default_rng(B + group)
