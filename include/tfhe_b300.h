@@ -79,9 +79,10 @@ enum {
  *   TFHE_FORM_TC: the gates of a batch share each BSK_i, so one BlindRotate step
  *     over B gates is a dense [B x 2lN] x [2lN x 2N] contraction of signed digits
  *     by negacyclic Toeplitz blocks of the key, run on the tcgen05 tensor cores
- *     with the key split into byte planes (exact in bf16, fp32 accumulation kept
- *     below 2^24, recombined mod 2^32).  Needs N = 1024 and 2l * Bgbit fitting the
- *     exactness budget; otherwise the call returns TFHE_EUNSUPPORTED. */
+ *     with the key split into byte planes (exact in fp16, fp32 accumulation kept
+ *     below 2^24, recombined mod 2^32).  Needs 256 <= N <= 1024, Bgbit <= 6 and
+ *     l N 32 128 <= 2^24 (the exactness budget of a pass); otherwise the call returns
+ *     TFHE_EUNSUPPORTED. */
 enum { TFHE_FORM_NTT = 0, TFHE_FORM_TC = 1, TFHE_FORM_NTT2 = 2 };
 /*   TFHE_FORM_NTT2: one thread block per gate like TFHE_FORM_NTT, with each external
  *     product computed by NTTs modulo the two 30-bit primes 998244353 and 754974721 in

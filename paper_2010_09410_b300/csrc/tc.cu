@@ -17,8 +17,10 @@
 // y0 = P + (T01 - T00) x1, y1 = P + (T10 - T00) x0).  After L levels a step is 3^L
 // Toeplitz products of size s = N / 2^L, each with a signed combination of digit blocks
 // (|x| <= 32 * 2^L), a key generator that is a signed sum of shifted key segments, and
-// signed output blocks; the host builds this plan (build_plan).  Every accumulation
-// then sums l*s terms below 32 * 2^L * 128 = l*N*32*128 <= 2^24, so it stays exact.
+// signed output blocks; the host builds this plan (build_plan).  An accumulation over l
+// rows sums l*s terms below 32 * 2^L * 128, at most l*N*32*128 <= 2^24, so it stays
+// exact; a job's 2l rows go in one pass when the digit jobs' bound allows it (see
+// ONE_PASS_LIMIT).
 //
 // The Toeplitz operand is never materialised.  Row n' of a size-s Toeplitz matrix with
 // generator t (T[n'][k'] = t[n'-k']) is the window r_vec[s-1-n'+k'] of
@@ -36,8 +38,9 @@
 // [tile][term j][row r < 2l][stage < s/KS] blocks of 32 KB, each [mg < 16][kb < 16]
 // [m8 < 8][8 fp16] for gate m = 8 mg + m8 and digit index k' = stage*KS + 8 kb + e.
 // The accumulators live gate-fastest within tiles ([tile][c][word][128 gates]) while the
-// BlindRotate runs, so the read-out warps' read-modify-writes and the digit jobs' loads
-// are whole 128-byte lines; the caller's [G][2][N] layout is written at the end.
+// BlindRotate runs, so the read-out warps' L2 reductions and the digit jobs' loads are
+// whole 128-byte lines; the gate path's key switch reads them in that layout, other
+// callers get [G][2][N] from a re-layout launch.
 // One launch of k_tc_blind_rotate runs all n steps.  Every wait polls a bounded number
 // of times; on time-out the block records TFHE_ETIMEOUT in the context's error word and
 // winds down.
@@ -223,7 +226,7 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -236,7 +239,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 // collector (fill), the next two reuse it (use) and the last reuses and releases it
 // (lastuse).  COLL: 0 fill, 1 use, 2 lastuse.  Cuts the A reads from shared memory 4x.
 template <int COLL>
-__device__ __forceinline__ void mma_bf16_coll(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16_coll(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                               uint32_t idesc) {
     if constexpr (COLL == 0)
         asm volatile(
@@ -259,7 +262,7 @@ __device__ __forceinline__ void mma_bf16_coll(uint32_t d_tmem, uint64_t adesc, u
 // B columns 0 .. N/2-1 come from its own shared memory and A rows 128-255 and B columns
 // N/2 .. N-1 from the odd CTA's (same offsets); rows 0-127 of D go to the even CTA's
 // TMEM, rows 128-255 to the odd CTA's.
-__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                               uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -970,9 +973,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                 const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
                                 const uint32_t accum = (first && kk == 0) ? 0u : 1u;
                                 if constexpr (PAIR)
-                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, accum);
+                                    mma_f16_pair(tmem + p * NB, ad, bd, idesc, accum);
                                 else
-                                    mma_bf16(tmem + p * NB, ad, bd, idesc, accum);
+                                    mma_f16(tmem + p * NB, ad, bd, idesc, accum);
                             }
                             if (last) {
                                 if constexpr (PAIR) mma_commit_pair_both(&acc_full[p]);
@@ -988,15 +991,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
 #pragma unroll
                                 for (int p = 0; p < PLANES; p++) {
                                     const uint64_t bd = b_desc + (uint64_t)((p * BPL + kk * 256) / 16);
-                                    mma_bf16_pair(tmem + p * NB, ad, bd, idesc, 1u);
+                                    mma_f16_pair(tmem + p * NB, ad, bd, idesc, 1u);
                                 }
                             } else {
                                 static_assert(PLANES == 4, "collector sequence assumes 4 planes");
                                 const uint64_t bd = b_desc + (uint64_t)(kk * 256 / 16);
-                                mma_bf16_coll<0>(tmem, ad, bd, idesc);
-                                mma_bf16_coll<1>(tmem + NB, ad, bd + BPL / 16, idesc);
-                                mma_bf16_coll<1>(tmem + 2 * NB, ad, bd + 2 * BPL / 16, idesc);
-                                mma_bf16_coll<2>(tmem + 3 * NB, ad, bd + 3 * BPL / 16, idesc);
+                                mma_f16_coll<0>(tmem, ad, bd, idesc);
+                                mma_f16_coll<1>(tmem + NB, ad, bd + BPL / 16, idesc);
+                                mma_f16_coll<1>(tmem + 2 * NB, ad, bd + 2 * BPL / 16, idesc);
+                                mma_f16_coll<2>(tmem + 3 * NB, ad, bd + 3 * BPL / 16, idesc);
                             }
                         }
                     }
