@@ -77,9 +77,9 @@ constexpr int PB_PLANE_BYTES = PB_UNITS * 16;              // 3 KB
 constexpr int PB_STAGE_BYTES = PLANES * PB_PLANE_BYTES;    // 12 KB
 __host__ __device__ constexpr int b_plane_bytes(bool pair) { return pair ? PB_PLANE_BYTES : B_PLANE_BYTES; }
 __host__ __device__ constexpr int b_stage_bytes(bool pair) { return pair ? PB_STAGE_BYTES : B_STAGE_BYTES; }
-// stages + digit staging (one accumulator polynomial of 8 gates, rows padded by 4 words)
+// stages + digit staging (one accumulator polynomial of 8 gates, rows padded by 12 words)
 __host__ __device__ constexpr int smem_bytes(int N, bool pair) {
-    return STAGES * (A_STAGE_BYTES + b_stage_bytes(pair)) + 8 * (N + 4) * 4;
+    return STAGES * (A_STAGE_BYTES + b_stage_bytes(pair)) + 8 * (N + 12) * 4;
 }
 constexpr long long WAIT_CYCLES = 4000000000LL;           // ~2 s at 2 GHz
 
@@ -370,86 +370,124 @@ __host__ __device__ constexpr int out_coef_tab(int L, int j, int b) {
     return L == 0 ? t0[j][b] : (L == 1 ? t1[j][b] : (L == 2 ? t2[j][b] : t3[j][b]));
 }
 
-// Two small integers (|x| < 512) as packed fp16: the 16-bit field x + 0x6600 is the fp16
-// pattern of 1536 + x (exponent 10: unit spacing on [1024, 2048)), and both fields stay in
-// [0, 2^16), so one integer sum builds the pair and one packed subtraction of 1536
-// leaves x0 and x1 exactly.
-__device__ __forceinline__ uint32_t pack_f16x2(int x0, int x1) {
-    const uint32_t v = (uint32_t)x0 + ((uint32_t)x1 << 16) + 0x66006600u;
+// Packed fp16 pairs of small integers: sums and differences stay exact while every value
+// stays within |x| <= 2048 (11-bit significand); the digits and their Karatsuba
+// combinations are at most 2^L * Bg/2 <= 256 in magnitude.
+__device__ __forceinline__ uint32_t hadd2(uint32_t x, uint32_t y) {
     uint32_t r;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0x66006600u));
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(y));
     return r;
 }
+__device__ __forceinline__ uint32_t hsub2(uint32_t x, uint32_t y) {
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(y));
+    return r;
+}
+__device__ __forceinline__ uint32_t habs2(uint32_t x) { return x & 0x7FFF7FFFu; }
+// sum of the two halves of a packed pair of integers in [0, 512): 1536 + x has the fp16
+// pattern 0x6600 + x
+__device__ __forceinline__ int fold_f16_sums(uint32_t x) {
+    const uint32_t v = hadd2(x, 0x66006600u);
+    return (int)(v & 0xFFFFu) + (int)(v >> 16) - 2 * 0x6600;
+}
 
-// The 3^L Karatsuba digit combinations of a set of E positions, v[b][e] the digit of
-// position e in size-s block b of the polynomial, built as the plan's tree (negacyclic
-// split: x0, x1 - x0, x0 + x1; then per Toeplitz split: x0 + x1, x1, x0) instead of one
-// dense sum per term: 23 additions per position at L = 3 instead of 80.  emit(j, x)
-// receives term j (a std::integral_constant, build_plan's order) and its E values.
+// Gadget digits of two offset values as one packed fp16 pair: the Bgbit-wide fields at bit
+// `sh` (raw in [0, Bg)) are placed under the fp16 pattern 0x6600 (the value 1536 + raw:
+// exponent 10 gives unit spacing on [1024, 2048)), and one packed subtraction of
+// dsub = 1536 + Bg/2 in both halves leaves raw - Bg/2, the signed digit.  Bg <= 512.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t u0, uint32_t u1, int sh, uint32_t fmask,
+                                               uint32_t dsub) {
+    const uint32_t t = __byte_perm(u0 >> sh, u1 >> sh, 0x5410);  // low halves of both
+    return hsub2((t & fmask) | 0x66006600u, dsub);
+}
+
+// The 3^L Karatsuba digit combinations of 8 positions, v[b][w] the packed digits of
+// positions 2w, 2w+1 in size-s block b of the polynomial, built as the plan's tree
+// (negacyclic split: x0, x1 - x0, x0 + x1; then per Toeplitz split: x0 + x1, x1, x0)
+// instead of one dense sum per term: 23 additions per position at L = 3 instead of 80.
+// emit(j, x) receives term j (a std::integral_constant, build_plan's order) and its 4
+// packed words.
 __host__ __device__ constexpr int pow3(int k) { return k == 0 ? 1 : 3 * pow3(k - 1); }
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+constexpr int DW = 4;  // packed words per thread and block (8 positions)
 
-template <int M, int J0, int E, typename F>
-__device__ __forceinline__ void kara_split(const int (&v)[M][E], F &emit) {
+template <int M, int J0, typename F>
+__device__ __forceinline__ void kara_split(const uint32_t (&v)[M][DW], F &emit) {
     if constexpr (M == 1) {
         emit(std::integral_constant<int, J0>(), v[0]);
     } else {
         constexpr int H = M / 2, SUB = pow3(ilog2c(H));
-        int sa[H][E], s1[H][E], s0[H][E];
+        uint32_t sa[H][DW], s1[H][DW], s0[H][DW];
 #pragma unroll
         for (int h = 0; h < H; h++)
 #pragma unroll
-            for (int e = 0; e < E; e++) {
-                sa[h][e] = v[h][e] + v[H + h][e];
-                s1[h][e] = v[H + h][e];
-                s0[h][e] = v[h][e];
+            for (int w = 0; w < DW; w++) {
+                sa[h][w] = hadd2(v[h][w], v[H + h][w]);
+                s1[h][w] = v[H + h][w];
+                s0[h][w] = v[h][w];
             }
-        kara_split<H, J0, E>(sa, emit);
-        kara_split<H, J0 + SUB, E>(s1, emit);
-        kara_split<H, J0 + 2 * SUB, E>(s0, emit);
+        kara_split<H, J0>(sa, emit);
+        kara_split<H, J0 + SUB>(s1, emit);
+        kara_split<H, J0 + 2 * SUB>(s0, emit);
     }
 }
 
-template <int M, int E, typename F>
-__device__ __forceinline__ void kara_terms(const int (&v)[M][E], F &emit) {
+template <int M, typename F>
+__device__ __forceinline__ void kara_terms(const uint32_t (&v)[M][DW], F &emit) {
     if constexpr (M == 1) {
         emit(std::integral_constant<int, 0>(), v[0]);
     } else {
         constexpr int H = M / 2, SUB = pow3(ilog2c(H));
-        int p1[H][E], p2[H][E], p3[H][E];
+        uint32_t p1[H][DW], p2[H][DW], p3[H][DW];
 #pragma unroll
         for (int h = 0; h < H; h++)
 #pragma unroll
-            for (int e = 0; e < E; e++) {
-                p1[h][e] = v[h][e];
-                p2[h][e] = v[H + h][e] - v[h][e];
-                p3[h][e] = v[h][e] + v[H + h][e];
+            for (int w = 0; w < DW; w++) {
+                p1[h][w] = v[h][w];
+                p2[h][w] = hsub2(v[H + h][w], v[h][w]);
+                p3[h][w] = hadd2(v[h][w], v[H + h][w]);
             }
-        kara_split<H, 0, E>(p1, emit);
-        kara_split<H, SUB, E>(p2, emit);
-        kara_split<H, 2 * SUB, E>(p3, emit);
+        kara_split<H, 0>(p1, emit);
+        kara_split<H, SUB>(p2, emit);
+        kara_split<H, 2 * SUB>(p3, emit);
     }
 }
 
-// Stores term j's E digit combinations of one thread as packed fp16 into the A-operand
-// layout: unit u = base + j * term_stride (16 bytes, 8 positions; E = 4 fills half eh).
-template <int E>
+// Stores term j's 8 combinations of one thread (16 bytes) into the A-operand layout: the
+// digit blocks of the terms of one (tile, row, stage) are consecutive, so term j's unit is
+// j blocks after term 0's (a constant offset).
 struct DigitStore {
-    uint4 *digits;
-    size_t base, term_stride;
-    int eh;
+    uint4 *p;  // the thread's unit in term 0's block
     template <int j>
-    __device__ __forceinline__ void operator()(std::integral_constant<int, j>, const int (&x)[E]) const {
-        uint32_t wv[E / 2];
-#pragma unroll
-        for (int e = 0; e < E; e += 2) wv[e / 2] = pack_f16x2(x[e], x[e + 1]);
-        const size_t u = base + (size_t)j * term_stride;
-        if constexpr (E == 8)
-            digits[u] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-        else
-            reinterpret_cast<uint2 *>(digits)[2 * u + eh] = make_uint2(wv[0], wv[1]);
+    __device__ __forceinline__ void operator()(std::integral_constant<int, j>, const uint32_t (&x)[DW]) const {
+        p[(size_t)j * (A_STAGE_BYTES / 16)] = make_uint4(x[0], x[1], x[2], x[3]);
     }
 };
+
+// u[e] = (X^rot p - p)[k0 + e] + off for the 8 positions k0 .. k0+7 (k0 a multiple of 8)
+// of the row p of one gate in shared memory: X^rot p at k is p[k - rk] for k >= rk and
+// -p[k - rk + N] below it, all negated once more when rot >= N (rneg all ones).  The row
+// holds -p[0..7] after its N words, so that positions crossing the wrap read the right
+// sign without a branch.  plain (CMUX mode, the row holds d1 - d0): u = p + off.
+__device__ __forceinline__ void rotated_diff8(const uint32_t *row, int N, int k0, int rk, uint32_t rneg,
+                                              uint32_t off, bool plain, uint32_t (&u)[8]) {
+    const uint4 o0 = *(const uint4 *)(row + k0), o1 = *(const uint4 *)(row + k0 + 4);
+    const uint32_t own[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+    if (plain) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) u[e] = own[e] + off;
+        return;
+    }
+    int src = k0 - rk;
+    uint32_t sg = rneg;
+    if (src < 0) {
+        src += N;
+        sg = ~rneg;
+    }
+    const uint32_t base = off - sg;  // (v ^ sg) - sg is v or -v
+#pragma unroll
+    for (int e = 0; e < 8; e++) u[e] = (row[src + e] ^ sg) + base - own[e];
+}
 
 // The same tree as coefficients (weight of input block b in term j), checked against
 // in_coef_tab at compile time.
@@ -593,22 +631,25 @@ __global__ void k_tc_untile_cmux(int N, int tpg, int nx, int64_t count, int64_t 
 //   D(i, gt, .) waits for done_E[gt] >= E_per_tile * i (ACC(i) is complete).
 // Every wait is bounded.
 //
-// Warp roles (448 threads): warps 0-7 read TMEM out (warp w owns lanes 32(w%4)..+31 and
+// Warp roles (512 threads): warps 0-7 read TMEM out (warp w owns lanes 32(w%4)..+31 and
 // columns 64(w/4)..+63 of the block), warp 8 owns TMEM and one lane issues the MMAs,
-// warp 12 fetches jobs and streams stages with cp.async.bulk, warps 9-11 and 13 compute
-// digits.  The four planes of TMEM are handed back one by one after each K-pass's
+// warp 12 fetches jobs and streams stages with cp.async.bulk, warps 9-11 and 13-15
+// compute digits.  The four planes of TMEM are handed back one by one after each K-pass's
 // read-out, so the next pass's MMAs on plane p start as soon as plane p has been read;
 // the passes of a job accumulate in registers and the product is added once.
 // ---------------------------------------------------------------------------
-constexpr int P_THREADS = 448;
+constexpr int P_THREADS = 512;
 constexpr int EPI_WARPS = 8;                 // read-out warps: 2 per TMEM lane quarter
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 // A warp issues on SM sub-partition (warp index mod 4).  The MMA-issuing warp shares its
 // sub-partition only with the loader and two read-out warps; the ALU-heavy digit warps
-// (9, 10, 11, 13) sit on the other three.
+// (9-11, 13-15) sit two each on the other three.  16 warps of 128 registers fill the
+// register file.
 constexpr int MMA_WARP = 8;                  // TMEM owner + MMA issue
 constexpr int LOAD_WARP = 12;                // job fetch + stage loads
-__device__ __forceinline__ int digit_warp_index(int warp) { return warp == 13 ? 3 : warp - 9; }
+__device__ __forceinline__ int digit_warp_index(int warp) { return warp < LOAD_WARP ? warp - 9 : warp - 10; }
+constexpr int DG_THREADS = 192;              // digit warps 9-11 and 13-15
+__device__ __forceinline__ void dg_sync() { asm volatile("bar.sync 2, %0;" ::"n"(DG_THREADS) : "memory"); }
 constexpr int EPI_COLS = NB / 2;             // columns per read-out warp
 // read-out conversion constants: 1.5*2^23 and its bit pattern; the initial sum cancels the
 // bit-pattern offset added by both K-halves of all four planes (mod 2^32)
@@ -711,7 +752,7 @@ struct BrArgs {
     int cm_nx;
     int64_t cm_count;
     uint32_t *acc;              // [tiles_pad][2][N][128] (gate-fastest within a tile)
-    uint4 *digits;              // [tiles][nterms][2l][s/KS] x 32 KB
+    uint4 *digits;              // [tiles][2l][s/KS][nterms] x 32 KB
     const uint4 *win;           // [n][2l][2][nterms][4][2s] units
     uint32_t *sync;             // [0] product-job counter, [1] digit-job counter,
                                 // then per padded tile: done_D, done_E, two_pass (the last
@@ -782,12 +823,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];  // no swizzle: 16-byte alignment suffices
     uint8_t *a_st = smem;
     uint8_t *b_st = smem + STAGES * A_STAGE_BYTES;
-    uint32_t *d_rows = (uint32_t *)(b_st + STAGES * BST);  // [8][N + 4]
+    uint32_t *d_rows = (uint32_t *)(b_st + STAGES * BST);  // [8][N + 12]
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], pfull[STAGES];
     __shared__ __align__(8) uint64_t acc_full[PLANES], acc_empty[PLANES], drain;
     __shared__ __align__(8) uint64_t job_full[JQ], job_empty[JQ];
     __shared__ int jobs[JQ];
     __shared__ int job_passes[JQ];  // set by the loader before the job's first stage is full
+    // one-SM form: the MMA thread hands the job's pass count to the read-out (ro_passes,
+    // published by an arrival on passes_ready), so the read-out needs no global round trip
+    __shared__ int ro_passes[JQ];
+    __shared__ __align__(8) uint64_t passes_ready[JQ];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int8_t out_tab[NT][NBLK];  // out_coef_tab of this level
@@ -821,6 +866,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // MMA lane, read-out leader; pair form also the odd CTA's loader, stage
             // forwarder and read-out leader
             mbar_init(&job_empty[q], PAIR ? 5 : 2);
+            mbar_init(&passes_ready[q], 1);
         }
         abort_flag = 0;
 #pragma unroll
@@ -905,7 +951,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         break;
                     }
                     const int r = ts / kstages, ks = ts % kstages;
-                    const size_t blk = (((size_t)gt * a.nterms + J.j) * 2 * l + r) * kstages + ks;
+                    const size_t blk = (((size_t)gt * 2 * l + r) * kstages + ks) * a.nterms + J.j;
                     mbar_arrive_tx(&full[st], A_STAGE_BYTES + BST);
                     bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
                              A_STAGE_BYTES, &full[st]);
@@ -947,6 +993,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     tc_fence_after();
                     if (ts == 0) {
                         if (job_passes[slot] == 2) pass_stages = half_stages;
+                        if constexpr (!PAIR) {
+                            ro_passes[slot] = job_passes[slot];
+                            mbar_arrive(&passes_ready[slot]);
+                        }
                         mbar_arrive(&job_empty[slot]);  // the slot is read
                     }
                     // descriptors of the stage; K-steps and planes add their byte offset / 16
@@ -1043,18 +1093,36 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             const int slot = q % JQ;
             if (!mbar_wait_warp<PAIR>(&job_full[slot], (q / JQ) & 1, abort, err)) break;
             const int job = jobs[slot];
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            if (tid == 0) {
-                if (rank == 0) mbar_arrive(&job_empty[slot]);
-                else mbar_arrive_remote(cluster_addr(&job_empty[slot], 0));
+            auto release_slot = [&]() {  // every read-out thread has read the slot
+                if (tid == 0) {
+                    if (rank == 0) mbar_arrive(&job_empty[slot]);
+                    else mbar_arrive_remote(cluster_addr(&job_empty[slot], 0));
+                }
+            };
+            if constexpr (PAIR) {
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                release_slot();
             }
-            if (job < 0) break;
+            if (job < 0) {
+                if constexpr (!PAIR) release_slot();
+                break;
+            }
             const Job J = decode_e(a, job);
             const int gt = PAIR ? 2 * J.gt + (int)rank : J.gt;  // this CTA's gate tile
             const int bcol = J.sub % bpp;
-            if (tid == 0) epi_passes = passes_for<PAIR>(a, J, done_D, two_pass);
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            const int passes = epi_passes;
+            int passes;
+            if constexpr (PAIR) {
+                if (tid == 0) epi_passes = passes_for<PAIR>(a, J, done_D, two_pass);
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+                passes = epi_passes;
+            } else {
+                // The leader's acquire orders this job's additions into ACC after the digit
+                // jobs of its step (the readers of ACC(i)); taken now, it overlaps the
+                // read-out of the planes (the barrier before the additions publishes it).
+                if (tid == 0 && gt < a.tiles) wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
+                if (!mbar_wait_warp<false>(&passes_ready[slot], (q / JQ) & 1, abort, err)) break;
+                passes = ro_passes[slot];
+            }
             uint32_t sum[EPI_COLS];
             const uint32_t sum_init = 0u - (uint32_t)passes * RO_MAGIC_PER_PASS;
 #pragma unroll
@@ -1108,9 +1176,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // added with sign out_tab[j][b] into output block b.  The leader's acquire
             // orders these additions after this step's digit jobs of the tile (the
             // readers of ACC(i)).
-            if (tid == 0 && gt < a.tiles)
+            if (PAIR && tid == 0 && gt < a.tiles)
                 wait_count(&done_D[gt], (uint32_t)(DPARTS * (J.i + 1)), abort, err);
             asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            if constexpr (!PAIR) release_slot();
             if (*abort) break;
             if (gt * TILE_M + gl < a.G) {
                 // this warp's columns idx = 64 colh + e map to words c0 - idx, i.e. the
@@ -1137,14 +1206,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             if (tid == 0 && gt < a.tiles) red_release_add(&done_E[gt], 1u);
         }
     } else {
-        // ---- warps 9-11 and 13: digit jobs ----
+        // ---- warps 9-11 and 13-15: digit jobs ----
         const int tid = digit_warp_index(warp) * 32 + lane;
         const uint32_t off = gadget_offset(l, a.Bgbit);
         // One-pass check (see ONE_PASS_LIMIT): sum |x| over a term's K is bounded by the
         // sum, over the term's input blocks, of sum |digit| per block (triangle
-        // inequality), so the digit jobs keep one counter per block.  Level 3 digitises 4
-        // positions per pass (registers), the others 8.
-        constexpr int E = L == 3 ? 4 : 8;
+        // inequality), so the digit jobs keep one counter per block.  Levels 0-2 hold a
+        // thread's rotated differences over the l digits; level 3 recomputes them per digit
+        // (registers).
+        constexpr bool HOLD = NBLK <= 4;
+        const int Bgbit = a.Bgbit;
+        const uint32_t fmask = ((1u << Bgbit) - 1u) * 0x10001u;
+        const uint32_t dsub = f16_bits(1536 + (1 << (Bgbit - 1))) * 0x10001u;
         __shared__ int d_job;
         __shared__ int d_abs[8 * NBLK];  // per gate of the part and input block
         for (;;) {
@@ -1152,9 +1225,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 const unsigned jn = atomicAdd(d_counter, 1u);
                 d_job = (long long)jn < a.total_d ? (int)jn : -1;
             }
-            asm volatile("bar.sync 2, 128;" ::: "memory");
+            dg_sync();
             const int job = d_job;
-            asm volatile("bar.sync 2, 128;" ::: "memory");
+            dg_sync();
             if (job < 0 || *abort) break;
             int i, gt, mg;
             {
@@ -1175,7 +1248,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 }
             }
             if (tid == 0) wait_count(&done_E[gt], (uint32_t)(a.e_per_tile * i), abort, err);
-            asm volatile("bar.sync 2, 128;" ::: "memory");
+            dg_sync();
             if (*abort) break;
             if (i > 0 && !a.cmux) {
                 // Every product job of the tile's step i-1 has copied its digit stages, so
@@ -1183,7 +1256,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 // them: drop them from L2 without writing them back (2 KB per block: the
                 // part's 8 gates of each 32 KB stage block, 16 lines of 128 bytes).
                 const int nblk = NT * 2 * l * kstages;
-                for (int q = tid; q < nblk * 16; q += 128) {
+                for (int q = tid; q < nblk * 16; q += DG_THREADS) {
                     const uint4 *ln = a.digits + (size_t)(gt * nblk + q / 16) * (A_STAGE_BYTES / 16) +
                                       (size_t)mg * 128 + (q % 16) * 8;
                     asm volatile("discard.global.L2 [%0], 128;" ::"l"(ln) : "memory");
@@ -1193,153 +1266,190 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // into shared memory, then thread (m8 = tid & 7, kb = tid >> 3) digitises
             // positions kp = kc*KS + 8 kb .. + 7 of every size-s block of gate m8, so 8
             // consecutive threads write 128 contiguous bytes of the A-operand layout (stage
-            // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).
-            const int pitch = N + 4;
+            // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).  Row pitch N + 12:
+            // room for the negated first 8 words, and 8 rows on distinct bank quads.
+            const int pitch = N + 12;
             __shared__ uint32_t bbar_s[8];  // b~ of the part's gates (step 0)
+            // ModSwitched coefficient k of gate g's combination (fused form; 0 for a bad
+            // gate type or index)
+            auto ms_coef = [&](int64_t g, int k) -> uint32_t {
+                if (!gate_ok(a.types, a.idx, a.num_in, g)) return 0u;
+                uint32_t kappa, s1, s2;
+                gate_coeffs(a.types[g], kappa, s1, s2);
+                uint32_t x = s1 * __ldg(a.in + (int64_t)a.idx[2 * g] * a.n1 + k) +
+                             s2 * __ldg(a.in + (int64_t)a.idx[2 * g + 1] * a.n1 + k);
+                if (k == a.n1 - 1) x += kappa;
+                return (x + (1u << (a.ms_shift - 1))) >> a.ms_shift;
+            };
             if (i == 0 && !a.cmux) {
                 // step 0: the part's ModSwitched combinations (fused form) and b~
                 const int n1 = a.n1;
                 if (a.in) {
-                    for (int e = tid; e < 8 * n1; e += 128) {
+                    for (int e = tid; e < 8 * n1; e += DG_THREADS) {
                         const int m = e / n1, k = e - m * n1;
                         const int64_t g = (int64_t)gt * TILE_M + mg * 8 + m;
                         if (g >= a.G) continue;
-                        uint32_t v = 0;
-                        if (gate_ok(a.types, a.idx, a.num_in, g)) {
-                            uint32_t kappa, s1, s2;
-                            gate_coeffs(a.types[g], kappa, s1, s2);
-                            uint32_t x = s1 * __ldg(a.in + (int64_t)a.idx[2 * g] * n1 + k) +
-                                         s2 * __ldg(a.in + (int64_t)a.idx[2 * g + 1] * n1 + k);
-                            if (k == n1 - 1) x += kappa;
-                            v = (x + (1u << (a.ms_shift - 1))) >> a.ms_shift;
-                        } else if (k == 0) {
-                            atomicCAS(err, 0, TFHE_EINVAL);
-                        }
-                        a.bar_w[g * n1 + k] = v;
+                        if (k == 0 && !gate_ok(a.types, a.idx, a.num_in, g)) atomicCAS(err, 0, TFHE_EINVAL);
+                        a.bar_w[g * n1 + k] = ms_coef(g, k);
                     }
-                    asm volatile("bar.sync 2, 128;" ::: "memory");
+                    dg_sync();
                 }
                 if (tid < 8) {
                     const int g = gt * TILE_M + mg * 8 + tid;
                     bbar_s[tid] = g < a.G ? __ldcg(a.bar + (size_t)g * n1 + n1 - 1) % (uint32_t)(2 * N) : 0u;
                 }
-                asm volatile("bar.sync 2, 128;" ::: "memory");
+                dg_sync();
             }
-            int rot8[8];  // written at step 0 of this launch when fused: coherent loads
-#pragma unroll
-            for (int m8 = 0; m8 < 8; m8++) {
-                const int g = gt * TILE_M + mg * 8 + m8;
-                rot8[m8] = g < a.G && !a.cmux ? (int)(__ldcg(a.bar + (size_t)g * a.n1 + i) % (uint32_t)(2 * N)) : 0;
-            }
-            const int m8 = tid & 7, kb = tid >> 3;
-            for (int v = tid; v < 8 * NBLK; v += 128) d_abs[v] = 0;
+            // the thread's gate: every work unit of the thread has gate m8 (DG_THREADS and
+            // the unit strides are multiples of 8); a' written at step 0 of this launch when
+            // fused: coherent load
+            const int m8 = tid & 7;
+            const int g8 = gt * TILE_M + mg * 8 + m8;
+            const int rot = g8 < a.G && !a.cmux ? (int)(__ldcg(a.bar + (size_t)g8 * a.n1 + i) % (uint32_t)(2 * N)) : 0;
+            for (int v = tid; v < 8 * NBLK; v += DG_THREADS) d_abs[v] = 0;
             int asum[NBLK];
 #pragma unroll
             for (int b = 0; b < NBLK; b++) asum[b] = 0;
-            const int rot = rot8[m8];
             const int rk = rot >= N ? rot - N : rot;      // X^rot = (-1)^{rot >= N} X^rk
             const uint32_t rneg = rot >= N ? 0xFFFFFFFFu : 0u;
             const uint32_t *row = d_rows + m8 * pitch;
             for (int c = 0; c < 2; c++) {
-                asm volatile("bar.sync 2, 128;" ::: "memory");  // previous polynomial consumed
+                dg_sync();  // previous polynomial consumed
                 {
                     // item (k, h): word k for gates 4h .. 4h+3 of the part, 16 bytes of the
                     // tiled accumulator; the rows of two gate halves land on disjoint banks.
+                    // Words 0..7 are also written negated after the row's N words.
                     // Step 0 writes ACC(0) instead of reading it.
                     uint32_t *accp = a.acc + (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
-#pragma unroll 4
-                    for (int it = tid; it < 2 * N; it += 128) {
+                    auto put = [&](int it, const uint4 &o) {
                         const int k = it >> 1, h = it & 1;
-                        uint4 o;
-                        if (a.cmux) {
-                            // ACC(0) = d0; the shared rows take d1 - d0
-                            uint32_t v0[4], v1[4];
-#pragma unroll
-                            for (int q = 0; q < 4; q++) {
-                                const int x = (gt % a.tpg) * TILE_M + mg * 8 + 4 * h + q, y = gt / a.tpg;
-                                const bool ok = x < a.cm_nx && (int64_t)y * a.cm_nx + x < a.cm_count;
-                                const int64_t o_ = (int64_t)x * a.cm_dx + (int64_t)y * a.cm_dy + (int64_t)c * N + k;
-                                v0[q] = ok ? __ldg(a.cm_d0 + o_) : 0u;
-                                v1[q] = ok ? __ldg(a.cm_d1 + o_) - v0[q] : 0u;
-                            }
-                            __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, make_uint4(v0[0], v0[1], v0[2], v0[3]));
-                            o = make_uint4(v1[0], v1[1], v1[2], v1[3]);
-                        } else if (i > 0) {
-                            o = __ldcg((const uint4 *)(accp + (size_t)k * TILE_M) + h);
-                        } else {
-                            uint32_t v[4] = {0u, 0u, 0u, 0u};
-                            if (c == 1) {
-#pragma unroll
-                                for (int q = 0; q < 4; q++) {
-                                    const int g = gt * TILE_M + mg * 8 + 4 * h + q;
-                                    const uint32_t mu = 1u << 29;
-                                    if (g < a.G) v[q] = ((uint32_t)k + bbar_s[4 * h + q]) % (uint32_t)(2 * N) < (uint32_t)N ? mu : 0u - mu;
-                                }
-                            }
-                            o = make_uint4(v[0], v[1], v[2], v[3]);
-                            __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, o);
-                        }
                         uint32_t *rr = d_rows + 4 * h * pitch + k;
                         rr[0] = o.x;
                         rr[pitch] = o.y;
                         rr[2 * pitch] = o.z;
                         rr[3 * pitch] = o.w;
+                        if (k < 8) {
+                            rr[N] = 0u - o.x;
+                            rr[pitch + N] = 0u - o.y;
+                            rr[2 * pitch + N] = 0u - o.z;
+                            rr[3 * pitch + N] = 0u - o.w;
+                        }
+                    };
+                    if (a.cmux || i == 0) {
+#pragma unroll 4
+                        for (int it = tid; it < 2 * N; it += DG_THREADS) {
+                            const int k = it >> 1, h = it & 1;
+                            uint4 o;
+                            if (a.cmux) {
+                                // ACC(0) = d0; the shared rows take d1 - d0
+                                uint32_t v0[4], v1[4];
+#pragma unroll
+                                for (int q = 0; q < 4; q++) {
+                                    const int x = (gt % a.tpg) * TILE_M + mg * 8 + 4 * h + q, y = gt / a.tpg;
+                                    const bool ok = x < a.cm_nx && (int64_t)y * a.cm_nx + x < a.cm_count;
+                                    const int64_t o_ = (int64_t)x * a.cm_dx + (int64_t)y * a.cm_dy + (int64_t)c * N + k;
+                                    v0[q] = ok ? __ldg(a.cm_d0 + o_) : 0u;
+                                    v1[q] = ok ? __ldg(a.cm_d1 + o_) - v0[q] : 0u;
+                                }
+                                __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, make_uint4(v0[0], v0[1], v0[2], v0[3]));
+                                o = make_uint4(v1[0], v1[1], v1[2], v1[3]);
+                            } else {
+                                uint32_t v[4] = {0u, 0u, 0u, 0u};
+                                if (c == 1) {
+#pragma unroll
+                                    for (int q = 0; q < 4; q++) {
+                                        const int g = gt * TILE_M + mg * 8 + 4 * h + q;
+                                        const uint32_t mu = 1u << 29;
+                                        if (g < a.G) v[q] = ((uint32_t)k + bbar_s[4 * h + q]) % (uint32_t)(2 * N) < (uint32_t)N ? mu : 0u - mu;
+                                    }
+                                }
+                                o = make_uint4(v[0], v[1], v[2], v[3]);
+                                __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, o);
+                            }
+                            put(it, o);
+                        }
+                    } else {
+                        // 8 loads in flight per thread before their shared-memory stores
+                        for (int it0 = tid; it0 < 2 * N; it0 += 8 * DG_THREADS) {
+                            uint4 ov[8];
+#pragma unroll
+                            for (int q = 0; q < 8; q++) {
+                                const int it = it0 + q * DG_THREADS;
+                                if (it < 2 * N)
+                                    ov[q] = __ldcg((const uint4 *)(accp + (size_t)(it >> 1) * TILE_M) + (it & 1));
+                            }
+#pragma unroll
+                            for (int q = 0; q < 8; q++)
+                                if (it0 + q * DG_THREADS < 2 * N) put(it0 + q * DG_THREADS, ov[q]);
+                        }
                     }
                 }
-                asm volatile("bar.sync 2, 128;" ::: "memory");
-                for (int kc = 0; kc < kstages; kc++) {
+                dg_sync();
+                // Work units: spans (stage kc, position group kb, gate m8) of 8 positions with
+                // all l digits (levels 0-2: the rotated differences are computed once per span),
+                // or one digit of a span (level 3: registers).  Consecutive threads take
+                // consecutive gates of a span group: 8 threads write 128 contiguous bytes.
+                const int spans = 128 * kstages;
+                const int units = HOLD ? spans : spans * l;
+                const size_t jd_stride = (size_t)kstages * NT * (A_STAGE_BYTES / 16);
+                // packed sums of |digit| per block, folded into asum every 3 digits (each half
+                // then holds at most 3 * 4 * Bg/2 <= 384: exact, and below 512)
+                uint32_t ah[NBLK];
 #pragma unroll
-                    for (int eh = 0; eh < 8 / E; eh++) {
-                        const int kp = kc * KS + kb * 8 + eh * E;
-                        uint32_t xv[NBLK][E];
+                for (int b = 0; b < NBLK; b++) ah[b] = 0u;
+                int nacc = 0;
+                for (int v = tid; v < units; v += DG_THREADS) {
+                    const int sp = v % spans;
+                    const int jd0 = HOLD ? 0 : v / spans, jd1 = HOLD ? l : jd0 + 1;
+                    const int kc = sp >> 7, kb = (sp >> 3) & 15;
+                    const int kp = kc * KS + kb * 8;
+                    // the unit's 16 bytes in the block of term 0, row c*l + jd, stage kc: the
+                    // blocks of a tile are ordered [2l rows][stages][terms]
+                    uint4 *dst0 = a.digits + (((size_t)gt * 2 * l + c * l) * kstages + kc) * NT * (A_STAGE_BYTES / 16) +
+                                  ((size_t)mg * 16 + kb) * 8 + m8;
+                    uint32_t uh[HOLD ? NBLK : 1][8];
+                    if constexpr (HOLD) {
+#pragma unroll
+                        for (int b = 0; b < NBLK; b++) rotated_diff8(row, N, b * s + kp, rk, rneg, off, a.cmux, uh[b]);
+                    }
+                    for (int jd = jd0; jd < jd1; jd++) {
+                        const int sh = 32 - (jd + 1) * Bgbit;
+                        uint32_t dg[NBLK][DW];
 #pragma unroll
                         for (int b = 0; b < NBLK; b++) {
-                            const int k0 = b * s + kp;
-                            uint32_t own[E];
+                            uint32_t u[8];
+                            if constexpr (HOLD) {
 #pragma unroll
-                            for (int q = 0; q < E; q += 4) {
-                                const uint4 o4 = *(const uint4 *)(row + k0 + q);
-                                own[q] = o4.x;
-                                own[q + 1] = o4.y;
-                                own[q + 2] = o4.z;
-                                own[q + 3] = o4.w;
-                            }
-                            if (a.cmux) {  // the rows hold d1 - d0
-#pragma unroll
-                                for (int e = 0; e < E; e++) xv[b][e] = own[e];
+                                for (int e = 0; e < 8; e++) u[e] = uh[b][e];
                             } else {
+                                rotated_diff8(row, N, b * s + kp, rk, rneg, off, a.cmux, u);
+                            }
 #pragma unroll
-                                for (int e = 0; e < E; e++) {
-                                    const int k = k0 + e;
-                                    const int src = k - rk;
-                                    uint32_t v = src >= 0 ? row[src] : 0u - row[src + N];
-                                    v = (v ^ rneg) - rneg;  // negate when rot >= N
-                                    xv[b][e] = v - own[e];
-                                }
+                            for (int w = 0; w < DW; w++) {
+                                dg[b][w] = digit_pair(u[2 * w], u[2 * w + 1], sh, fmask, dsub);
+                                ah[b] = hadd2(ah[b], habs2(dg[b][w]));
                             }
                         }
-                        for (int jd = 0; jd < l; jd++) {
-                            int dg[NBLK][E];
+                        DigitStore emit{dst0 + (size_t)jd * jd_stride};
+                        kara_terms<NBLK>(dg, emit);
+                        if (++nacc == 3) {
 #pragma unroll
-                            for (int b = 0; b < NBLK; b++)
-#pragma unroll
-                                for (int e = 0; e < E; e++) {
-                                    dg[b][e] = gadget_digit(xv[b][e] + off, jd + 1, a.Bgbit);
-                                    asum[b] += abs(dg[b][e]);
-                                }
-                            const int r = c * l + jd;
-                            const size_t u0 = ((size_t)mg * 16 + kb) * 8 + m8;
-                            const size_t blk0 = ((size_t)gt * NT * 2 * l + r) * kstages + kc;
-                            DigitStore<E> emit{a.digits, blk0 * (A_STAGE_BYTES / 16) + u0,
-                                               (size_t)2 * l * kstages * (A_STAGE_BYTES / 16), eh};
-                            kara_terms<NBLK, E>(dg, emit);
+                            for (int b = 0; b < NBLK; b++) {
+                                asum[b] += fold_f16_sums(ah[b]);
+                                ah[b] = 0u;
+                            }
+                            nacc = 0;
                         }
                     }
                 }
+                if (nacc > 0) {
+#pragma unroll
+                    for (int b = 0; b < NBLK; b++) asum[b] += fold_f16_sums(ah[b]);
+                }
             }
-            // one-pass check: reduce the block sums over the 16 threads of each gate, then
-            // mark the step if some gate exceeds the bound for some term (read by the
-            // product jobs)
+            // one-pass check: reduce the block sums over the threads of each gate, then mark
+            // the step if some gate exceeds the bound for some term (read by the product
+            // jobs)
 #pragma unroll
             for (int b = 0; b < NBLK; b++) {
                 int v = asum[b];
@@ -1347,9 +1457,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 v += __shfl_xor_sync(0xffffffffu, v, 16);
                 if (lane < 8) atomicAdd(&d_abs[lane * NBLK + b], v);
             }
-            asm volatile("bar.sync 2, 128;" ::: "memory");
-            if (tid < 8 * NT) {
-                const int gq = tid / NT, jt = tid % NT;
+            dg_sync();
+            for (int t = tid; t < 8 * NT; t += DG_THREADS) {
+                const int gq = t / NT, jt = t % NT;
                 int v = 0;
 #pragma unroll
                 for (int j = 0; j < NT; j++) {  // compile-time coefficients, selected by jt
@@ -1360,7 +1470,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 }
                 if (v > a.one_pass_limit) atomicMax(&two_pass[gt], (uint32_t)(i + 1));
             }
-            asm volatile("bar.sync 2, 128;" ::: "memory");
+            dg_sync();
             if (tid == 0) red_release_add(&done_D[gt], 1u);
         }
     }

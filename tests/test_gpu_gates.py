@@ -262,3 +262,25 @@ def test_tc_variants_agree_on_every_word(torch_cuda, G):
     samples = sorted({g for t in range(0, G, 128) for g in (t, min(t + 127, G - 1))})
     want = orc.gate_batch(p, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=samples)
     assert np.array_equal(outs[1][samples], want)
+
+
+def test_tc_uneven_tile_chunks(torch_cuda):
+    """4,224 gates = 33 tiles: the tensor-core launch runs its tiles in two chunks of 17
+    and 16 (all steps of one chunk before the next).  Every output decrypts to its
+    plaintext gate, the first and last gate of every tile match the oracle word for word,
+    and the words equal the two-prime per-gate form's."""
+    p = ti.STD
+    ctx, k = gpu_context(p, ti.SEED_FLAT)
+    G = 4224
+    b = ti.flat_level(G)
+    outs = {}
+    for form in (1, 2):
+        out = empty(torch_cuda, G, p.n + 1)
+        ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=form)
+        ctx.sync()
+        outs[form] = from_dev(out)
+    assert np.array_equal(orc.tlwe_decrypt(k.s0, outs[1]), b.expected)
+    assert np.array_equal(outs[1], outs[2])
+    samples = sorted({g for t in range(0, G, 128) for g in (t, min(t + 127, G - 1))})
+    want = orc.gate_batch(p, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=samples)
+    assert np.array_equal(outs[1][samples], want)
