@@ -65,7 +65,7 @@ constexpr int TILE_M = 128;  // gates per tile (TMEM lanes)
 constexpr int NB = 128;      // output columns per tile and MMA N
 constexpr int KS = 128;      // digits (K) per pipeline stage
 constexpr int PLANES = 4;    // byte planes of the key
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int A_STAGE_BYTES = TILE_M * KS * 2;            // 32 KB
 constexpr int B_UNITS = NB + KS;                          // units per plane and stage
 constexpr int B_PLANE_BYTES = B_UNITS * 16;               // 4 KB
