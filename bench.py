@@ -45,6 +45,11 @@ def parse():
                     help="Karatsuba levels of the tensor-core form (-1: library default)")
     ap.add_argument("--tc-variant", type=int, default=-1,
                     help="tensor-core BlindRotate: 0 one SM per tile, 1 SM pairs, -1 default")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "levels", "dataflow"],
+                    help="dag/mixed: level by level (autotuned form per level, graph replay) or "
+                         "dataflow (every gate in the two-prime per-gate form, started once its "
+                         "inputs exist); auto: dataflow for dag, levels for mixed (the faster "
+                         "on B300); the other schedule is timed too and reported")
     ap.add_argument("--cb-reads", type=int, default=64,
                     help="cb workload: reads of 9 TLWE address bits each (576 bootstraps at 64)")
     ap.add_argument("--workload", default="level", choices=["level", "dag", "mixed", "rom", "mux", "ramcycle", "romp", "cb"],
@@ -539,15 +544,45 @@ def run_other(args):
         dev_in = dev(np.concatenate(cts))
         out = torch.zeros((total, p.n + 1), dtype=torch.int32, device="cuda")
 
+        schedule = args.schedule
+        if schedule == "auto":
+            schedule = "dataflow" if args.workload == "dag" else "levels"
+
+        def run_sched(which, dst):
+            if which == "levels":
+                plan.run(dev_in, dst, use_graph=True)
+            else:
+                plan.run_dataflow(dev_in, dst)
+
         def step():
-            plan.run(dev_in, out, use_graph=True)
+            run_sched(schedule, out)
         units, unit = total, "gates/s"
-        metric = ("bootstrapped gates/s through the level scheduler, " +
+        metric = ("bootstrapped gates/s through the " +
+                  ("level scheduler (graph replay), " if schedule == "levels" else
+                   "dataflow scheduler (two-prime per-gate form), ") +
                   ("20,000-gate 60-level DAG" if args.workload == "dag" else
-                   f"16 uneven circuits ({total} gates) interleaved") + ", graph replay")
-        workload = metric.split(", ", 1)[1]
+                   f"16 uneven circuits ({total} gates) interleaved"))
+        workload = ("20,000-gate 60-level DAG" if args.workload == "dag" else
+                    f"16 uneven circuits ({total} gates) interleaved")
+        extra["schedule"] = schedule
         step()
         ctx.sync()
+        # the other schedule: same words, its time (best of two after a warm-up)
+        other = "levels" if schedule == "dataflow" else "dataflow"
+        out_o = torch.zeros_like(out)
+        run_sched(other, out_o)
+        t_o = []
+        for _ in range(2):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run_sched(other, out_o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_o.append(e0.elapsed_time(e1))
+        extra["other_schedule"] = {"schedule": other, "ms_per_step": min(t_o),
+                                   "gates_per_s": total / (min(t_o) / 1e3),
+                                   "same_words": bool(torch.equal(out, out_o))}
         # correctness guard: every output decrypts to the plaintext circuit
         truth = np.array([[[ti.plain_gate(t, a, b) for b in (0, 1)] for a in (0, 1)]
                           for t in range(10)], np.uint8)

@@ -441,6 +441,19 @@ int tfhe_plan_circuit_last_level(const tfhe_plan *plan, int c);
 int tfhe_plan_run(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out, int use_graph,
                   void **level_events, void *stream);
 
+/* Evaluate the plan as a dataflow (Section 6.2(d): list scheduling over the gate DAG)
+ * instead of level by level: one persistent launch of two blocks per SM, in which each
+ * block takes the next ready gate, evaluates it end to end in the two-prime per-gate
+ * form (combination, ModSwitch, BlindRotate, SampleExtract, key switch) and makes ready
+ * every consumer whose last input it produced; a wide level's last wave then overlaps the
+ * next level's first gates.  Same arguments and outputs as tfhe_plan_run (the words are
+ * identical: every form is exact); the plan's form choice is not used.  A block that
+ * finds no ready gate waits, and gives up with TFHE_ETIMEOUT (at the next sync) only
+ * after about 2 s in which no gate became ready.  TFHE_EUNSUPPORTED without the
+ * two-prime form.  Asynchronous on `stream`. */
+int tfhe_plan_run_dataflow(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out,
+                           void *stream);
+
 void tfhe_plan_destroy(tfhe_plan *plan);
 
 /* Plan autotuner (the level scheduler's choice of form and Karatsuba level per batch

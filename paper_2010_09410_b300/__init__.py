@@ -35,7 +35,7 @@ EXPORTS = [
     "tfhe_ctx_set_keys", "tfhe_ctx_reserve", "tfhe_ctx_sync", "tfhe_gate_batch",
     "tfhe_gate_batch_host", "tfhe_blind_rotate", "tfhe_extract_keyswitch", "tfhe_cmux_batch",
     "tfhe_cmux_tree_read", "tfhe_ram_write", "tfhe_circuit_plan", "tfhe_plan_num_levels",
-    "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_destroy",
+    "tfhe_plan_circuit_last_level", "tfhe_plan_run", "tfhe_plan_run_dataflow", "tfhe_plan_destroy",
     "tfhe_ctx_enable_timing", "tfhe_ctx_stage_times", "tfhe_gate_batch_noalloc",
     "tfhe_ctx_set_tc_level",
     "tfhe_ctx_tc_level",
@@ -108,6 +108,7 @@ def lib():
         "tfhe_plan_num_levels": (i32, [vp]),
         "tfhe_plan_circuit_last_level": (i32, [vp, i32]),
         "tfhe_plan_run": (i32, [vp, vp, vp, i32, vp, vp]),
+        "tfhe_plan_run_dataflow": (i32, [vp, vp, vp, vp]),
         "tfhe_plan_destroy": (None, [vp]),
         "tfhe_ctx_enable_timing": (i32, [vp, i32]),
         "tfhe_ctx_stage_times": (i32, [vp, vp, vp]),
@@ -378,6 +379,12 @@ class Plan:
         self.ctx._check(lib().tfhe_plan_run(self.h, _ptr(primary_in), _ptr(gate_out),
                                             1 if use_graph else 0, ev, _stream(stream)),
                         "plan_run")
+        return gate_out
+
+    def run_dataflow(self, primary_in, gate_out, stream=None):
+        """All gates in the two-prime per-gate form, each started once its inputs exist."""
+        self.ctx._check(lib().tfhe_plan_run_dataflow(self.h, _ptr(primary_in), _ptr(gate_out),
+                                                     _stream(stream)), "plan_run_dataflow")
         return gate_out
 
     def close(self):

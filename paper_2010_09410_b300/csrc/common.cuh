@@ -173,6 +173,31 @@ int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);
 // Gate inputs for the tensor-core BlindRotate's fused combination: its step-0 digit jobs
 // compute bar = ModSwitch(gate combination) from these (into the `bar` buffer) and
 // initialise the accumulators.
+// Dataflow evaluation of a gate DAG (Section 6.2(d) list scheduling) in the two-prime
+// per-gate form: a persistent grid of blocks takes ready gates from a queue, evaluates
+// each end to end (combination, ModSwitch, BlindRotate, SampleExtract, key switch) and
+// queues every consumer whose last input it completed.  Gates are numbered 0 .. G-1;
+// gate g reads wires idx[2g], idx[2g+1] and writes wire num_in + g of `wires`
+// ([num_in + G][n+1]).  Consumers of g: cons[cons_off[g] .. cons_off[g+1]) (a gate that
+// reads g twice appears twice); pending[g] counts g's inputs that are gates; queue holds
+// the ready gates in the order they became ready (-1: not yet), its first `ready0` entries
+// set; ctr = {tickets taken, gates queued}.  The caller resets pending, queue and ctr
+// before each run.
+struct TfheDataflow {
+    uint32_t *wires;
+    int64_t num_in, G;
+    const uint8_t *types;
+    const int32_t *idx;
+    const int32_t *cons_off, *cons;
+    int32_t *pending, *queue;
+    uint32_t *ctr;
+    uint32_t *scratch;  // [blocks][n+1]: ModSwitched combination of each block's gate
+    int blocks;         // grid size (two per SM); scratch holds this many rows
+};
+int tfhe_dataflow_ntt2(tfhe_ctx *ctx, const TfheDataflow &df, cudaStream_t st);
+// the grid size the dataflow engine runs with on this context's device
+int tfhe_dataflow_blocks(tfhe_ctx *ctx);
+
 struct TcGateInputs {
     const uint32_t *in;
     int64_t num_in;

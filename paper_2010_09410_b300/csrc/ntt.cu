@@ -251,25 +251,15 @@ __global__ void __launch_bounds__(256) k_cmux_ntt(int N, int logN, int l, int Bg
         o[j] = base[j] + prod32_word(prod, N, j >= N, j >= N ? j - N : j);
 }
 
-// Per-gate BlindRotate in the two-prime NTT form (TFHE_FORM_NTT2): as k_blind_rotate_ntt,
-// with each external product computed by extprod32 against the BSK in the two-prime NTT
-// form (u32[n][2l][2][2 primes][N]).  Shared memory: digits, products, accumulator,
-// rotation difference and the twiddle table (112 KB at N = 1024, l = 3).
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_blind_rotate_ntt2(
-    int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
-    uint32_t *__restrict__ acc_out, const uint32_t *__restrict__ bsk2p,
-    const uint32_t *__restrict__ tw) {
-    extern __shared__ __align__(16) uint32_t smb[];
-    uint32_t *dig = smb;                          // [2][2l][N]
-    uint32_t *prod = dig + (size_t)4 * l * N;      // [2][2][N]
-    uint32_t *acc = prod + (size_t)4 * N;          // [2][N]
-    uint32_t *diff = acc + 2 * N;                  // [2][N]
-    uint32_t *tws = diff + 2 * N;                  // [2][2][N][2]
-    for (int x = threadIdx.x; x < 2 * N; x += blockDim.x)
-        reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
-    const size_t g = blockIdx.x;
-    const uint32_t *mb = bar + g * (n + 1);
+// BlindRotate of one gate by the whole block in the two-prime NTT form: ACC (shared,
+// u32[2][N]) <- X^{-b~}(0, v), then for i < n: ACC += BSK_i (.) (X^{a~_i} ACC - ACC).  mb is
+// the ModSwitched combination (u32[n+1], global: a~_0 .. a~_{n-1}, b~); dig, prod, diff
+// are shared work areas, tws the block's twiddle copy.
+__device__ __forceinline__ void br_ntt2_block(int n, int N, int logN, int l, int Bgbit,
+                                              const uint32_t *mb, uint32_t *acc, uint32_t *dig,
+                                              uint32_t *prod, uint32_t *diff,
+                                              const uint32_t *__restrict__ bsk2p,
+                                              const uint32_t *tws) {
     const uint32_t mu = 1u << 29;
     const int M = 2 * N;
     const int bb = (int)(mb[n] % (uint32_t)M);
@@ -292,8 +282,174 @@ __global__ void __launch_bounds__(MAXT, 1) k_blind_rotate_ntt2(
             acc[j] += prod32_word(prod, N, j >= N, j >= N ? j - N : j);
         __syncthreads();
     }
+}
+
+// Per-gate BlindRotate in the two-prime NTT form (TFHE_FORM_NTT2): as k_blind_rotate_ntt,
+// with each external product computed by extprod32 against the BSK in the two-prime NTT
+// form (u32[n][2l][2][2 primes][N]).  Shared memory: digits, products, accumulator,
+// rotation difference and the twiddle table (112 KB at N = 1024, l = 3).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_blind_rotate_ntt2(
+    int n, int N, int logN, int l, int Bgbit, const uint32_t *__restrict__ bar,
+    uint32_t *__restrict__ acc_out, const uint32_t *__restrict__ bsk2p,
+    const uint32_t *__restrict__ tw) {
+    extern __shared__ __align__(16) uint32_t smb[];
+    uint32_t *dig = smb;                          // [2][2l][N]
+    uint32_t *prod = dig + (size_t)4 * l * N;      // [2][2][N]
+    uint32_t *acc = prod + (size_t)4 * N;          // [2][N]
+    uint32_t *diff = acc + 2 * N;                  // [2][N]
+    uint32_t *tws = diff + 2 * N;                  // [2][2][N][2]
+    for (int x = threadIdx.x; x < 2 * N; x += blockDim.x)
+        reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
+    const size_t g = blockIdx.x;
+    br_ntt2_block(n, N, logN, l, Bgbit, bar + g * (n + 1), acc, dig, prod, diff, bsk2p, tws);
     uint32_t *o = acc_out + g * 2 * N;
     for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) o[j] = acc[j];
+}
+
+// ---- dataflow engine (TfheDataflow) ------------------------------------------------
+
+__device__ __forceinline__ int df_ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void df_st_release(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int df_sub_acq_rel(int32_t *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(-v) : "memory");
+    return old;
+}
+// give up a wait for a queue slot after this many cycles without any gate being queued
+// (about 2 s at 2 GHz)
+constexpr long long DF_STALL_CYCLES = 4000000000LL;
+
+// SampleExtract (coefficient 0) and identity key switch of the block's accumulator
+// (shared, u32[2][N]) into the TLWE `out` (u32[n+1]): a'_0 = a_0, a'_i = -a_{N-i}, b' = b_0;
+// out = (0, b') - sum_{i, j} KSK[i][j][digit_j(a'_i)].  Thread (c, grp) sums 16-byte column
+// c of the key rows for i = grp, grp + ngrp, ...; the groups' sums meet in `part` (shared,
+// uint4[ngrp][ncol]).  KSK rows: u32[N][t][base-1][n_pad] (v = 0 dropped).
+__device__ __forceinline__ void ks_block(const uint32_t *acc, int n, int N, int t, int bb,
+                                         int n_pad, const uint4 *__restrict__ ksk, uint32_t *out,
+                                         uint4 *part) {
+    const int ncol = n_pad >> 2, ngrp = (int)blockDim.x / ncol;
+    const int c = threadIdx.x % ncol, grp = threadIdx.x / ncol;
+    const int base1 = (1 << bb) - 1;
+    const uint32_t prec = 1u << (32 - (1 + bb * t)), mask = (1u << bb) - 1;
+    if (grp < ngrp) {
+        uint4 r = make_uint4(0, 0, 0, 0);
+        for (int i = grp; i < N; i += ngrp) {
+            const uint32_t ab = (i == 0 ? acc[0] : 0u - acc[N - i]) + prec;
+            const uint4 *rows = ksk + (size_t)i * t * base1 * ncol + c;
+#pragma unroll 8
+            for (int j = 0; j < t; j++) {
+                const uint32_t d = (ab >> (32 - (j + 1) * bb)) & mask;
+                if (d) {
+                    const uint4 k = __ldg(rows + ((size_t)j * base1 + d - 1) * ncol);
+                    r.x += k.x;
+                    r.y += k.y;
+                    r.z += k.z;
+                    r.w += k.w;
+                }
+            }
+        }
+        part[grp * ncol + c] = r;
+    }
+    __syncthreads();
+    if (grp == 0) {
+        uint4 r = part[c];
+        for (int q = 1; q < ngrp; q++) {
+            const uint4 o = part[q * ncol + c];
+            r.x += o.x;
+            r.y += o.y;
+            r.z += o.z;
+            r.w += o.w;
+        }
+        const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+        for (int q = 0; q < 4; q++) {
+            const int k = 4 * c + q;
+            if (k <= n) out[k] = (k == n ? acc[N] : 0u) - v[q];
+        }
+    }
+}
+
+// The engine: every block loops { take a ticket t; wait until queue[t] holds a gate (or
+// t >= G: done); evaluate the gate; queue its consumers that became ready }.  Every gate
+// is queued exactly once, after its inputs are written, and the DAG is acyclic, so a
+// block that waits always has a gate coming unless the run has failed; a wait gives up
+// (TFHE_ETIMEOUT) only when no gate has been queued for DF_STALL_CYCLES.
+__global__ void __launch_bounds__(512, 2) k_dataflow_ntt2(
+    TfheDataflow df, int n, int N, int logN, int l, int Bgbit, int t, int bb, int n_pad,
+    int ms_shift, const uint32_t *__restrict__ bsk2p, const uint32_t *__restrict__ tw,
+    const uint4 *__restrict__ ksk, int *err) {
+    extern __shared__ __align__(16) uint32_t smb[];
+    uint32_t *dig = smb;                          // [2][2l][N]
+    uint32_t *prod = dig + (size_t)4 * l * N;      // [2][2][N]
+    uint32_t *acc = prod + (size_t)4 * N;          // [2][N]
+    uint32_t *diff = acc + 2 * N;                  // [2][N]
+    uint32_t *tws = diff + 2 * N;                  // [2][2][N][2]
+    __shared__ int s_gate;
+    for (int x = threadIdx.x; x < 2 * N; x += blockDim.x)
+        reinterpret_cast<uint4 *>(tws)[x] = __ldg(reinterpret_cast<const uint4 *>(tw) + x);
+    const int n1 = n + 1;
+    uint32_t *mb = df.scratch + (size_t)blockIdx.x * n1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t tk = atomicAdd(&df.ctr[0], 1u);
+            int gate = -1;
+            if ((int64_t)tk < df.G) {
+                long long t0 = clock64();
+                uint32_t seen = *(volatile uint32_t *)&df.ctr[1];
+                while ((gate = df_ld_acquire(df.queue + tk)) < 0) {
+                    const uint32_t now = *(volatile uint32_t *)&df.ctr[1];
+                    if (now != seen) {
+                        seen = now;
+                        t0 = clock64();
+                    } else if (clock64() - t0 > DF_STALL_CYCLES || *(volatile int *)err) {
+                        atomicCAS(err, 0, TFHE_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            s_gate = gate;
+        }
+        __syncthreads();
+        const int g = s_gate;
+        if (g < 0) break;
+        // combination (inputs written by other blocks of this launch: coherent loads) and
+        // ModSwitch into the block's scratch row
+        {
+            uint32_t kappa, s1, s2;
+            gate_coeffs(df.types[g], kappa, s1, s2);
+            const uint32_t *w0 = df.wires + (size_t)df.idx[2 * g] * n1;
+            const uint32_t *w1 = df.wires + (size_t)df.idx[2 * g + 1] * n1;
+            for (int k = threadIdx.x; k < n1; k += blockDim.x) {
+                uint32_t x = s1 * __ldcg(w0 + k) + s2 * __ldcg(w1 + k);
+                if (k == n) x += kappa;
+                mb[k] = (x + (1u << (ms_shift - 1))) >> ms_shift;
+            }
+        }
+        __syncthreads();
+        br_ntt2_block(n, N, logN, l, Bgbit, mb, acc, dig, prod, diff, bsk2p, tws);
+        ks_block(acc, n, N, t, bb, n_pad, ksk, df.wires + (size_t)(df.num_in + g) * n1,
+                 reinterpret_cast<uint4 *>(dig));
+        // publish: the barrier orders the block's output stores before the leader's fence
+        // (cumulative); each consumer whose last gate input this was is queued
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            for (int e = df.cons_off[g]; e < df.cons_off[g + 1]; e++) {
+                const int cg = df.cons[e];
+                if (df_sub_acq_rel(df.pending + cg, 1) == 1) {
+                    const uint32_t slot = atomicAdd(&df.ctr[1], 1u);
+                    df_st_release(df.queue + slot, cg);
+                }
+            }
+        }
+    }
 }
 
 // One block per RAM cell c (write bar, Section 8.2): r = new; for j < v:
@@ -442,6 +598,33 @@ int tfhe_blind_rotate_ntt2(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, in
     }
     tm.stop();
     return tfhe_check_launch(ctx, "blind_rotate_ntt2");
+}
+
+int tfhe_dataflow_blocks(tfhe_ctx *ctx) {
+    if (!ctx->sms && cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+        return 0;
+    return 2 * ctx->sms;
+}
+
+int tfhe_dataflow_ntt2(tfhe_ctx *ctx, const TfheDataflow &df, cudaStream_t st) {
+    const tfhe_params &p = ctx->p;
+    if (df.G == 0) return TFHE_OK;
+    if (!ctx->bsk_ntt2)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "dataflow: two-prime NTT form not available here");
+    if (ctx->n_pad / 4 > 512)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "dataflow: key rows wider than the block");
+    const size_t smem = ((size_t)4 * p.l * p.N + (size_t)16 * p.N) * 4;
+    if ((size_t)(ctx->n_pad / 4) * (512 / (ctx->n_pad / 4)) * 16 > (size_t)4 * p.l * p.N * 4)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "dataflow: key-switch partial sums do not fit");
+    TFHE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dataflow_ntt2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    StageTimer tm(ctx, TFHE_STAGE_BLIND_ROTATE_NTT, st);
+    k_dataflow_ntt2<<<df.blocks, 512, smem, st>>>(df, p.n, p.N, ctx->logN, p.l, p.Bgbit, p.ks_t,
+                                                  p.ks_basebit, ctx->n_pad, 32 - (ctx->logN + 1),
+                                                  ctx->bsk_ntt2, ctx->tw32,
+                                                  (const uint4 *)ctx->ksk, ctx->d_err);
+    tm.stop();
+    return tfhe_check_launch(ctx, "dataflow_ntt2");
 }
 
 static size_t cmux_smem(const tfhe_params &p) {

@@ -19,6 +19,15 @@ struct tfhe_plan {
     int32_t *d_idx = nullptr;         // level-major input wire indices (internal numbering)
     int64_t *d_perm = nullptr;        // output slot (circuit order) -> internal wire
     uint32_t *d_wires = nullptr;      // [total_wires][n+1]
+    // dataflow runs (tfhe_plan_run_dataflow): consumers of each gate (CSR over the
+    // level-major gate positions), gate inputs per gate, the initial queue (the gates
+    // without gate inputs, then -1) and counters, reset from these copies before each run
+    int32_t *d_cons_off = nullptr, *d_cons = nullptr;
+    int32_t *d_pending0 = nullptr, *d_pending = nullptr;
+    int32_t *d_queue0 = nullptr, *d_queue = nullptr;
+    uint32_t *d_ctr0 = nullptr, *d_ctr = nullptr;
+    uint32_t *d_scratch = nullptr;
+    int df_blocks = 0;
     // graph cache
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -48,6 +57,10 @@ extern "C" void tfhe_plan_destroy(tfhe_plan *plan) {
     if (plan->d_idx) cudaFree(plan->d_idx);
     if (plan->d_perm) cudaFree(plan->d_perm);
     if (plan->d_wires) cudaFree(plan->d_wires);
+    for (void *q : {(void *)plan->d_cons_off, (void *)plan->d_cons, (void *)plan->d_pending0,
+                    (void *)plan->d_pending, (void *)plan->d_queue0, (void *)plan->d_queue,
+                    (void *)plan->d_ctr0, (void *)plan->d_ctr, (void *)plan->d_scratch})
+        if (q) cudaFree(q);
     delete plan;
 }
 
@@ -217,8 +230,97 @@ extern "C" int tfhe_circuit_plan(tfhe_ctx *ctx, const tfhe_circuit *circuits, in
         tfhe_plan_destroy(plan);
         return rc;
     }
+    // dataflow tables: consumers (CSR), gate inputs per gate, initial queue
+    {
+        std::vector<int32_t> pend(total_g, 0), cnt(total_g + 1, 0);
+        for (int64_t q = 0; q < total_g; q++)
+            for (int s = 0; s < 2; s++) {
+                const int64_t w = h_idx[2 * q + s];
+                if (w >= total_in) {
+                    cnt[w - total_in + 1]++;
+                    pend[q]++;
+                }
+            }
+        for (int64_t q = 0; q < total_g; q++) cnt[q + 1] += cnt[q];
+        std::vector<int32_t> cons(std::max<int64_t>(cnt[total_g], 1), 0), fillc(cnt.begin(), cnt.end() - 1);
+        for (int64_t q = 0; q < total_g; q++)
+            for (int s = 0; s < 2; s++) {
+                const int64_t w = h_idx[2 * q + s];
+                if (w >= total_in) cons[fillc[w - total_in]++] = (int32_t)q;
+            }
+        std::vector<int32_t> queue0(std::max<int64_t>(total_g, 1), -1);
+        uint32_t ready = 0;
+        for (int64_t q = 0; q < total_g; q++)
+            if (pend[q] == 0) queue0[ready++] = (int32_t)q;
+        const uint32_t ctr0[2] = {0u, ready};
+        plan->df_blocks = tfhe_dataflow_blocks(ctx);
+        const size_t gq = (size_t)std::max<int64_t>(total_g, 1);
+        bool ok = plan->df_blocks > 0 &&
+                  cudaMalloc(&plan->d_cons_off, (gq + 1) * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_cons, cons.size() * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_pending0, gq * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_pending, gq * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_queue0, gq * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_queue, gq * 4) == cudaSuccess &&
+                  cudaMalloc(&plan->d_ctr0, 8) == cudaSuccess && cudaMalloc(&plan->d_ctr, 8) == cudaSuccess &&
+                  cudaMalloc(&plan->d_scratch, (size_t)plan->df_blocks * wb * 4) == cudaSuccess;
+        if (!ok) {
+            tfhe_plan_destroy(plan);
+            return tfhe_set_error(ctx, TFHE_ENOMEM, "circuit_plan: dataflow tables");
+        }
+        ok = cudaMemcpy(plan->d_cons_off, cnt.data(), (total_g + 1) * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(plan->d_cons, cons.data(), cons.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             (total_g == 0 || cudaMemcpy(plan->d_pending0, pend.data(), total_g * 4, cudaMemcpyHostToDevice) == cudaSuccess) &&
+             cudaMemcpy(plan->d_queue0, queue0.data(), gq * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(plan->d_ctr0, ctr0, 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        if (!ok) {
+            tfhe_plan_destroy(plan);
+            return tfhe_set_error(ctx, TFHE_ECUDA, "circuit_plan: dataflow upload");
+        }
+    }
     *out = plan;
     return TFHE_OK;
+}
+
+// Dataflow run: every gate in the two-prime per-gate form, each started as soon as its
+// inputs are written (TfheDataflow), instead of level by level.
+extern "C" int tfhe_plan_run_dataflow(tfhe_plan *plan, const uint32_t *primary_in, uint32_t *gate_out,
+                                      void *stream) {
+    if (!plan) return TFHE_EINVAL;
+    tfhe_ctx *ctx = plan->ctx;
+    if ((plan->total_inputs > 0 && !primary_in) || (plan->total_gates > 0 && !gate_out))
+        return tfhe_set_error(ctx, TFHE_EINVAL, "plan_run_dataflow: null pointer");
+    if (!ctx->has_keys) return tfhe_set_error(ctx, TFHE_ENOKEYS, "plan_run_dataflow: keys not set");
+    if (!ctx->bsk_ntt2)
+        return tfhe_set_error(ctx, TFHE_EUNSUPPORTED, "plan_run_dataflow: two-prime NTT form not available here");
+    cudaStream_t st = (cudaStream_t)stream;
+    TFHE_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t wb = (size_t)ctx->p.n + 1;
+    const int64_t G = plan->total_gates;
+    if (plan->total_inputs > 0)
+        TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(plan->d_wires, primary_in, plan->total_inputs * wb * 4,
+                                           cudaMemcpyDeviceToDevice, st));
+    if (G == 0) return TFHE_OK;
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(plan->d_pending, plan->d_pending0, G * 4, cudaMemcpyDeviceToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(plan->d_queue, plan->d_queue0, G * 4, cudaMemcpyDeviceToDevice, st));
+    TFHE_CUDA_TRY(ctx, cudaMemcpyAsync(plan->d_ctr, plan->d_ctr0, 8, cudaMemcpyDeviceToDevice, st));
+    TfheDataflow df{};
+    df.wires = plan->d_wires;
+    df.num_in = plan->total_inputs;
+    df.G = G;
+    df.types = plan->d_types;
+    df.idx = plan->d_idx;
+    df.cons_off = plan->d_cons_off;
+    df.cons = plan->d_cons;
+    df.pending = plan->d_pending;
+    df.queue = plan->d_queue;
+    df.ctr = plan->d_ctr;
+    df.scratch = plan->d_scratch;
+    df.blocks = plan->df_blocks;
+    int rc = tfhe_dataflow_ntt2(ctx, df, st);
+    if (rc != TFHE_OK) return rc;
+    k_gather_rows<<<(unsigned)G, 128, 0, st>>>(plan->d_wires, plan->d_perm, gate_out, (int)wb);
+    return tfhe_check_launch(ctx, "gather_rows");
 }
 
 extern "C" int tfhe_plan_num_levels(const tfhe_plan *plan) { return plan ? plan->num_levels : -1; }

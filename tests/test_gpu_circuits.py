@@ -93,6 +93,11 @@ def test_dag_20000_gates_60_levels(torch_cuda):
     plan.run(dev_in, out2, use_graph=True)
     ctx.sync()
     assert torch.equal(out, out2)
+    # the dataflow run gives the same words (all gates in the two-prime per-gate form)
+    out3 = torch.zeros_like(out)
+    plan.run_dataflow(dev_in, out3)
+    ctx.sync()
+    assert torch.equal(out, out3)
 
 
 def test_16_mixed_circuits_interleaved(torch_cuda):
@@ -128,6 +133,11 @@ def test_16_mixed_circuits_interleaved(torch_cuda):
         off += c.num_gates
         samples = sample_gates(lvs[i], 40, 940 + i)[:3]
         check_circuit(p, k, c, cts[i], bits[i], g, samples)
+    # the dataflow run gives the same words for all 16 circuits at once
+    out2 = torch.zeros_like(out)
+    plan.run_dataflow(dev_in, out2)
+    ctx.sync()
+    assert torch.equal(out, out2)
 
 
 def test_autotuned_plan_matches_fixed_forms(torch_cuda):
