@@ -1263,11 +1263,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 }
             }
             // One accumulator polynomial of the part's 8 gates at a time: the rows are copied
-            // into shared memory, then thread (m8 = tid & 7, kb = tid >> 3) digitises
-            // positions kp = kc*KS + 8 kb .. + 7 of every size-s block of gate m8, so 8
-            // consecutive threads write 128 contiguous bytes of the A-operand layout (stage
-            // kc, row r, term j).  X^{a} p at k is p[k - a] (sign by wrap).  Row pitch N + 12:
-            // room for the negated first 8 words, and 8 rows on distinct bank quads.
+            // into shared memory, then each work unit (stage kc, position group kb, gate
+            // m8 = tid & 7) digitises positions kp = kc*KS + 8 kb .. + 7 of every size-s
+            // block of gate m8, so 8 consecutive threads write 128 contiguous bytes of the
+            // A-operand layout (stage kc, row r, term j).  X^{a} p at k is p[k - a] (sign by
+            // wrap).  Row pitch N + 12: room for the negated first 8 words, and 8 rows on
+            // distinct bank quads.
             const int pitch = N + 12;
             __shared__ uint32_t bbar_s[8];  // b~ of the part's gates (step 0)
             // ModSwitched coefficient k of gate g's combination (fused form; 0 for a bad
