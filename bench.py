@@ -383,7 +383,7 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #   --clock-control none -k regex:"k_tc_blind_rotate|k_extract_keyswitch_staged" -s 2 -c 2
     #   python bench.py --form tc --steps 1 --warmup 3 --no-cpu-baseline
-    "k_tc_blind_rotate<2>": {"bytes": 32.711e9 + 63.460e9, "source_sha256": "88c53f83a677f733d74c819047d7b3fdcfe783dc84d606210effbd03b4cb85e0"},
+    "k_tc_blind_rotate<2>": {"bytes": 32.780e9 + 63.471e9, "source_sha256": "3144a66b8a665e76049bf93d264a155a73ff19c9488cb2b0bcc6106bd48d062f"},
     "k_extract_keyswitch_staged": {"bytes": 79.464e6 + 1.275e6, "source_sha256": "72c94a6c879ea426c95cac355d8881772d54492a707151e3b2374c521ecb4774"},
 }
 

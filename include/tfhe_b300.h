@@ -61,7 +61,9 @@ enum {
     TFHE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
     TFHE_ETIMEOUT = -4,     /* a device-side wait gave up (bounded spin) */
     TFHE_EUNSUPPORTED = -5, /* parameters or form not supported by this build */
-    TFHE_ENOKEYS = -6       /* tfhe_ctx_set_keys has not been called */
+    TFHE_ENOKEYS = -6,      /* tfhe_ctx_set_keys has not been called */
+    TFHE_EBOUNDS = -7       /* debug builds only (compiled with TFHE_BOUNDS_CHECK): a device
+                               index check failed; the access was skipped or redirected */
 };
 
 /* Two-input gate types (uint8 in gate-type arrays).  NY negates the first input,

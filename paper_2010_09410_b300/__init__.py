@@ -15,11 +15,13 @@ import functools
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtfhe_b300.so")
+# TFHE_B300_BOUNDS=1 selects the debug build with device index checks (TFHE_EBOUNDS)
+LIB_PATH = os.path.join(_HERE, "libtfhe_b300_bounds.so" if os.environ.get("TFHE_B300_BOUNDS") == "1"
+                        else "libtfhe_b300.so")
 
 TFHE_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPORTED",
-          -6: "ENOKEYS"}
+          -6: "ENOKEYS", -7: "EBOUNDS"}
 FORM_NTT = 0
 FORM_TC = 1
 FORM_NTT2 = 2

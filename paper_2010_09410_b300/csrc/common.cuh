@@ -183,6 +183,21 @@ int tfhe_tc_set_pass_limit(tfhe_ctx *ctx, int limit);
 // the ready gates in the order they became ready (-1: not yet), its first `ready0` entries
 // set; ctr = {tickets taken, gates queued}.  The caller resets pending, queue and ctr
 // before each run.
+// Debug builds (-DTFHE_BOUNDS_CHECK, libtfhe_b300_bounds.so): device index checks on the
+// hot path.  A failed check records TFHE_EBOUNDS in the context's error word (read at the
+// next sync) and the caller skips the access, or points a bulk copy at an in-bounds
+// source so that its barrier still completes; nothing traps.  In normal builds every
+// check is the constant true and compiles away.
+#ifdef TFHE_BOUNDS_CHECK
+__device__ __forceinline__ bool tfhe_in_bounds(size_t i, size_t n, int *err) {
+    if (i < n) return true;
+    atomicCAS(err, 0, TFHE_EBOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool tfhe_in_bounds(size_t, size_t, int *) { return true; }
+#endif
+
 struct TfheDataflow {
     uint32_t *wires;
     int64_t num_in, G;

@@ -424,8 +424,12 @@ __global__ void __launch_bounds__(512, 2) k_dataflow_ntt2(
         {
             uint32_t kappa, s1, s2;
             gate_coeffs(df.types[g], kappa, s1, s2);
-            const uint32_t *w0 = df.wires + (size_t)df.idx[2 * g] * n1;
-            const uint32_t *w1 = df.wires + (size_t)df.idx[2 * g + 1] * n1;
+            int64_t i0 = df.idx[2 * g], i1 = df.idx[2 * g + 1];
+            const int64_t wires = df.num_in + df.G;
+            if (!tfhe_in_bounds((size_t)i0, (size_t)wires, err)) i0 = 0;
+            if (!tfhe_in_bounds((size_t)i1, (size_t)wires, err)) i1 = 0;
+            const uint32_t *w0 = df.wires + (size_t)i0 * n1;
+            const uint32_t *w1 = df.wires + (size_t)i1 * n1;
             for (int k = threadIdx.x; k < n1; k += blockDim.x) {
                 uint32_t x = s1 * __ldcg(w0 + k) + s2 * __ldcg(w1 + k);
                 if (k == n) x += kappa;
@@ -443,9 +447,10 @@ __global__ void __launch_bounds__(512, 2) k_dataflow_ntt2(
             __threadfence();
             for (int e = df.cons_off[g]; e < df.cons_off[g + 1]; e++) {
                 const int cg = df.cons[e];
+                if (!tfhe_in_bounds((size_t)cg, (size_t)df.G, err)) continue;
                 if (df_sub_acq_rel(df.pending + cg, 1) == 1) {
                     const uint32_t slot = atomicAdd(&df.ctr[1], 1u);
-                    df_st_release(df.queue + slot, cg);
+                    if (tfhe_in_bounds(slot, (size_t)df.G, err)) df_st_release(df.queue + slot, cg);
                 }
             }
         }

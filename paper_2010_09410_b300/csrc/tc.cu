@@ -457,9 +457,16 @@ __device__ __forceinline__ void kara_terms(const uint32_t (&v)[M][DW], F &emit) 
 // digit blocks of the terms of one (tile, row, stage) are consecutive, so term j's unit is
 // j blocks after term 0's (a constant offset).
 struct DigitStore {
-    uint4 *p;  // the thread's unit in term 0's block
+    uint4 *p;     // the thread's unit in term 0's block
+#ifdef TFHE_BOUNDS_CHECK
+    size_t left;  // units of the digit buffer from p on
+    int *err;
+#endif
     template <int j>
     __device__ __forceinline__ void operator()(std::integral_constant<int, j>, const uint32_t (&x)[DW]) const {
+#ifdef TFHE_BOUNDS_CHECK
+        if (!tfhe_in_bounds((size_t)j * (A_STAGE_BYTES / 16), left, err)) return;
+#endif
         p[(size_t)j * (A_STAGE_BYTES / 16)] = make_uint4(x[0], x[1], x[2], x[3]);
     }
 };
@@ -758,6 +765,9 @@ struct BrArgs {
                                 // then per padded tile: done_D, done_E, two_pass (the last
                                 // step + 1 whose products need two passes)
     int *err;
+    // extents of the digit, accumulator, window and combination buffers, for the debug
+    // build's index checks (TFHE_BOUNDS_CHECK)
+    size_t digits_units, acc_words, win_units, bar_words;
 };
 
 // Chunk of stream entry `job` when `units` units are split into `nchunks` chunks of
@@ -952,12 +962,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     }
                     const int r = ts / kstages, ks = ts % kstages;
                     const size_t blk = (((size_t)gt * 2 * l + r) * kstages + ks) * a.nterms + J.j;
+                    size_t a_src = blk * (A_STAGE_BYTES / 16);
+                    if (!tfhe_in_bounds(a_src + A_STAGE_BYTES / 16 - 1, a.digits_units, a.err)) a_src = 0;
                     mbar_arrive_tx(&full[st], A_STAGE_BYTES + BST);
-                    bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + blk * (A_STAGE_BYTES / 16),
-                             A_STAGE_BYTES, &full[st]);
+                    bulk_g2s(a_st + st * A_STAGE_BYTES, a.digits + a_src, A_STAGE_BYTES, &full[st]);
                     const size_t poly = ((size_t)(a.cmux ? gt / a.tpg : J.i) * 2 * l + r) * 2 + J.c;
-                    const uint4 *wsrc = a.win + ((poly * a.nterms + J.j) * PLANES) * 2 * s +
-                                        (P0 + ks * KS);
+                    size_t w_src = ((poly * a.nterms + J.j) * PLANES) * 2 * s + (P0 + ks * KS);
+                    if (!tfhe_in_bounds(w_src + (size_t)(PLANES - 1) * 2 * s + BPL / 16 - 1, a.win_units, a.err))
+                        w_src = 0;
+                    const uint4 *wsrc = a.win + w_src;
 #pragma unroll
                     for (int p = 0; p < PLANES; p++)
                         bulk_g2s(b_st + st * BST + p * BPL, wsrc + (size_t)p * 2 * s, BPL, &full[st]);
@@ -1190,13 +1203,18 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 for (int b = 0; b < NBLK; b++) {
                     const int sg = out_tab[J.j][b];
                     if (!sg) continue;
-                    uint32_t *col = a.acc + ((size_t)(gt * 2 + J.c) * N + (size_t)b * s + w0) * TILE_M + gl;
+                    const size_t col0 = ((size_t)(gt * 2 + J.c) * N + (size_t)b * s + w0) * TILE_M + gl;
+                    uint32_t *col = a.acc + col0;
                     if (sg > 0) {
 #pragma unroll
-                        for (int q = 0; q < EPI_COLS; q++) red_add_u32(col + (size_t)q * TILE_M, sum[EPI_COLS - 1 - q]);
+                        for (int q = 0; q < EPI_COLS; q++)
+                            if (tfhe_in_bounds(col0 + (size_t)q * TILE_M, a.acc_words, a.err))
+                                red_add_u32(col + (size_t)q * TILE_M, sum[EPI_COLS - 1 - q]);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < EPI_COLS; q++) red_add_u32(col + (size_t)q * TILE_M, 0u - sum[EPI_COLS - 1 - q]);
+                        for (int q = 0; q < EPI_COLS; q++)
+                            if (tfhe_in_bounds(col0 + (size_t)q * TILE_M, a.acc_words, a.err))
+                                red_add_u32(col + (size_t)q * TILE_M, 0u - sum[EPI_COLS - 1 - q]);
                     }
                 }
             }
@@ -1259,6 +1277,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                 for (int q = tid; q < nblk * 16; q += DG_THREADS) {
                     const uint4 *ln = a.digits + (size_t)(gt * nblk + q / 16) * (A_STAGE_BYTES / 16) +
                                       (size_t)mg * 128 + (q % 16) * 8;
+#ifdef TFHE_BOUNDS_CHECK
+                    if (!tfhe_in_bounds((size_t)(ln - a.digits) + 7, a.digits_units, a.err)) continue;
+#endif
                     asm volatile("discard.global.L2 [%0], 128;" ::"l"(ln) : "memory");
                 }
             }
@@ -1291,13 +1312,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         const int64_t g = (int64_t)gt * TILE_M + mg * 8 + m;
                         if (g >= a.G) continue;
                         if (k == 0 && !gate_ok(a.types, a.idx, a.num_in, g)) atomicCAS(err, 0, TFHE_EINVAL);
-                        a.bar_w[g * n1 + k] = ms_coef(g, k);
+                        if (tfhe_in_bounds((size_t)g * n1 + k, a.bar_words, a.err)) a.bar_w[g * n1 + k] = ms_coef(g, k);
                     }
                     dg_sync();
                 }
                 if (tid < 8) {
                     const int g = gt * TILE_M + mg * 8 + tid;
-                    bbar_s[tid] = g < a.G ? __ldcg(a.bar + (size_t)g * n1 + n1 - 1) % (uint32_t)(2 * N) : 0u;
+                    bbar_s[tid] = g < a.G && tfhe_in_bounds((size_t)g * n1 + n1 - 1, a.bar_words, a.err)
+                                      ? __ldcg(a.bar + (size_t)g * n1 + n1 - 1) % (uint32_t)(2 * N) : 0u;
                 }
                 dg_sync();
             }
@@ -1306,7 +1328,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
             // fused: coherent load
             const int m8 = tid & 7;
             const int g8 = gt * TILE_M + mg * 8 + m8;
-            const int rot = g8 < a.G && !a.cmux ? (int)(__ldcg(a.bar + (size_t)g8 * a.n1 + i) % (uint32_t)(2 * N)) : 0;
+            const int rot = g8 < a.G && !a.cmux && tfhe_in_bounds((size_t)g8 * a.n1 + i, a.bar_words, a.err)
+                                ? (int)(__ldcg(a.bar + (size_t)g8 * a.n1 + i) % (uint32_t)(2 * N)) : 0;
             for (int v = tid; v < 8 * NBLK; v += DG_THREADS) d_abs[v] = 0;
             int asum[NBLK];
 #pragma unroll
@@ -1322,6 +1345,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                     // Words 0..7 are also written negated after the row's N words.
                     // Step 0 writes ACC(0) instead of reading it.
                     uint32_t *accp = a.acc + (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
+                    const size_t acc0 = (size_t)(gt * 2 + c) * N * TILE_M + mg * 8;
+                    auto acc_ok = [&](int k, int h) {
+                        return tfhe_in_bounds(acc0 + (size_t)k * TILE_M + 4 * h + 3, a.acc_words, a.err);
+                    };
                     auto put = [&](int it, const uint4 &o) {
                         const int k = it >> 1, h = it & 1;
                         uint32_t *rr = d_rows + 4 * h * pitch + k;
@@ -1352,7 +1379,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                     v0[q] = ok ? __ldg(a.cm_d0 + o_) : 0u;
                                     v1[q] = ok ? __ldg(a.cm_d1 + o_) - v0[q] : 0u;
                                 }
-                                __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, make_uint4(v0[0], v0[1], v0[2], v0[3]));
+                                if (acc_ok(k, h))
+                                    __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, make_uint4(v0[0], v0[1], v0[2], v0[3]));
                                 o = make_uint4(v1[0], v1[1], v1[2], v1[3]);
                             } else {
                                 uint32_t v[4] = {0u, 0u, 0u, 0u};
@@ -1365,7 +1393,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                     }
                                 }
                                 o = make_uint4(v[0], v[1], v[2], v[3]);
-                                __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, o);
+                                if (acc_ok(k, h)) __stcg((uint4 *)(accp + (size_t)k * TILE_M) + h, o);
                             }
                             put(it, o);
                         }
@@ -1377,7 +1405,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                             for (int q = 0; q < 8; q++) {
                                 const int it = it0 + q * DG_THREADS;
                                 if (it < 2 * N)
-                                    ov[q] = __ldcg((const uint4 *)(accp + (size_t)(it >> 1) * TILE_M) + (it & 1));
+                                    ov[q] = acc_ok(it >> 1, it & 1)
+                                                ? __ldcg((const uint4 *)(accp + (size_t)(it >> 1) * TILE_M) + (it & 1))
+                                                : make_uint4(0u, 0u, 0u, 0u);
                             }
 #pragma unroll
                             for (int q = 0; q < 8; q++)
@@ -1431,7 +1461,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                                 ah[b] = hadd2(ah[b], habs2(dg[b][w]));
                             }
                         }
-                        DigitStore emit{dst0 + (size_t)jd * jd_stride};
+                        uint4 *dst = dst0 + (size_t)jd * jd_stride;
+#ifdef TFHE_BOUNDS_CHECK
+                        const size_t used = (size_t)(dst - a.digits);
+                        DigitStore emit{dst, used < a.digits_units ? a.digits_units - used : 0, a.err};
+#else
+                        DigitStore emit{dst};
+#endif
                         kara_terms<NBLK>(dg, emit);
                         if (++nacc == 3) {
 #pragma unroll
@@ -1829,7 +1865,7 @@ int tfhe_tc_reserve(tfhe_ctx *ctx, int gates, int level) {
 // Arguments of a `steps`-step persistent launch over the tiles of G rows (gates or
 // CMUXes), with the buffers and job table sized for it; the caller sets the mode fields.
 static int persistent_args(tfhe_ctx *ctx, int G, int steps, int level, const uint4 *win,
-                           BrArgs &args) {
+                           size_t win_bytes, BrArgs &args) {
     const tfhe_params &p = ctx->p;
     TcWorkspace *w = ctx->tc;
     const TcWorkspace::Level &V = w->lv[level];
@@ -1874,6 +1910,10 @@ static int persistent_args(tfhe_ctx *ctx, int G, int steps, int level, const uin
     args.ms_shift = 32 - (ctx->logN + 1);
     args.acc = w->acc_t;
     args.digits = w->digits;
+    args.digits_units = w->digits_cap / 16;
+    args.acc_words = w->acc_t_cap / 4;
+    args.win_units = win_bytes / 16;
+    args.bar_words = (size_t)G * (p.n + 1);
     args.win = win;
     args.sync = w->sync;
     args.err = ctx->d_err;
@@ -1942,7 +1982,7 @@ int tfhe_blind_rotate_tc(tfhe_ctx *ctx, const uint32_t *bar, uint32_t *acc, int 
     const TcWorkspace::Level &V = w->lv[level];
     if (!V.ready) return tfhe_set_error(ctx, TFHE_ENOKEYS, "tensor-core form: key windows not prepared");
     BrArgs args;
-    rc = persistent_args(ctx, G, p.n, level, V.win, args);
+    rc = persistent_args(ctx, G, p.n, level, V.win, V.win_cap, args);
     if (rc != TFHE_OK) return rc;
     args.bar = bar;
     args.in = gates ? gates->in : nullptr;
@@ -2000,7 +2040,7 @@ int tfhe_cmux_tc(tfhe_ctx *ctx, const uint32_t *sel, const CmuxGeom &g, cudaStre
         if (rc != TFHE_OK) return rc;
     }
     BrArgs args;
-    rc = persistent_args(ctx, (int)(tiles * TILE_M), 1, level, w->cm_win, args);
+    rc = persistent_args(ctx, (int)(tiles * TILE_M), 1, level, w->cm_win, w->cm_win_cap, args);
     if (rc != TFHE_OK) return rc;
     args.cmux = 1;
     args.tpg = tpg;
