@@ -383,8 +383,8 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #   --clock-control none -k regex:"k_tc_blind_rotate|k_extract_keyswitch_staged" -s 2 -c 2
     #   python bench.py --form tc --steps 1 --warmup 3 --no-cpu-baseline
-    "k_tc_blind_rotate<2>": {"bytes": 32.780e9 + 63.471e9, "source_sha256": "3144a66b8a665e76049bf93d264a155a73ff19c9488cb2b0bcc6106bd48d062f"},
-    "k_extract_keyswitch_staged": {"bytes": 79.464e6 + 1.275e6, "source_sha256": "72c94a6c879ea426c95cac355d8881772d54492a707151e3b2374c521ecb4774"},
+    "k_tc_blind_rotate<2>": {"bytes": 29.526e9 + 51.952e9, "source_sha256": "6a2c45c26dd77236d643fc5b957f1eee1b5e6cd399b6c1d246823ed536b1c247"},
+    "k_extract_keyswitch_staged": {"bytes": 79.268e6 + 1.284e6, "source_sha256": "72c94a6c879ea426c95cac355d8881772d54492a707151e3b2374c521ecb4774"},
 }
 
 

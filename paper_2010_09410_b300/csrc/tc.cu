@@ -456,10 +456,19 @@ __device__ __forceinline__ void kara_terms(const uint32_t (&v)[M][DW], F &emit) 
 // Stores term j's 8 combinations of one thread (16 bytes) into the A-operand layout: the
 // digit blocks of the terms of one (tile, row, stage) are consecutive, so term j's unit is
 // j blocks after term 0's (a constant offset).
+// The stores carry an L2 evict-last policy: a digit block waits in L2 for its product
+// jobs while the windows and accumulators stream past it (78 GB of DRAM traffic per
+// 4096-gate launch instead of 96 GB with plain stores).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 struct DigitStore {
-    uint4 *p;     // the thread's unit in term 0's block
+    uint4 *p;      // the thread's unit in term 0's block
+    uint64_t pol;  // L2 evict-last policy
 #ifdef TFHE_BOUNDS_CHECK
-    size_t left;  // units of the digit buffer from p on
+    size_t left;   // units of the digit buffer from p on
     int *err;
 #endif
     template <int j>
@@ -467,7 +476,9 @@ struct DigitStore {
 #ifdef TFHE_BOUNDS_CHECK
         if (!tfhe_in_bounds((size_t)j * (A_STAGE_BYTES / 16), left, err)) return;
 #endif
-        p[(size_t)j * (A_STAGE_BYTES / 16)] = make_uint4(x[0], x[1], x[2], x[3]);
+        asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p + (size_t)j * (A_STAGE_BYTES / 16)),
+                     "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "l"(pol)
+                     : "memory");
     }
 };
 
@@ -1236,6 +1247,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
         const int Bgbit = a.Bgbit;
         const uint32_t fmask = ((1u << Bgbit) - 1u) * 0x10001u;
         const uint32_t dsub = f16_bits(1536 + (1 << (Bgbit - 1))) * 0x10001u;
+        const uint64_t pol = l2_evict_last_policy();
         __shared__ int d_job;
         __shared__ int d_abs[8 * NBLK];  // per gate of the part and input block
         for (;;) {
@@ -1464,9 +1476,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_blind_rotate(BrArgs a) {
                         uint4 *dst = dst0 + (size_t)jd * jd_stride;
 #ifdef TFHE_BOUNDS_CHECK
                         const size_t used = (size_t)(dst - a.digits);
-                        DigitStore emit{dst, used < a.digits_units ? a.digits_units - used : 0, a.err};
+                        DigitStore emit{dst, pol, used < a.digits_units ? a.digits_units - used : 0, a.err};
 #else
-                        DigitStore emit{dst};
+                        DigitStore emit{dst, pol};
 #endif
                         kara_terms<NBLK>(dg, emit);
                         if (++nacc == 3) {
