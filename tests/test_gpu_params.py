@@ -52,3 +52,27 @@ def test_cmux_batch(torch_cuda, p):
     got = from_dev(out)
     for q in range(B):
         assert np.array_equal(got[q], orc.cmux(p, sel[q // group], d1[q], d0[q])), q
+
+
+def test_tc_levels_at_n512(torch_cuda):
+    """The tensor-core form at N = 512 on every Karatsuba level it supports (level 0: 4
+    stages of 128 digits per row; level 2: s = 128, one stage), 140 gates (a full tile and a
+    ragged one), word for word against the oracle on the first and last gate of each tile."""
+    torch = torch_cuda
+    p = P512
+    ctx, k = gpu_context(p, SEED)
+    G = 140
+    b = ti.flat_level(G, seed=SEED, p=p)
+    sample = [0, 127, 128, 139]
+    want = orc.gate_batch(p, k.bsk, k.ksk, b.inp, b.types, b.idx, gates=sample)
+    try:
+        for level in (0, 1, 2):
+            ctx.set_tc_level(level)
+            out = torch.zeros((G, p.n + 1), dtype=torch.int32, device="cuda")
+            ctx.gate_batch(to_dev(b.inp), to_dev(b.types), to_dev(b.idx), out, form=1)
+            ctx.sync()
+            got = from_dev(out)
+            assert np.array_equal(orc.tlwe_decrypt(k.s0, got), b.expected), level
+            assert np.array_equal(got[sample], want), level
+    finally:
+        ctx.set_tc_level(-1)
